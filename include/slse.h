@@ -1,0 +1,170 @@
+/*
+ * slse.h - C ABI of the GB300 (sm_103a) implementation of SLSE-FRS, the
+ * "Sequential Least-Squares Estimators with Fast Randomized Sketching" method
+ * (arXiv 2509.06856).
+ *
+ * Problem (paper Sec. 1): given tall data X (N x d, N >> d, full column rank) and
+ * Y (N), return the OLS estimator beta-hat = argmin 1/2 ||Y - X beta||^2.
+ * SLSE-FRS (Algorithm 2, Sec. 3) forms one randomized Hadamard transform of
+ * [X | Y], takes nested row samples of growing size m_1 < ... < m_K from it, runs
+ * a_i momentum-IHS (M-IHS) steps on each sketched subproblem (1st stage, Eq. 3.1)
+ * and finishes with full-data M-IHS steps (2nd stage, Eq. 3.2).  Every M-IHS step
+ * is preconditioned by the fixed sketched Hessian H-hat = (S-hat X)^T (S-hat X),
+ * applied through the R factor of a QR of S-hat X (Appendix, implementation
+ * details).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Matrices are row-major.  X has leading dimension ldx >= d (elements).
+ * - Pointers named "device" must be CUDA device (or managed) memory of the
+ *   current device; the call enqueues its kernels on `stream` (0 = legacy
+ *   default stream).  Pointers named "host" are ordinary host memory.
+ * - Workspace: `workspace` is caller-owned device memory of `ws_bytes` bytes,
+ *   aligned to 256 bytes.  If `workspace` is NULL the library allocates the
+ *   workspace itself with cudaMallocAsync on `stream` and frees it before
+ *   returning (stream-ordered).  If `workspace` is not NULL and `ws_bytes` is
+ *   smaller than slse_workspace_size(...), the call returns SLSE_ENOMEM and
+ *   launches nothing.
+ * - Errors are returned as slse_status codes; no C++ exception crosses the ABI.
+ *   SLSE_EINVAL means an argument failed validation and nothing was launched.
+ * - Same inputs + same seed => bit-identical random draws and sketch, and a
+ *   deterministic estimate (all reductions have a fixed order).
+ * - Gradient sign: g = X^T (Y - X beta), i.e. minus the paper's
+ *   nabla f = X^T (X beta - Y) (Sec. 1); the M-IHS step adds mu H-hat^{-1} g.
+ * - Kernel limits of this build: 1 <= d <= 512, d <= N, N' = 2^ceil(log2 N) <= 2^26.
+ */
+#ifndef SLSE_H
+#define SLSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *slse_stream_t; /* the same type as cudaStream_t */
+
+typedef enum {
+  SLSE_OK = 0,
+  SLSE_EINVAL = 1,   /* invalid argument; nothing launched */
+  SLSE_ENOMEM = 2,   /* workspace too small, or the internal allocation failed */
+  SLSE_ECUDA = 3,    /* a CUDA runtime call failed */
+  SLSE_ENOTCONV = 4, /* tol > 0 and the 2nd stage reached T first; beta_out holds the last iterate */
+  SLSE_ENUMERIC = 5, /* NaN/Inf in an iterate, or a zero pivot in the QR */
+  SLSE_ETIMEOUT = 6  /* a bounded device-side wait gave up (grid barrier in the QR kernel) */
+} slse_status;
+
+typedef enum { SLSE_F64 = 0, SLSE_F32 = 1, SLSE_BF16 = 2 } slse_dtype;
+
+typedef enum { SLSE_SRHT = 0, SLSE_COUNTSKETCH = 1, SLSE_GAUSSIAN = 2 } slse_sketch_kind;
+
+/* Arithmetic of the path.
+ * SLSE_PREC_FP64: every step in FP64 (X stored F64 or F32; F32 values are widened exactly).
+ * SLSE_PREC_MIXED_BF16: sketch applied in FP32 and stored in BF16; 1st-stage gradients on
+ *   the BF16 sketch with FP32 accumulation; 2nd-stage residual-gradient in FP32 with
+ *   error-free (TwoProd/TwoSum) residuals against an FP64 base point and two-sum
+ *   compensated accumulation; QR, preconditioner and update in FP64.  Requires X F32. */
+typedef enum { SLSE_PREC_FP64 = 0, SLSE_PREC_MIXED_BF16 = 1, SLSE_PREC_MIXED_FP8 = 2 } slse_precision;
+
+typedef struct {
+  int64_t N;       /* rows, N >= d */
+  int32_t d;       /* columns, 1 <= d <= 512 */
+  int32_t dtype;   /* slse_dtype of X and Y: SLSE_F64 or SLSE_F32 */
+  const void *X;   /* device, N x d row-major, leading dimension ldx */
+  int64_t ldx;     /* >= d */
+  const void *Y;   /* device, N, same dtype as X */
+} slse_problem;
+
+typedef struct {
+  int32_t K;            /* number of sketched subproblems (0 = no 1st stage) */
+  const int64_t *m;     /* host, K ascending sketch sizes, 1 <= m_i <= N' */
+  const int32_t *a;     /* host, K inner iteration counts a_i >= 0 */
+  int64_t r;            /* Hessian sketch size, d <= r <= N' */
+  double mu, eta;       /* M-IHS step and momentum */
+  int32_t T;            /* cap on the total number of iterations (both stages) */
+  double tol;           /* 2nd stage stops when ||b+ - b|| <= tol (1-rho)/rho ||b+||, rho = sqrt(d/r); <= 0: run to T */
+  int32_t kind;         /* slse_sketch_kind (only SLSE_SRHT in this build) */
+  int32_t prec;         /* slse_precision */
+  int32_t momentum_reset; /* 1: beta_{-1} = beta_0 at the start of each subproblem and of the 2nd stage */
+} slse_schedule;
+
+typedef struct {
+  double ms_draws, ms_sketch, ms_qr, ms_stage1, ms_stage2, ms_total; /* CUDA-event times */
+  int32_t iters_stage1, iters_stage2;
+  double final_rel_step;  /* ||b_T - b_{T-1}|| / ||b_T|| of the last iteration */
+  double bytes_moved;     /* algorithmic HBM bytes of the sketch passes and gradient passes */
+  int32_t rebases;        /* mixed path: number of 2nd-stage residual re-bases */
+  int32_t status;
+} slse_report;
+
+typedef struct {
+  double *beta_hist;  /* device, cap x d: row t = iterate after iteration t+1 (NULL: none) */
+  float *ms_hist;     /* host, cap: CUDA-event ms from the call's start to the end of iteration t+1 */
+  int32_t cap;
+  int32_t count;      /* out: iterations recorded */
+} slse_trace;
+
+/* Workspace query.  op: SLSE_OP_FIT (sched required), SLSE_OP_SKETCH (arg = m, prec in
+ * sched->prec if sched != NULL else FP64), SLSE_OP_GRAD, SLSE_OP_DRAWS (arg = N), SLSE_OP_QR
+ * (arg = r).  Returns 0 for invalid arguments. */
+enum { SLSE_OP_FIT = 0, SLSE_OP_SKETCH = 1, SLSE_OP_GRAD = 2, SLSE_OP_DRAWS = 3, SLSE_OP_QR = 4 };
+size_t slse_workspace_size(const slse_problem *prob, const slse_schedule *sched, int32_t op, int64_t arg);
+
+/* Algorithm 2 end to end (paper Sec. 3).  seed selects the random draws D, P and the
+ * sampling order (Philox4x32-10).  beta_out: host, d doubles.  report, trace: nullable.
+ * Synchronous: returns after beta_out is written.  sched == NULL selects the paper's
+ * experimental defaults (slse_default_schedule) in FP64. */
+slse_status slse_fit(const slse_problem *prob, const slse_schedule *sched, uint64_t seed,
+                     double *beta_out, slse_report *report, slse_trace *trace,
+                     void *workspace, size_t ws_bytes, slse_stream_t stream);
+
+/* One SRHT sketch of size m (Sec. 3): SX = sqrt(N'/m) * rows sigma[0..m) of H D P X_pad / sqrt(N'),
+ * SY likewise.  prec FP64 -> SX, SY are double; MIXED_BF16 -> bf16.  SX: device m x ldsx
+ * (ldsx >= d), SY: device m.  Asynchronous on `stream`. */
+slse_status slse_sketch(const slse_problem *prob, int32_t kind, int32_t prec, uint64_t seed, int64_t m,
+                        void *SX, int64_t ldsx, void *SY, void *workspace, size_t ws_bytes,
+                        slse_stream_t stream);
+
+/* Residual-gradient pass g = X^T (Y - X beta) (Sec. 3, Eq. 3.2 and its FLOP count).
+ * beta: device d doubles; g_out: device d doubles.  prec FP64: FP64 arithmetic.
+ * prec MIXED_BF16 (X F32): error-free FP32 residuals and compensated accumulation.
+ * Asynchronous on `stream`. */
+slse_status slse_grad(const slse_problem *prob, const double *beta, double *g_out, int32_t prec,
+                      void *workspace, size_t ws_bytes, slse_stream_t stream);
+
+/* The random draws of the sketch (Sec. 3, matrices D, P and B) for N' = 2^ceil(log2 N):
+ * P (device int32, N'): the permutation, row j of P X is X[P[j]];
+ * sigma (device int32, N'): the sampling order, sketch i keeps rows sigma[0..m_i);
+ * D (device int8, N', nullable): the Rademacher signs +-1.  Asynchronous. */
+slse_status slse_draws(int64_t N, uint64_t seed, int32_t *P, int32_t *sigma, int8_t *D,
+                       void *workspace, size_t ws_bytes, slse_stream_t stream);
+
+/* FP64 Householder QR of the r x d matrix A (device, row-major, lda >= d, r >= d), as used
+ * for H-hat^{-1} v = R^{-1} R^{-T} v (Appendix, implementation details).  A is not modified.
+ * R: device d x d (ld d), upper triangular with non-negative diagonal.  Hinv: device d x d
+ * (ld d) = (R^T R)^{-1}, nullable.  Asynchronous. */
+slse_status slse_qr(const double *A, int64_t r, int32_t d, int64_t lda, double *R, double *Hinv,
+                    void *workspace, size_t ws_bytes, slse_stream_t stream);
+
+/* The paper's experimental schedule (Sec. 5 preamble): r = 6d, eta = d/r, mu = (1-eta)^2,
+ * m_1 = 8d doubling while m_i <= N'/2, a_i = 2, T = 100, tol = 0, FP64, momentum reset.
+ * Writes at most cap entries into m_buf/a_buf (host) and points out->m/out->a at them.
+ * Returns K (the number of sizes the schedule wants; > cap means truncated). */
+int32_t slse_default_schedule(int64_t N, int32_t d, slse_schedule *out, int64_t *m_buf, int32_t *a_buf,
+                              int32_t cap);
+
+/* Theorem 4.3 lower bound on the inner iterations: log_3[((1+omega) r + 1)/omega] with
+ * r = sqrt((m_i - d)/(m_prev - d)).  Host-only.  Returns NaN for m_prev <= d or omega <= 0. */
+double slse_ai_bound(double omega, int64_t m_prev, int64_t m_i, int32_t d);
+
+const char *slse_status_string(int32_t status);
+
+/* Library version: major*10000 + minor*100 + patch. */
+int32_t slse_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLSE_H */

@@ -1,0 +1,279 @@
+"""GB300 (sm_103a) SLSE-FRS: Python binding over the C ABI declared in include/slse.h.
+
+Argument marshalling only: every step of the method runs in the CUDA kernels of
+``libslse.so``.  PyTorch is used for device memory and the current CUDA stream.
+The library must be built first (``python paper_2509_06856_gb300/build.py`` or
+``__graft_entry__.build()``); importing this package without it raises ImportError.
+
+Paper: "Sequential Least-Squares Estimators with Fast Randomized Sketching for
+Linear Statistical Models" (arXiv 2509.06856), Algorithm 2.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libslse.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libslse.so is not built ({LIB_PATH}); run python paper_2509_06856_gb300/build.py")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+# ----------------------------------------------------------------------------- C types
+OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ENUMERIC, ETIMEOUT = range(7)
+F64, F32, BF16 = 0, 1, 2
+SRHT, COUNTSKETCH, GAUSSIAN = 0, 1, 2
+PREC = {"fp64": 0, "mixed_bf16": 1, "mixed_fp8": 2}
+OP_FIT, OP_SKETCH, OP_GRAD, OP_DRAWS, OP_QR = range(5)
+
+
+class CProblem(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("d", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("X", ctypes.c_void_p), ("ldx", ctypes.c_int64), ("Y", ctypes.c_void_p)]
+
+
+class CSchedule(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("m", ctypes.POINTER(ctypes.c_int64)), ("a", ctypes.POINTER(ctypes.c_int32)),
+                ("r", ctypes.c_int64), ("mu", ctypes.c_double), ("eta", ctypes.c_double), ("T", ctypes.c_int32),
+                ("tol", ctypes.c_double), ("kind", ctypes.c_int32), ("prec", ctypes.c_int32),
+                ("momentum_reset", ctypes.c_int32)]
+
+
+class CReport(ctypes.Structure):
+    _fields_ = [("ms_draws", ctypes.c_double), ("ms_sketch", ctypes.c_double), ("ms_qr", ctypes.c_double),
+                ("ms_stage1", ctypes.c_double), ("ms_stage2", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("iters_stage1", ctypes.c_int32), ("iters_stage2", ctypes.c_int32),
+                ("final_rel_step", ctypes.c_double), ("bytes_moved", ctypes.c_double),
+                ("rebases", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+
+class CTrace(ctypes.Structure):
+    _fields_ = [("beta_hist", ctypes.c_void_p), ("ms_hist", ctypes.POINTER(ctypes.c_float)),
+                ("cap", ctypes.c_int32), ("count", ctypes.c_int32)]
+
+
+_vp, _sz, _i32, _i64, _u64 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+_lib.slse_workspace_size.restype = _sz
+_lib.slse_workspace_size.argtypes = [ctypes.POINTER(CProblem), ctypes.POINTER(CSchedule), _i32, _i64]
+_lib.slse_fit.restype = _i32
+_lib.slse_fit.argtypes = [ctypes.POINTER(CProblem), ctypes.POINTER(CSchedule), _u64, ctypes.POINTER(ctypes.c_double),
+                          ctypes.POINTER(CReport), ctypes.POINTER(CTrace), _vp, _sz, _vp]
+_lib.slse_sketch.restype = _i32
+_lib.slse_sketch.argtypes = [ctypes.POINTER(CProblem), _i32, _i32, _u64, _i64, _vp, _i64, _vp, _vp, _sz, _vp]
+_lib.slse_grad.restype = _i32
+_lib.slse_grad.argtypes = [ctypes.POINTER(CProblem), _vp, _vp, _i32, _vp, _sz, _vp]
+_lib.slse_draws.restype = _i32
+_lib.slse_draws.argtypes = [_i64, _u64, _vp, _vp, _vp, _vp, _sz, _vp]
+_lib.slse_qr.restype = _i32
+_lib.slse_qr.argtypes = [_vp, _i64, _i32, _i64, _vp, _vp, _vp, _sz, _vp]
+_lib.slse_default_schedule.restype = _i32
+_lib.slse_default_schedule.argtypes = [_i64, _i32, ctypes.POINTER(CSchedule), ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_int32), _i32]
+_lib.slse_ai_bound.restype = ctypes.c_double
+_lib.slse_ai_bound.argtypes = [ctypes.c_double, _i64, _i64, _i32]
+_lib.slse_status_string.restype = ctypes.c_char_p
+_lib.slse_status_string.argtypes = [_i32]
+_lib.slse_version.restype = _i32
+
+EXPORTED = ["slse_workspace_size", "slse_fit", "slse_sketch", "slse_grad", "slse_draws", "slse_qr",
+            "slse_default_schedule", "slse_ai_bound", "slse_status_string", "slse_version"]
+
+
+class SlseError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {_lib.slse_status_string(status).decode()} (status {status})")
+        self.status = status
+
+
+def status_string(s: int) -> str:
+    return _lib.slse_status_string(s).decode()
+
+
+def version() -> int:
+    return int(_lib.slse_version())
+
+
+def ai_bound(omega: float, m_prev: int, m_i: int, d: int) -> float:
+    """Theorem 4.3 lower bound on a_i (host helper of the library)."""
+    return float(_lib.slse_ai_bound(omega, m_prev, m_i, d))
+
+
+# ----------------------------------------------------------------------------- schedule
+@dataclass
+class Schedule:
+    m: list
+    a: list
+    r: int
+    mu: float
+    eta: float
+    T: int = 100
+    tol: float = 0.0
+    prec: str = "fp64"
+    momentum_reset: bool = True
+    kind: int = SRHT
+    _keep: list = field(default_factory=list, repr=False)
+
+    def to_c(self) -> CSchedule:
+        K = len(self.m)
+        m_arr = (ctypes.c_int64 * max(1, K))(*[int(v) for v in self.m])
+        a_arr = (ctypes.c_int32 * max(1, K))(*[int(v) for v in self.a])
+        self._keep = [m_arr, a_arr]
+        return CSchedule(K, ctypes.cast(m_arr, ctypes.POINTER(ctypes.c_int64)),
+                         ctypes.cast(a_arr, ctypes.POINTER(ctypes.c_int32)), int(self.r), float(self.mu),
+                         float(self.eta), int(self.T), float(self.tol), int(self.kind), PREC[self.prec],
+                         1 if self.momentum_reset else 0)
+
+
+def default_schedule(N: int, d: int, prec: str = "fp64", T: int = 100, tol: float = 0.0) -> Schedule:
+    """The paper's experimental schedule (Sec. 5 preamble), from the library."""
+    c = CSchedule()
+    mb = (ctypes.c_int64 * 64)()
+    ab = (ctypes.c_int32 * 64)()
+    K = _lib.slse_default_schedule(N, d, ctypes.byref(c), mb, ab, 64)
+    if K < 0 or K > 64:
+        raise ValueError("invalid problem size")
+    return Schedule(m=list(mb[:K]), a=list(ab[:K]), r=c.r, mu=c.mu, eta=c.eta, T=T, tol=tol, prec=prec,
+                    momentum_reset=bool(c.momentum_reset))
+
+
+# ----------------------------------------------------------------------------- helpers
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _dtype_code(t) -> int:
+    torch = _torch()
+    if t.dtype == torch.float64:
+        return F64
+    if t.dtype == torch.float32:
+        return F32
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def problem(X, Y) -> CProblem:
+    """C problem struct for device tensors X (N x d, unit column stride) and Y (N)."""
+    if X.dim() != 2 or X.stride(1) != 1:
+        raise ValueError("X must be a row-major 2-D tensor")
+    if Y.dim() != 1 or Y.stride(0) != 1 or Y.shape[0] != X.shape[0] or Y.dtype != X.dtype:
+        raise ValueError("Y must be a contiguous vector matching X")
+    return CProblem(X.shape[0], X.shape[1], _dtype_code(X), X.data_ptr(), X.stride(0), Y.data_ptr())
+
+
+def workspace_size(X, Y, op: int = OP_FIT, schedule: Schedule | None = None, arg: int = 0) -> int:
+    p = problem(X, Y)
+    cs = schedule.to_c() if schedule is not None else None
+    return int(_lib.slse_workspace_size(ctypes.byref(p), ctypes.byref(cs) if cs is not None else None, op, arg))
+
+
+def alloc_workspace(nbytes: int, device=None):
+    torch = _torch()
+    return torch.empty(max(256, nbytes), dtype=torch.uint8, device=device or "cuda")
+
+
+def _check(status: int, what: str, allow=()):
+    if status != OK and status not in allow:
+        raise SlseError(status, what)
+
+
+@dataclass
+class FitResult:
+    beta: np.ndarray
+    status: int
+    report: dict
+    beta_hist: object = None   # torch (count x d) on the device, when traced
+    ms_hist: list = None
+
+
+def fit(X, Y, schedule: Schedule | None = None, seed: int = 0, workspace=None, trace_cap: int = 0,
+        stream=None, raise_on_error: bool = True) -> FitResult:
+    """slse_fit: Algorithm 2 on device tensors X, Y.  Returns beta-hat on the host."""
+    torch = _torch()
+    p = problem(X, Y)
+    cs = schedule.to_c() if schedule is not None else None
+    beta = (ctypes.c_double * p.d)()
+    rep = CReport()
+    tr = None
+    hist = None
+    ms = None
+    if trace_cap > 0:
+        hist = torch.zeros((trace_cap, p.d), dtype=torch.float64, device=X.device)
+        ms = (ctypes.c_float * trace_cap)()
+        tr = CTrace(hist.data_ptr(), ctypes.cast(ms, ctypes.POINTER(ctypes.c_float)), trace_cap, 0)
+    ws_ptr, ws_len = (workspace.data_ptr(), workspace.numel() * workspace.element_size()) if workspace is not None \
+        else (None, 0)
+    st = _lib.slse_fit(ctypes.byref(p), ctypes.byref(cs) if cs is not None else None, seed, beta, ctypes.byref(rep),
+                       ctypes.byref(tr) if tr is not None else None, ws_ptr, ws_len, _stream(stream))
+    if raise_on_error:
+        _check(st, "slse_fit", allow=(ENOTCONV,))
+    report = {f: getattr(rep, f) for f, _ in CReport._fields_}
+    out = FitResult(beta=np.frombuffer(beta, dtype=np.float64).copy(), status=st, report=report)
+    if tr is not None:
+        out.beta_hist = hist[:tr.count]
+        out.ms_hist = list(ms[:tr.count])
+    return out
+
+
+def sketch(X, Y, m: int, seed: int = 0, prec: str = "fp64", workspace=None, stream=None):
+    """slse_sketch: (S X, S Y) for one SRHT sketch of size m.  FP64 -> float64, mixed -> bfloat16."""
+    torch = _torch()
+    p = problem(X, Y)
+    dt = torch.float64 if prec == "fp64" else torch.bfloat16
+    SX = torch.empty((m, p.d), dtype=dt, device=X.device)
+    SY = torch.empty(m, dtype=dt, device=X.device)
+    ws_ptr, ws_len = (workspace.data_ptr(), workspace.numel()) if workspace is not None else (None, 0)
+    st = _lib.slse_sketch(ctypes.byref(p), SRHT, PREC[prec], seed, m, SX.data_ptr(), p.d, SY.data_ptr(), ws_ptr,
+                          ws_len, _stream(stream))
+    _check(st, "slse_sketch")
+    return SX, SY
+
+
+def grad(X, Y, beta, prec: str = "fp64", workspace=None, stream=None):
+    """slse_grad: g = X^T (Y - X beta) on the device (float64 vector)."""
+    torch = _torch()
+    p = problem(X, Y)
+    b = beta if (torch.is_tensor(beta) and beta.is_cuda) else torch.as_tensor(np.asarray(beta, np.float64),
+                                                                                device=X.device)
+    b = b.to(torch.float64).contiguous()
+    g = torch.empty(p.d, dtype=torch.float64, device=X.device)
+    ws_ptr, ws_len = (workspace.data_ptr(), workspace.numel()) if workspace is not None else (None, 0)
+    st = _lib.slse_grad(ctypes.byref(p), b.data_ptr(), g.data_ptr(), PREC[prec], ws_ptr, ws_len, _stream(stream))
+    _check(st, "slse_grad")
+    return g
+
+
+def draws(N: int, seed: int, device="cuda", stream=None):
+    """slse_draws: (P, sigma, D) for N' = 2^ceil(log2 N)."""
+    torch = _torch()
+    Np = 1 << max(0, int(N - 1).bit_length())
+    P = torch.empty(Np, dtype=torch.int32, device=device)
+    sigma = torch.empty(Np, dtype=torch.int32, device=device)
+    D = torch.empty(Np, dtype=torch.int8, device=device)
+    st = _lib.slse_draws(N, seed, P.data_ptr(), sigma.data_ptr(), D.data_ptr(), None, 0, _stream(stream))
+    _check(st, "slse_draws")
+    return P, sigma, D
+
+
+def qr(A, want_hinv: bool = True, stream=None):
+    """slse_qr: FP64 Householder R (non-negative diagonal) and optionally (R^T R)^{-1}."""
+    torch = _torch()
+    if A.dtype != torch.float64 or A.dim() != 2 or A.stride(1) != 1:
+        raise ValueError("A must be a row-major float64 matrix")
+    r, d = A.shape
+    R = torch.empty((d, d), dtype=torch.float64, device=A.device)
+    H = torch.empty((d, d), dtype=torch.float64, device=A.device) if want_hinv else None
+    st = _lib.slse_qr(A.data_ptr(), r, d, A.stride(0), R.data_ptr(), H.data_ptr() if H is not None else None, None, 0,
+                      _stream(stream))
+    _check(st, "slse_qr")
+    return R, H

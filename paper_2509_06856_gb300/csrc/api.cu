@@ -1,0 +1,607 @@
+// C ABI of the SLSE-FRS library: argument validation, workspace layout, and the
+// host-side stage loop of Algorithm 2 (paper Sec. 3).  All arithmetic runs in the
+// kernels of draws.cu, srht.cu, grad.cu and linalg.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "slse_internal.cuh"
+
+using namespace slse;
+
+namespace {
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+constexpr size_t kStateBytes = 4096;  // DevState + per-CTA partials of the update kernel
+constexpr int64_t kMaxNp = int64_t(1) << 26;
+
+int num_sms() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return n;
+}
+
+int64_t padded(int64_t N) {
+  int64_t p = 1;
+  while (p < N) p <<= 1;
+  return p;
+}
+
+bool valid_problem(const slse_problem *p) {
+  if (!p || !p->X || !p->Y) return false;
+  if (p->N < 1 || p->d < 1 || p->d > 512 || p->d > p->N) return false;
+  if (p->ldx < p->d) return false;
+  if (p->dtype != SLSE_F64 && p->dtype != SLSE_F32) return false;
+  if (padded(p->N) > kMaxNp) return false;
+  return true;
+}
+
+struct Sched {
+  std::vector<int64_t> m;
+  std::vector<int32_t> a;
+  int64_t r;
+  double mu, eta, tol;
+  int T, prec, momentum_reset;
+};
+
+bool make_sched(const slse_problem *p, const slse_schedule *s, Sched &o) {
+  const int64_t Np = padded(p->N);
+  if (!s) {
+    int64_t mb[64];
+    int32_t ab[64];
+    slse_schedule d;
+    const int K = slse_default_schedule(p->N, p->d, &d, mb, ab, 64);
+    if (K > 64) return false;
+    o.m.assign(mb, mb + K);
+    o.a.assign(ab, ab + K);
+    o.r = d.r; o.mu = d.mu; o.eta = d.eta; o.tol = d.tol; o.T = d.T; o.prec = d.prec;
+    o.momentum_reset = d.momentum_reset;
+    return true;
+  }
+  if (s->K < 0 || (s->K > 0 && (!s->m || !s->a))) return false;
+  if (s->kind != SLSE_SRHT) return false;
+  if (s->prec != SLSE_PREC_FP64 && s->prec != SLSE_PREC_MIXED_BF16) return false;
+  if (s->prec == SLSE_PREC_MIXED_BF16 && p->dtype != SLSE_F32) return false;
+  if (s->r < p->d || s->r > Np || s->T < 0) return false;
+  if (!std::isfinite(s->mu) || !std::isfinite(s->eta) || !std::isfinite(s->tol)) return false;
+  o.m.assign(s->m, s->m + s->K);
+  o.a.assign(s->a, s->a + s->K);
+  for (int i = 0; i < s->K; ++i) {
+    if (o.m[i] < 1 || o.m[i] > Np || o.a[i] < 0) return false;
+    if (i > 0 && o.m[i] <= o.m[i - 1]) return false;
+  }
+  o.r = s->r; o.mu = s->mu; o.eta = s->eta; o.tol = s->tol; o.T = s->T; o.prec = s->prec;
+  o.momentum_reset = s->momentum_reset;
+  return true;
+}
+
+// ------------------------------------------------------------------ workspace layout
+struct Layout {
+  size_t total = 0;
+  size_t take(size_t bytes) {
+    const size_t o = align256(total);
+    total = o + align256(bytes);
+    return o;
+  }
+};
+
+struct FitLayout {
+  int64_t Np, n_samp, h0, ldu;
+  SrhtPlan sp;
+  int nblk;
+  size_t o_state, o_psd, o_sigma, o_pos, o_big, o_wy, o_u, o_v, o_A, o_R, o_Hinv, o_qr, o_part, o_g, o_ring,
+      o_b0, o_d32, o_out, o_r0;
+  size_t total;
+};
+
+size_t elem_bytes_u(int prec) { return prec == SLSE_PREC_FP64 ? 8 : 2; }
+
+FitLayout fit_layout(const slse_problem *p, const Sched &s, int nsm) {
+  FitLayout L{};
+  const int d = p->d;
+  L.Np = padded(p->N);
+  L.sp = srht_plan(L.Np);
+  const int64_t mK = s.m.empty() ? 0 : s.m.back();
+  if (mK + s.r <= L.Np) { L.h0 = mK; L.n_samp = mK + s.r; }
+  else { L.h0 = 0; L.n_samp = mK > s.r ? mK : s.r; }
+  L.ldu = (d + 7) & ~int64_t(7);
+  const size_t eu = elem_bytes_u(s.prec);
+  L.nblk = 2 * (nsm > 0 ? nsm : 152);
+  Layout w;
+  L.o_state = w.take(kStateBytes);
+  L.o_psd = w.take(4 * (size_t)L.Np);
+  L.o_sigma = w.take(4 * (size_t)L.Np);
+  L.o_pos = w.take(4 * (size_t)L.Np);
+  size_t big = draws_ws_bytes(L.Np);
+  const size_t wbytes = L.sp.single ? 0 : (size_t)L.Np * L.ldu * eu;
+  const size_t wybytes = L.sp.single ? 0 : (size_t)L.Np * eu;
+  if (wbytes + align256(wybytes) + 256 > big) big = align256(wbytes) + align256(wybytes);
+  L.o_big = w.take(big);
+  L.o_wy = L.o_big + align256(wbytes);
+  L.o_u = w.take((size_t)L.n_samp * L.ldu * eu);
+  L.o_v = w.take((size_t)L.n_samp * eu);
+  L.o_A = w.take((size_t)s.r * d * 8);
+  L.o_R = w.take((size_t)d * d * 8);
+  L.o_Hinv = w.take((size_t)d * d * 8);
+  L.o_qr = w.take(qr_ws_bytes(s.r, d, nsm > 0 ? nsm : 152));
+  L.o_part = w.take((size_t)L.nblk * d * 8);
+  L.o_g = w.take((size_t)d * 8);
+  L.o_ring = w.take((size_t)3 * d * 8);
+  L.o_b0 = w.take((size_t)d * 8);
+  L.o_d32 = w.take((size_t)d * 4);
+  L.o_out = w.take((size_t)d * 8);
+  L.o_r0 = w.take(s.prec == SLSE_PREC_MIXED_BF16 ? (size_t)p->N * 4 : 0);
+  L.total = w.total;
+  return L;
+}
+
+struct SketchLayout {
+  int64_t Np, ldw;
+  SrhtPlan sp;
+  size_t o_psd, o_sigma, o_pos, o_big, o_wy, total;
+};
+
+SketchLayout sketch_layout(const slse_problem *p, int prec) {
+  SketchLayout L{};
+  L.Np = padded(p->N);
+  L.sp = srht_plan(L.Np);
+  L.ldw = (p->d + 7) & ~int64_t(7);
+  const size_t eu = elem_bytes_u(prec);
+  Layout w;
+  L.o_psd = w.take(4 * (size_t)L.Np);
+  L.o_sigma = w.take(4 * (size_t)L.Np);
+  L.o_pos = w.take(4 * (size_t)L.Np);
+  size_t big = draws_ws_bytes(L.Np);
+  const size_t wbytes = L.sp.single ? 0 : (size_t)L.Np * L.ldw * eu;
+  const size_t wybytes = L.sp.single ? 0 : (size_t)L.Np * eu;
+  if (align256(wbytes) + align256(wybytes) > big) big = align256(wbytes) + align256(wybytes);
+  L.o_big = w.take(big);
+  L.o_wy = L.o_big + align256(wbytes);
+  L.total = w.total;
+  return L;
+}
+
+size_t grad_ws(const slse_problem *p, int nsm) {
+  Layout w;
+  w.take(kStateBytes);
+  w.take((size_t)2 * (nsm > 0 ? nsm : 152) * p->d * 8);
+  return w.total;
+}
+
+// ------------------------------------------------------------------ helpers
+__global__ void k_init_state(DevState *st, int rebase) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    DevState z = {};
+    z.rebase = rebase;
+    *st = z;
+  }
+}
+__global__ void k_set_stage2(DevState *st, int rebase) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    st->rebase = rebase;
+    st->done = 0;
+  }
+}
+
+struct Workspace {
+  void *ptr = nullptr;
+  bool owned = false;
+  cudaStream_t s = nullptr;
+  ~Workspace() {
+    if (owned && ptr) cudaFreeAsync(ptr, s);
+  }
+};
+
+slse_status acquire(Workspace &w, void *user, size_t user_bytes, size_t need, cudaStream_t s) {
+  w.s = s;
+  if (user) {
+    if (user_bytes < need) return SLSE_ENOMEM;
+    if (reinterpret_cast<uintptr_t>(user) % 256 != 0) return SLSE_EINVAL;
+    w.ptr = user;
+    return SLSE_OK;
+  }
+  if (cudaMallocAsync(&w.ptr, need, s) != cudaSuccess) {
+    cudaGetLastError();
+    w.ptr = nullptr;
+    return SLSE_ENOMEM;
+  }
+  w.owned = true;
+  return SLSE_OK;
+}
+
+struct Events {
+  std::vector<cudaEvent_t> ev;
+  cudaEvent_t make() {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    ev.push_back(e);
+    return e;
+  }
+  ~Events() {
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+};
+
+// Pinned host mailbox for the stage-2 stop flag (one per host thread).
+struct Mailbox {
+  DevState *h = nullptr;
+  ~Mailbox() {
+    if (h) cudaFreeHost(h);
+  }
+  DevState *get() {
+    if (!h && cudaHostAlloc((void **)&h, 4 * sizeof(DevState), cudaHostAllocDefault) != cudaSuccess) h = nullptr;
+    return h;
+  }
+};
+thread_local Mailbox t_mailbox;
+
+float ms_between(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  if (a && b && cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+    cudaGetLastError();
+    ms = 0.f;
+  }
+  return ms;
+}
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) {                       \
+      if (getenv("SLSE_LOG"))                      \
+        fprintf(stderr, "slse: %s failed: %s (%s:%d)\n", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return SLSE_ECUDA;                           \
+    }                                              \
+  } while (0)
+
+slse_status status_from_bits(unsigned bits) {
+  if (bits & ST_TIMEOUT) return SLSE_ETIMEOUT;
+  if (bits & ST_NUMERIC) return SLSE_ENUMERIC;
+  if (bits & ST_NOTCONV) return SLSE_ENOTCONV;
+  return SLSE_OK;
+}
+
+int grad_blocks(int64_t rows, int maxblk) {
+  int64_t b = (rows + 31) / 32;
+  if (b > maxblk) b = maxblk;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+slse_status fit_impl(const slse_problem *p, const Sched &s, uint64_t seed, double *beta_out, slse_report *rep,
+                     slse_trace *tr, void *ws_user, size_t ws_bytes, cudaStream_t st) {
+  const int nsm = num_sms();
+  if (nsm <= 0) return SLSE_ECUDA;
+  const FitLayout L = fit_layout(p, s, nsm);
+  Workspace W;
+  slse_status a = acquire(W, ws_user, ws_bytes, L.total, st);
+  if (a != SLSE_OK) return a;
+  char *base = static_cast<char *>(W.ptr);
+  DevState *dst = reinterpret_cast<DevState *>(base + L.o_state);
+  int32_t *Psd = reinterpret_cast<int32_t *>(base + L.o_psd);
+  int32_t *sigma = reinterpret_cast<int32_t *>(base + L.o_sigma);
+  int32_t *pos = reinterpret_cast<int32_t *>(base + L.o_pos);
+  void *big = base + L.o_big;
+  void *WY = base + L.o_wy;
+  void *U = base + L.o_u;
+  void *V = base + L.o_v;
+  double *A = reinterpret_cast<double *>(base + L.o_A);
+  double *R = reinterpret_cast<double *>(base + L.o_R);
+  double *Hinv = reinterpret_cast<double *>(base + L.o_Hinv);
+  void *qrws = base + L.o_qr;
+  double *part = reinterpret_cast<double *>(base + L.o_part);
+  double *g = reinterpret_cast<double *>(base + L.o_g);
+  double *ring = reinterpret_cast<double *>(base + L.o_ring);
+  double *b0 = reinterpret_cast<double *>(base + L.o_b0);
+  float *d32 = reinterpret_cast<float *>(base + L.o_d32);
+  double *outb = reinterpret_cast<double *>(base + L.o_out);
+  float *r0 = s.prec == SLSE_PREC_MIXED_BF16 ? reinterpret_cast<float *>(base + L.o_r0) : nullptr;
+  const int d = p->d;
+  const bool mixed = s.prec == SLSE_PREC_MIXED_BF16;
+  const int T = s.T;
+
+  Events E;
+  cudaEvent_t e_start = E.make(), e_draws = E.make(), e_sketch = E.make(), e_qr = E.make(), e_s1 = E.make(),
+              e_end = E.make();
+  if (!e_start || !e_end) return SLSE_ECUDA;
+  const int hist_cap = tr ? (tr->cap < T ? tr->cap : T) : 0;
+  std::vector<cudaEvent_t> e_it;
+  if (tr && tr->ms_hist)
+    for (int t = 0; t < hist_cap; ++t) {
+      cudaEvent_t e = E.make();
+      if (!e) return SLSE_ECUDA;
+      e_it.push_back(e);
+    }
+  auto mark_iter = [&](int t) -> cudaError_t {
+    if (t < (int)e_it.size()) return cudaEventRecord(e_it[t], st);
+    return cudaSuccess;
+  };
+
+  CK(cudaEventRecord(e_start, st));
+  k_init_state<<<1, 32, 0, st>>>(dst, 0);
+  CK(cudaGetLastError());
+  // a1: random draws
+  CK(launch_draws(L.Np, seed, Psd, nullptr, sigma, nullptr, big, st));
+  CK(launch_pos_map(sigma, L.Np, 0, L.n_samp, pos, st));
+  CK(cudaEventRecord(e_draws, st));
+  // a2-a4: SRHT into the sampled rows (unscaled by the sketch size: U = Z[sigma] with Z = H D P X / sqrt(N'))
+  CK(launch_srht(L.sp, s.prec, p->dtype, p->X, p->ldx, p->Y, p->N, d, Psd, pos, big, WY, L.ldu, U, V, L.ldu,
+                 1.0 / std::sqrt((double)L.Np), st));
+  CK(cudaEventRecord(e_sketch, st));
+  // a5: QR of S-hat X = sqrt(N'/r) U[h0 : h0 + r]
+  CK(launch_gather_hessian_rows(s.prec, U, L.ldu, L.h0, s.r, d, std::sqrt((double)L.Np / (double)s.r), A, st));
+  CK(launch_qr(A, s.r, d, d, R, Hinv, qrws, dst, st));
+  CK(cudaEventRecord(e_qr, st));
+  CK(cudaMemsetAsync(ring, 0, (size_t)3 * d * 8, st));
+
+  UpdateArgs ua{};
+  ua.g = g; ua.Hinv = Hinv; ua.beta_ring = ring; ua.beta0 = b0; ua.delta32 = d32;
+  ua.hist = tr ? tr->beta_hist : nullptr; ua.hist_cap = hist_cap; ua.d = d; ua.mu = s.mu; ua.eta = s.eta;
+  ua.T = T;
+
+  // a8 stage 1: a_i M-IHS steps on each nested sketch
+  int t = 0;
+  for (size_t i = 0; i < s.m.size() && t < T; ++i) {
+    const int64_t m = s.m[i];
+    const int nb = grad_blocks(m, L.nblk);
+    for (int j = 0; j < s.a[i] && t < T; ++j) {
+      CK(launch_grad(mixed ? GM_STAGE1_BF16 : GM_STAGE1_F64, mixed ? SLSE_BF16 : SLSE_F64, U, L.ldu, V, m, d,
+                     ring, dst, nullptr, nullptr, nullptr, part, nb, 0, st));
+      CK(launch_reduce(part, nb, d, (double)L.Np / (double)m, g, dst, 0, st));
+      ua.first = (j == 0 && s.momentum_reset) || t == 0;
+      ua.stage2 = 0; ua.thr = 0.0; ua.mixed = 0; ua.check_done = 0;
+      CK(launch_update(ua, dst, st));
+      CK(mark_iter(t));
+      ++t;
+    }
+  }
+  const int t1 = t;
+  CK(cudaEventRecord(e_s1, st));
+  // a8 stage 2: full-data M-IHS steps until the relative step is small or T is reached
+  if (t < T) {
+    k_set_stage2<<<1, 32, 0, st>>>(dst, mixed ? 1 : 0);
+    CK(cudaGetLastError());
+    DevState *mb = t_mailbox.get();
+    if (!mb) return SLSE_ECUDA;
+    const double rho = std::sqrt((double)d / (double)s.r);
+    const double thr = s.tol > 0.0 ? s.tol * (1.0 - rho) / rho : 0.0;
+    const int nb = L.nblk;
+    cudaEvent_t e_flag[2] = {E.make(), E.make()};
+    if (!e_flag[0] || !e_flag[1]) return SLSE_ECUDA;
+    for (int k = 0; t + k < T; ++k) {
+      CK(launch_grad(mixed ? GM_MIXED : GM_F64, p->dtype, p->X, p->ldx, p->Y, p->N, d, ring, dst, d32, r0, b0,
+                     part, nb, 1, st));
+      CK(launch_reduce(part, nb, d, 1.0, g, dst, 1, st));
+      ua.first = (k == 0 && s.momentum_reset) || (t + k) == 0;
+      ua.stage2 = 1; ua.thr = thr; ua.mixed = mixed ? 1 : 0; ua.check_done = 1;
+      CK(launch_update(ua, dst, st));
+      CK(mark_iter(t + k));
+      CK(cudaMemcpyAsync(&mb[k & 1], dst, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+      CK(cudaEventRecord(e_flag[k & 1], st));
+      if (k > 0) {
+        CK(cudaEventSynchronize(e_flag[(k - 1) & 1]));
+        if (((volatile DevState *)&mb[(k - 1) & 1])->done) break;
+      }
+    }
+  }
+  CK(launch_copy_beta(ring, dst, d, outb, st));
+  DevState *mb = t_mailbox.get();
+  if (!mb) return SLSE_ECUDA;
+  CK(cudaMemcpyAsync(&mb[2], dst, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+  CK(cudaEventRecord(e_end, st));
+  CK(cudaMemcpyAsync(beta_out, outb, (size_t)d * 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const DevState fin = mb[2];
+  slse_status status = status_from_bits(fin.status);
+  if (rep) {
+    rep->ms_draws = ms_between(e_start, e_draws);
+    rep->ms_sketch = ms_between(e_draws, e_sketch);
+    rep->ms_qr = ms_between(e_sketch, e_qr);
+    rep->ms_stage1 = ms_between(e_qr, e_s1);
+    rep->ms_total = ms_between(e_start, e_end);
+    rep->ms_stage2 = rep->ms_total - rep->ms_draws - rep->ms_sketch - rep->ms_qr - rep->ms_stage1;
+    rep->iters_stage1 = t1;
+    rep->iters_stage2 = fin.iter - t1;
+    rep->final_rel_step = fin.rel_step;
+    rep->rebases = fin.rebases;
+    const double bx = p->dtype == SLSE_F64 ? 8.0 : 4.0, bu = (double)elem_bytes_u(s.prec);
+    double bytes = 0.0;
+    if (L.sp.single) bytes += (double)p->N * (d + 1) * bx + (double)L.n_samp * (d + 1) * bu;
+    else bytes += (double)p->N * (d + 1) * bx + 2.0 * (double)L.Np * (d + 1) * bu + (double)L.n_samp * (d + 1) * bu;
+    for (size_t i = 0; i < s.m.size(); ++i) bytes += (double)s.a[i] * (double)s.m[i] * (d + 1) * bu;
+    bytes += (double)(fin.iter - t1) * (double)p->N * (d + 1) * bx;
+    rep->bytes_moved = bytes;
+    rep->status = status;
+  }
+  if (tr) {
+    tr->count = fin.iter < hist_cap ? fin.iter : hist_cap;
+    if (tr->ms_hist)
+      for (int k = 0; k < tr->count && k < (int)e_it.size(); ++k) tr->ms_hist[k] = ms_between(e_start, e_it[k]);
+  }
+  return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t slse_workspace_size(const slse_problem *prob, const slse_schedule *sched, int32_t op, int64_t arg) {
+  const int nsm = num_sms() > 0 ? num_sms() : 152;
+  switch (op) {
+    case SLSE_OP_FIT: {
+      if (!valid_problem(prob)) return 0;
+      Sched s;
+      if (!make_sched(prob, sched, s)) return 0;
+      return fit_layout(prob, s, nsm).total;
+    }
+    case SLSE_OP_SKETCH: {
+      if (!valid_problem(prob)) return 0;
+      const int prec = sched ? sched->prec : SLSE_PREC_FP64;
+      return sketch_layout(prob, prec).total;
+    }
+    case SLSE_OP_GRAD:
+      if (!valid_problem(prob)) return 0;
+      return grad_ws(prob, nsm);
+    case SLSE_OP_DRAWS: {
+      if (arg < 1 || padded(arg) > kMaxNp) return 0;
+      return align256(draws_ws_bytes(padded(arg)));
+    }
+    case SLSE_OP_QR: {
+      if (!prob || prob->d < 1 || prob->d > 512 || arg < prob->d) return 0;
+      Layout w;
+      w.take(kStateBytes);
+      w.take((size_t)arg * prob->d * 8);
+      w.take(qr_ws_bytes(arg, prob->d, nsm));
+      return w.total;
+    }
+    default:
+      return 0;
+  }
+}
+
+slse_status slse_fit(const slse_problem *prob, const slse_schedule *sched, uint64_t seed, double *beta_out,
+                     slse_report *report, slse_trace *trace, void *workspace, size_t ws_bytes, slse_stream_t stream) {
+  if (report) std::memset(report, 0, sizeof(*report));
+  if (!valid_problem(prob) || !beta_out) return SLSE_EINVAL;
+  if (trace && (trace->cap < 0 || (trace->cap > 0 && !trace->beta_hist && !trace->ms_hist))) return SLSE_EINVAL;
+  Sched s;
+  if (!make_sched(prob, sched, s)) return SLSE_EINVAL;
+  slse_status st = fit_impl(prob, s, seed, beta_out, report, trace, workspace, ws_bytes, (cudaStream_t)stream);
+  if (report) report->status = st;
+  return st;
+}
+
+slse_status slse_sketch(const slse_problem *prob, int32_t kind, int32_t prec, uint64_t seed, int64_t m, void *SX,
+                        int64_t ldsx, void *SY, void *workspace, size_t ws_bytes, slse_stream_t stream) {
+  if (!valid_problem(prob) || !SX || !SY) return SLSE_EINVAL;
+  if (kind != SLSE_SRHT) return SLSE_EINVAL;
+  if (prec != SLSE_PREC_FP64 && prec != SLSE_PREC_MIXED_BF16) return SLSE_EINVAL;
+  if (prec == SLSE_PREC_MIXED_BF16 && prob->dtype != SLSE_F32) return SLSE_EINVAL;
+  const int64_t Np = padded(prob->N);
+  if (m < 1 || m > Np || ldsx < prob->d) return SLSE_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const SketchLayout L = sketch_layout(prob, prec);
+  Workspace W;
+  slse_status a = acquire(W, workspace, ws_bytes, L.total, st);
+  if (a != SLSE_OK) return a;
+  char *base = static_cast<char *>(W.ptr);
+  int32_t *Psd = reinterpret_cast<int32_t *>(base + L.o_psd);
+  int32_t *sigma = reinterpret_cast<int32_t *>(base + L.o_sigma);
+  int32_t *pos = reinterpret_cast<int32_t *>(base + L.o_pos);
+  CK(launch_draws(Np, seed, Psd, nullptr, sigma, nullptr, base + L.o_big, st));
+  CK(launch_pos_map(sigma, Np, 0, m, pos, st));
+  CK(launch_srht(L.sp, prec, prob->dtype, prob->X, prob->ldx, prob->Y, prob->N, prob->d, Psd, pos, base + L.o_big,
+                 base + L.o_wy, L.ldw, SX, SY, ldsx, 1.0 / std::sqrt((double)m), st));
+  return SLSE_OK;
+}
+
+slse_status slse_grad(const slse_problem *prob, const double *beta, double *g_out, int32_t prec, void *workspace,
+                      size_t ws_bytes, slse_stream_t stream) {
+  if (!valid_problem(prob) || !beta || !g_out) return SLSE_EINVAL;
+  if (prec != SLSE_PREC_FP64 && prec != SLSE_PREC_MIXED_BF16) return SLSE_EINVAL;
+  if (prec == SLSE_PREC_MIXED_BF16 && prob->dtype != SLSE_F32) return SLSE_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nsm = num_sms();
+  if (nsm <= 0) return SLSE_ECUDA;
+  Workspace W;
+  slse_status a = acquire(W, workspace, ws_bytes, grad_ws(prob, nsm), st);
+  if (a != SLSE_OK) return a;
+  char *base = static_cast<char *>(W.ptr);
+  DevState *dst = reinterpret_cast<DevState *>(base);
+  double *part = reinterpret_cast<double *>(base + kStateBytes);
+  const int nb = grad_blocks(prob->N, 2 * nsm);
+  const bool mixed = prec == SLSE_PREC_MIXED_BF16;
+  k_init_state<<<1, 32, 0, st>>>(dst, mixed ? 1 : 0);
+  CK(cudaGetLastError());
+  CK(launch_grad(mixed ? GM_MIXED : GM_F64, prob->dtype, prob->X, prob->ldx, prob->Y, prob->N, prob->d, beta, dst,
+                 nullptr, nullptr, nullptr, part, nb, 0, st));
+  CK(launch_reduce(part, nb, prob->d, 1.0, g_out, dst, 0, st));
+  return SLSE_OK;
+}
+
+slse_status slse_draws(int64_t N, uint64_t seed, int32_t *P, int32_t *sigma, int8_t *D, void *workspace,
+                       size_t ws_bytes, slse_stream_t stream) {
+  if (N < 1 || padded(N) > kMaxNp || !P || !sigma) return SLSE_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t Np = padded(N);
+  Workspace W;
+  slse_status a = acquire(W, workspace, ws_bytes, align256(draws_ws_bytes(Np)), st);
+  if (a != SLSE_OK) return a;
+  CK(launch_draws(Np, seed, nullptr, P, sigma, D, W.ptr, st));
+  return SLSE_OK;
+}
+
+slse_status slse_qr(const double *A, int64_t r, int32_t d, int64_t lda, double *R, double *Hinv, void *workspace,
+                    size_t ws_bytes, slse_stream_t stream) {
+  if (!A || !R || d < 1 || d > 512 || r < d || lda < d) return SLSE_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nsm = num_sms();
+  if (nsm <= 0) return SLSE_ECUDA;
+  Layout w;
+  const size_t o_state = w.take(kStateBytes);
+  const size_t o_a = w.take((size_t)r * d * 8);
+  const size_t o_qr = w.take(qr_ws_bytes(r, d, nsm));
+  Workspace W;
+  slse_status a = acquire(W, workspace, ws_bytes, w.total, st);
+  if (a != SLSE_OK) return a;
+  char *base = static_cast<char *>(W.ptr);
+  DevState *dst = reinterpret_cast<DevState *>(base + o_state);
+  double *Ac = reinterpret_cast<double *>(base + o_a);
+  k_init_state<<<1, 32, 0, st>>>(dst, 0);
+  CK(cudaGetLastError());
+  CK(cudaMemcpy2DAsync(Ac, (size_t)d * 8, A, (size_t)lda * 8, (size_t)d * 8, (size_t)r, cudaMemcpyDeviceToDevice, st));
+  CK(launch_qr(Ac, r, d, d, R, Hinv, base + o_qr, dst, st));
+  return SLSE_OK;
+}
+
+int32_t slse_default_schedule(int64_t N, int32_t d, slse_schedule *out, int64_t *m_buf, int32_t *a_buf, int32_t cap) {
+  if (!out || N < 1 || d < 1) return -1;
+  const int64_t Np = padded(N);
+  int32_t K = 0;
+  for (int64_t m = 8 * (int64_t)d; m <= Np / 2; m *= 2) {
+    if (K < cap && m_buf && a_buf) {
+      m_buf[K] = m;
+      a_buf[K] = 2;
+    }
+    ++K;
+  }
+  std::memset(out, 0, sizeof(*out));
+  out->K = K < cap ? K : cap;
+  out->m = m_buf;
+  out->a = a_buf;
+  out->r = 6 * (int64_t)d;
+  out->eta = (double)d / (double)out->r;
+  out->mu = (1.0 - out->eta) * (1.0 - out->eta);
+  out->T = 100;
+  out->tol = 0.0;
+  out->kind = SLSE_SRHT;
+  out->prec = SLSE_PREC_FP64;
+  out->momentum_reset = 1;
+  return K;
+}
+
+double slse_ai_bound(double omega, int64_t m_prev, int64_t m_i, int32_t d) {
+  if (!(omega > 0.0) || m_prev <= d || m_i <= d) return NAN;
+  const double r = std::sqrt((double)(m_i - d) / (double)(m_prev - d));
+  return std::log(((1.0 + omega) * r + 1.0) / omega) / std::log(3.0);
+}
+
+const char *slse_status_string(int32_t s) {
+  switch (s) {
+    case SLSE_OK: return "ok";
+    case SLSE_EINVAL: return "invalid argument";
+    case SLSE_ENOMEM: return "workspace too small or allocation failed";
+    case SLSE_ECUDA: return "CUDA runtime error";
+    case SLSE_ENOTCONV: return "iteration cap reached before the tolerance";
+    case SLSE_ENUMERIC: return "non-finite iterate or zero pivot";
+    case SLSE_ETIMEOUT: return "bounded device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+int32_t slse_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,493 @@
+// Fused one-pass residual-gradient kernels and the M-IHS update (paper Sec. 3,
+// Eqs. 3.1 and 3.2; cost model "(4d+1) rows + 2d^2 + 5d" FLOPs per iteration).
+//
+// g = sum_i x_i^T (y_i - x_i beta) over the rows of X (2nd stage) or over the first
+// m_i rows of the sampled sketch U (1st stage, scaled by N'/m_i).  One warp owns one
+// row at a time: each lane holds a slice of the row (vector loads, 16 bytes per
+// lane), forms its part of x_i beta, the warp reduces it with shuffles, and every
+// lane then accumulates x_i r_i into its own slice of g.  Each row of X is read
+// exactly once per pass.  Per-CTA partials are reduced in a fixed order (no atomics)
+// so the result is deterministic.
+//
+// Mixed-precision 2nd stage (X stored FP32): the residual is formed against a base
+// point beta_0 in FP64.  A "rebase" pass computes r0_i = y_i - x_i beta_0 with
+// error-free transformations (TwoProd via FMA, TwoSum; beta_0 split into two FP32
+// words) and stores r0 in FP32; later passes compute r_i = r0_i - x_i (beta - beta_0)
+// in FP32, whose rounding error scales with ||beta - beta_0|| and vanishes as the
+// iteration converges.  x_i r_i is accumulated in FP32 and folded every 16 rows into
+// a two-word (TwoSum) accumulator.  The update kernel re-bases when
+// ||beta - beta_0|| > 2^-10 ||beta||.
+#include "slse_internal.cuh"
+
+namespace slse {
+namespace {
+
+constexpr int kGradThreads = 256;
+constexpr int kWarps = kGradThreads / 32;
+constexpr int kFlushRows = 16;
+
+struct GradArgs {
+  const void *X;
+  int64_t ldx;
+  const void *Y;
+  int64_t nrows;
+  int d;
+  const double *beta_ring;
+  DevState *st;
+  const float *delta32;
+  float *r0;
+  double *beta0;
+  double *partials;
+  int check_done;
+};
+
+template <class Tx, int VW> struct Vec;
+template <> struct Vec<float, 4> {
+  static __device__ __forceinline__ void load(const float *p, float (&o)[4], bool stream) {
+    const float4 t = stream ? __ldcs(reinterpret_cast<const float4 *>(p)) : __ldg(reinterpret_cast<const float4 *>(p));
+    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+  }
+};
+template <> struct Vec<float, 1> {
+  static __device__ __forceinline__ void load(const float *p, float (&o)[1], bool stream) {
+    o[0] = stream ? __ldcs(p) : __ldg(p);
+  }
+};
+template <> struct Vec<double, 2> {
+  static __device__ __forceinline__ void load(const double *p, double (&o)[2], bool stream) {
+    const double2 t = stream ? __ldcs(reinterpret_cast<const double2 *>(p)) : __ldg(reinterpret_cast<const double2 *>(p));
+    o[0] = t.x; o[1] = t.y;
+  }
+};
+template <> struct Vec<double, 1> {
+  static __device__ __forceinline__ void load(const double *p, double (&o)[1], bool stream) {
+    o[0] = stream ? __ldcs(p) : __ldg(p);
+  }
+};
+template <> struct Vec<float, 2> {  // FP32 data widened to FP64 arithmetic uses float pairs
+  static __device__ __forceinline__ void load(const float *p, float (&o)[2], bool stream) {
+    const float2 t = stream ? __ldcs(reinterpret_cast<const float2 *>(p)) : __ldg(reinterpret_cast<const float2 *>(p));
+    o[0] = t.x; o[1] = t.y;
+  }
+};
+
+__device__ __forceinline__ void load_bf16x8(const __nv_bfloat16 *p, float (&o)[8]) {
+  const uint4 t = __ldg(reinterpret_cast<const uint4 *>(p));
+  const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    o[2 * k] = __uint_as_float(w[k] << 16);
+    o[2 * k + 1] = __uint_as_float(w[k] & 0xFFFF0000u);
+  }
+}
+
+template <class T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// Write the CTA partial: sum of the kWarps per-warp slices in a fixed order.
+__device__ __forceinline__ void cta_partial(double (*sm)[512], int d, double *out) {
+  __syncthreads();
+  for (int c = threadIdx.x; c < d; c += blockDim.x) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) s += sm[w][c];
+    out[c] = s;
+  }
+}
+
+// ---------------------------------------------------------------- FP64 arithmetic
+// Tx = double (X F64 or U F64) or float (X F32, widened exactly).  VW = elements per lane load.
+template <class Tx, int VW, int VMAX>
+__global__ void __launch_bounds__(kGradThreads) k_grad_f64(const GradArgs a) {
+  __shared__ double sm[kWarps][512];
+  if (a.check_done && a.st->done) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * kWarps + warp, nw = (int64_t)gridDim.x * kWarps;
+  const int d = a.d;
+  const double *beta = a.beta_ring + (size_t)(a.st->iter % 3) * d;
+  const Tx *X = static_cast<const Tx *>(a.X);
+  const Tx *Y = static_cast<const Tx *>(a.Y);
+  double b[VMAX][VW], g[VMAX][VW];
+#pragma unroll
+  for (int v = 0; v < VMAX; ++v)
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      const int col = (v * 32 + lane) * VW + e;
+      b[v][e] = col < d ? beta[col] : 0.0;
+      g[v][e] = 0.0;
+    }
+  for (int64_t i = gw; i < a.nrows; i += nw) {
+    const Tx *row = X + i * a.ldx;
+    double x[VMAX][VW];
+#pragma unroll
+    for (int v = 0; v < VMAX; ++v) {
+      const int col0 = (v * 32 + lane) * VW;
+      Tx t[VW];
+      if (col0 < d) Vec<Tx, VW>::load(row + col0, t, true);
+      else {
+#pragma unroll
+        for (int e = 0; e < VW; ++e) t[e] = Tx(0);
+      }
+#pragma unroll
+      for (int e = 0; e < VW; ++e) x[v][e] = (col0 + e < d) ? (double)t[e] : 0.0;
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int v = 0; v < VMAX; ++v)
+#pragma unroll
+      for (int e = 0; e < VW; ++e) s = fma(x[v][e], b[v][e], s);
+    s = warp_sum(s);
+    const double r = (double)Y[i] - s;
+#pragma unroll
+    for (int v = 0; v < VMAX; ++v)
+#pragma unroll
+      for (int e = 0; e < VW; ++e) g[v][e] = fma(x[v][e], r, g[v][e]);
+  }
+#pragma unroll
+  for (int v = 0; v < VMAX; ++v)
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      const int col = (v * 32 + lane) * VW + e;
+      if (col < d) sm[warp][col] = g[v][e];
+    }
+  cta_partial(sm, d, a.partials + (size_t)blockIdx.x * d);
+}
+
+// ---------------------------------------------------------------- 1st stage on BF16 sketch
+template <int VW, int VMAX>
+__global__ void __launch_bounds__(kGradThreads) k_grad_bf16(const GradArgs a) {
+  __shared__ double sm[kWarps][512];
+  if (a.check_done && a.st->done) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * kWarps + warp, nw = (int64_t)gridDim.x * kWarps;
+  const int d = a.d;
+  const double *beta = a.beta_ring + (size_t)(a.st->iter % 3) * d;
+  const __nv_bfloat16 *U = static_cast<const __nv_bfloat16 *>(a.X);
+  const __nv_bfloat16 *V = static_cast<const __nv_bfloat16 *>(a.Y);
+  float b[VMAX][VW], g[VMAX][VW];
+#pragma unroll
+  for (int v = 0; v < VMAX; ++v)
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      const int col = (v * 32 + lane) * VW + e;
+      b[v][e] = col < d ? (float)beta[col] : 0.f;
+      g[v][e] = 0.f;
+    }
+  for (int64_t i = gw; i < a.nrows; i += nw) {
+    const __nv_bfloat16 *row = U + i * a.ldx;
+    float x[VMAX][VW];
+#pragma unroll
+    for (int v = 0; v < VMAX; ++v) {
+      const int col0 = (v * 32 + lane) * VW;
+      float t[VW];
+      if constexpr (VW == 8) {
+        if (col0 < d) load_bf16x8(row + col0, t);
+        else {
+#pragma unroll
+          for (int e = 0; e < VW; ++e) t[e] = 0.f;
+        }
+      } else {
+        t[0] = col0 < d ? __bfloat162float(row[col0]) : 0.f;
+      }
+#pragma unroll
+      for (int e = 0; e < VW; ++e) x[v][e] = (col0 + e < d) ? t[e] : 0.f;
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int v = 0; v < VMAX; ++v)
+#pragma unroll
+      for (int e = 0; e < VW; ++e) s = fmaf(x[v][e], b[v][e], s);
+    s = warp_sum(s);
+    const float r = __bfloat162float(V[i]) - s;
+#pragma unroll
+    for (int v = 0; v < VMAX; ++v)
+#pragma unroll
+      for (int e = 0; e < VW; ++e) g[v][e] = fmaf(x[v][e], r, g[v][e]);
+  }
+#pragma unroll
+  for (int v = 0; v < VMAX; ++v)
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      const int col = (v * 32 + lane) * VW + e;
+      if (col < d) sm[warp][col] = (double)g[v][e];
+    }
+  cta_partial(sm, d, a.partials + (size_t)blockIdx.x * d);
+}
+
+// ---------------------------------------------------------------- mixed 2nd stage (X F32)
+template <int VW, int VMAX>
+__global__ void __launch_bounds__(kGradThreads) k_grad_mixed(const GradArgs a) {
+  __shared__ double sm[kWarps][512];
+  if (a.check_done && a.st->done) return;
+  const int rebase = a.st->rebase;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * kWarps + warp, nw = (int64_t)gridDim.x * kWarps;
+  const int d = a.d;
+  const double *beta = a.beta_ring + (size_t)(a.st->iter % 3) * d;
+  const float *X = static_cast<const float *>(a.X);
+  const float *Y = static_cast<const float *>(a.Y);
+  float bh[VMAX][VW], bl[VMAX][VW];
+  float gacc[VMAX][VW], ghi[VMAX][VW], glo[VMAX][VW];
+#pragma unroll
+  for (int v = 0; v < VMAX; ++v)
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      const int col = (v * 32 + lane) * VW + e;
+      if (rebase) {
+        const double bd = col < d ? beta[col] : 0.0;
+        bh[v][e] = (float)bd;
+        bl[v][e] = (float)(bd - (double)bh[v][e]);
+      } else {
+        bh[v][e] = col < d ? a.delta32[col] : 0.f;
+        bl[v][e] = 0.f;
+      }
+      gacc[v][e] = 0.f; ghi[v][e] = 0.f; glo[v][e] = 0.f;
+    }
+  int nacc = 0;
+  for (int64_t i = gw; i < a.nrows; i += nw) {
+    const float *row = X + i * a.ldx;
+    float x[VMAX][VW];
+#pragma unroll
+    for (int v = 0; v < VMAX; ++v) {
+      const int col0 = (v * 32 + lane) * VW;
+      float t[VW];
+      if (col0 < d) Vec<float, VW>::load(row + col0, t, true);
+      else {
+#pragma unroll
+        for (int e = 0; e < VW; ++e) t[e] = 0.f;
+      }
+#pragma unroll
+      for (int e = 0; e < VW; ++e) x[v][e] = (col0 + e < d) ? t[e] : 0.f;
+    }
+    float r;
+    if (rebase) {
+      // Dot2 (Ogita, Rump, Oishi 2005): s + c = x . (bh + bl) with error-free products/sums
+      float s = 0.f, c = 0.f;
+#pragma unroll
+      for (int v = 0; v < VMAX; ++v)
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+          float p, pe, se;
+          two_prod(x[v][e], bh[v][e], p, pe);
+          two_sum(s, p, s, se);
+          c = fmaf(x[v][e], bl[v][e], c + (pe + se));
+        }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, s, off);
+        const float c2 = __shfl_xor_sync(0xffffffffu, c, off);
+        float e;
+        two_sum(s, s2, s, e);
+        c = (c + c2) + e;
+      }
+      float rh, re;
+      two_sum(Y[i], -s, rh, re);
+      r = rh + (re - c);
+      if (a.r0 && lane == 0) a.r0[i] = r;
+    } else {
+      float s = 0.f;
+#pragma unroll
+      for (int v = 0; v < VMAX; ++v)
+#pragma unroll
+        for (int e = 0; e < VW; ++e) s = fmaf(x[v][e], bh[v][e], s);
+      s = warp_sum(s);
+      r = __ldg(a.r0 + i) - s;
+    }
+#pragma unroll
+    for (int v = 0; v < VMAX; ++v)
+#pragma unroll
+      for (int e = 0; e < VW; ++e) gacc[v][e] = fmaf(x[v][e], r, gacc[v][e]);
+    if (++nacc == kFlushRows) {
+      nacc = 0;
+#pragma unroll
+      for (int v = 0; v < VMAX; ++v)
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+          float s, err;
+          two_sum(ghi[v][e], gacc[v][e], s, err);
+          ghi[v][e] = s;
+          glo[v][e] += err;
+          gacc[v][e] = 0.f;
+        }
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < VMAX; ++v)
+#pragma unroll
+    for (int e = 0; e < VW; ++e) {
+      const int col = (v * 32 + lane) * VW + e;
+      if (col < d) sm[warp][col] = ((double)ghi[v][e] + (double)gacc[v][e]) + (double)glo[v][e];
+    }
+  if (rebase && a.beta0 && blockIdx.x == 0) {
+    for (int c = threadIdx.x; c < d; c += blockDim.x) a.beta0[c] = beta[c];
+    if (threadIdx.x == 0) a.st->rebases += 1;
+  }
+  cta_partial(sm, d, a.partials + (size_t)blockIdx.x * d);
+}
+
+// ---------------------------------------------------------------- reduction and update
+__global__ void k_reduce(const double *partials, int nblk, int d, double scale, double *g, const DevState *st,
+                         int check_done) {
+  __shared__ double sm[8][33];
+  if (check_done && st->done) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + lane;
+  double s = 0.0;
+  if (c < d)
+    for (int b = warp; b < nblk; b += 8) s += partials[(size_t)b * d + c];
+  sm[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0 && c < d) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += sm[w][lane];
+    g[c] = scale * t;
+  }
+}
+
+struct UpdArgs {
+  UpdateArgs u;
+  double *part;  // 3 doubles per CTA
+};
+
+// beta+ = beta + mu H^{-1} g + eta (beta - beta_prev); one warp per row of H^{-1}.
+__global__ void __launch_bounds__(256) k_update(const UpdArgs A, DevState *st) {
+  const UpdateArgs &a = A.u;
+  __shared__ double s_red[8][3];
+  __shared__ int s_last;
+  if (a.check_done && st->done) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int d = a.d;
+  const int t = st->iter;
+  const double *b = a.beta_ring + (size_t)(t % 3) * d;
+  const double *bp = a.beta_ring + (size_t)((t + 2) % 3) * d;
+  double *bn = a.beta_ring + (size_t)((t + 1) % 3) * d;
+  const int i = blockIdx.x * 8 + warp;
+  double ds = 0.0, nn = 0.0, dd = 0.0;
+  if (i < d) {
+    const double *Hrow = a.Hinv + (size_t)i * d;
+    double h = 0.0;
+    for (int k = lane; k < d; k += 32) h = fma(Hrow[k], a.g[k], h);
+    h = warp_sum(h);
+    if (lane == 0) {
+      const double mom = a.first ? 0.0 : a.eta * (b[i] - bp[i]);
+      const double v = b[i] + a.mu * h + mom;
+      bn[i] = v;
+      ds = (v - b[i]) * (v - b[i]);
+      nn = v * v;
+      if (a.mixed) {
+        const double del = v - a.beta0[i];
+        a.delta32[i] = (float)del;
+        dd = del * del;
+      }
+      if (a.hist && t < a.hist_cap) a.hist[(size_t)t * d + i] = v;
+    }
+  }
+  if (lane == 0) { s_red[warp][0] = ds; s_red[warp][1] = nn; s_red[warp][2] = dd; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x0 = 0, x1 = 0, x2 = 0;
+    for (int w = 0; w < 8; ++w) { x0 += s_red[w][0]; x1 += s_red[w][1]; x2 += s_red[w][2]; }
+    A.part[3 * blockIdx.x + 0] = x0;
+    A.part[3 * blockIdx.x + 1] = x1;
+    A.part[3 * blockIdx.x + 2] = x2;
+    __threadfence();
+    const unsigned prev = atomicAdd(&st->upd_count, 1u);
+    s_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last || threadIdx.x != 0) return;
+  __threadfence();
+  double x0 = 0, x1 = 0, x2 = 0;
+  for (unsigned c = 0; c < gridDim.x; ++c) {
+    x0 += __ldcg(A.part + 3 * c + 0);
+    x1 += __ldcg(A.part + 3 * c + 1);
+    x2 += __ldcg(A.part + 3 * c + 2);
+  }
+  st->upd_count = 0;
+  const double rel = sqrt(x0) / (sqrt(x1) > 0.0 ? sqrt(x1) : 1.0);
+  st->rel_step = rel;
+  const int tn = t + 1;
+  st->iter = tn;
+  if (!isfinite(x0) || !isfinite(x1)) {
+    st->status |= ST_NUMERIC;
+    st->done = 1;
+  }
+  if (a.stage2) {
+    if (a.thr > 0.0 && rel <= a.thr) st->done = 1;
+    else if (tn >= a.T) {
+      st->done = 1;
+      if (a.thr > 0.0) st->status |= ST_NOTCONV;
+    }
+    if (a.mixed) st->rebase = (x2 > 0x1p-20 * x1) ? 1 : 0;
+  }
+}
+
+__global__ void k_copy_beta(const double *ring, const DevState *st, int d, double *out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < d) out[c] = ring[(size_t)(st->iter % 3) * d + c];
+}
+
+template <class K>
+cudaError_t launch1(K kern, int nblk, const GradArgs &a, cudaStream_t s) {
+  kern<<<nblk, kGradThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+inline bool aligned(const void *p, int64_t ld, int64_t elem_bytes, int vw) {
+  return (reinterpret_cast<uintptr_t>(p) % (size_t)(vw * elem_bytes) == 0) && (ld % vw == 0);
+}
+
+}  // namespace
+
+int grad_grid(int nsm) { return 2 * nsm; }
+
+cudaError_t launch_grad(int mode, int xdtype, const void *X, int64_t ldx, const void *Y, int64_t nrows, int d,
+                        const double *beta_ring, DevState *st, const float *delta32, float *r0, double *beta0,
+                        double *partials, int nblk, int check_done, cudaStream_t s) {
+  GradArgs a{X, ldx, Y, nrows, d, beta_ring, st, delta32, r0, beta0, partials, check_done};
+  if (d > 512 || d < 1) return cudaErrorInvalidValue;
+  switch (mode) {
+    case GM_F64:
+    case GM_STAGE1_F64:
+      if (xdtype == SLSE_F64) {
+        if (d % 2 == 0 && aligned(X, ldx, 8, 2)) return launch1(k_grad_f64<double, 2, 8>, nblk, a, s);
+        return launch1(k_grad_f64<double, 1, 16>, nblk, a, s);
+      } else {
+        if (d % 2 == 0 && aligned(X, ldx, 4, 2)) return launch1(k_grad_f64<float, 2, 8>, nblk, a, s);
+        return launch1(k_grad_f64<float, 1, 16>, nblk, a, s);
+      }
+    case GM_STAGE1_BF16:
+      if (ldx % 8 == 0 && aligned(X, ldx, 2, 8)) return launch1(k_grad_bf16<8, 2>, nblk, a, s);
+      return launch1(k_grad_bf16<1, 16>, nblk, a, s);
+    case GM_MIXED:
+      if (xdtype != SLSE_F32) return cudaErrorInvalidValue;
+      if (d % 4 == 0 && aligned(X, ldx, 4, 4)) return launch1(k_grad_mixed<4, 4>, nblk, a, s);
+      return launch1(k_grad_mixed<1, 16>, nblk, a, s);
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_reduce(const double *partials, int nblk, int d, double scale, double *g, DevState *st,
+                          int check_done, cudaStream_t s) {
+  k_reduce<<<(d + 31) / 32, 256, 0, s>>>(partials, nblk, d, scale, g, st, check_done);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update(const UpdateArgs &a, DevState *st, cudaStream_t s) {
+  // per-CTA partial sums live right after the DevState's own cache line block
+  UpdArgs A{a, reinterpret_cast<double *>(st + 1)};
+  k_update<<<(a.d + 7) / 8, 256, 0, s>>>(A, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_beta(const double *beta_ring, DevState *st, int d, double *out, cudaStream_t s) {
+  k_copy_beta<<<(d + 255) / 256, 256, 0, s>>>(beta_ring, st, d, out);
+  return cudaGetLastError();
+}
+
+}  // namespace slse

@@ -1,0 +1,225 @@
+// FP64 Householder QR of the Hessian sketch S-hat X (r x d), the explicit
+// R^{-1}, and H-hat^{-1} = R^{-1} R^{-T} (paper, Appendix "implementation details":
+// H-hat^{-1} v is applied through the QR of S-hat X).
+//
+// FP64 runs at ~1/57 of the FP32 rate on this part, so the QR is spread over every
+// SM: one cooperative persistent kernel, each CTA owning a contiguous block of rows.
+// Column j costs one grid-wide reduction of the d-j dot products v^T A[:, j..d)
+// (which also yields ||A[j:, j]||^2), done as per-CTA partials + a sliced
+// second-level sum, and a rank-1 update of each CTA's own rows.  Grid barriers are
+// bounded spins (ST_TIMEOUT after ~1 s, never a hang).
+#include "slse_internal.cuh"
+
+namespace slse {
+namespace {
+
+constexpr int kQrThreads = 256;
+
+struct QrArgs {
+  double *A;
+  int64_t r, lda;
+  int d;
+  double *R;
+  double *red;   // 2 x G x d
+  double *fin;   // 2 x d
+  double *piv;   // 2 x d
+  DevState *st;
+};
+
+__global__ void __launch_bounds__(kQrThreads) k_qr(const QrArgs a) {
+  const int G = gridDim.x, b = blockIdx.x;
+  const int d = a.d;
+  const int64_t r = a.r;
+  const int64_t rb0 = (r * b) / G, rb1 = (r * (b + 1)) / G;
+  double *A = a.A;
+  for (int j = 0; j < d; ++j) {
+    const int nc = d - j;
+    const int buf = j & 1;
+    double *red = a.red + (size_t)buf * G * d;
+    double *fin = a.fin + (size_t)buf * d;
+    double *piv = a.piv + (size_t)buf * d;
+    const int64_t lo = rb0 > j ? rb0 : j;
+    // phase 1: partial dot products of column j with columns j..d-1 over own rows
+    for (int c = threadIdx.x; c < nc; c += kQrThreads) {
+      double s = 0.0;
+      for (int64_t i = lo; i < rb1; ++i) s = fma(A[i * a.lda + j], A[i * a.lda + j + c], s);
+      red[(size_t)b * d + c] = s;
+      if (j >= rb0 && j < rb1) piv[c] = A[(int64_t)j * a.lda + j + c];
+    }
+    if (!grid_barrier(a.st, G)) return;
+    // phase 2: CTA b sums a slice of the columns over all CTAs (fixed order)
+    const int c0 = (int)(((int64_t)nc * b) / G), c1 = (int)(((int64_t)nc * (b + 1)) / G);
+    for (int c = c0 + threadIdx.x; c < c1; c += kQrThreads) {
+      double s = 0.0;
+      for (int q = 0; q < G; ++q) s += __ldcg(red + (size_t)q * d + c);
+      fin[c] = s;
+    }
+    if (!grid_barrier(a.st, G)) return;
+    // phase 3: Householder reflector from column j, applied to own rows
+    const double nrm2 = __ldcg(fin);
+    const double ajj = __ldcg(piv);
+    if (nrm2 > 0.0) {
+      const double nrm = sqrt(nrm2);
+      const double alpha = ajj >= 0.0 ? -nrm : nrm;
+      const double vj = ajj - alpha;
+      const double tau = 1.0 / (nrm * (nrm + fabs(ajj)));  // 2 / v^T v
+      for (int c = 1 + threadIdx.x; c < nc; c += kQrThreads) {
+        const double w = __ldcg(fin + c) - alpha * __ldcg(piv + c);  // v^T A[:, j+c]
+        const double tw = tau * w;
+        for (int64_t i = lo; i < rb1; ++i) {
+          const double vi = (i == j) ? vj : A[i * a.lda + j];
+          A[i * a.lda + j + c] -= vi * tw;
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0 && j >= rb0 && j < rb1) A[(int64_t)j * a.lda + j] = alpha;
+    } else if (threadIdx.x == 0 && b == 0) {
+      atomicOr(&a.st->status, ST_NUMERIC);
+    }
+    __syncthreads();
+  }
+  if (!grid_barrier(a.st, G)) return;
+  // R = upper triangle of A[0:d, 0:d] with rows scaled to a non-negative diagonal
+  for (int64_t e = (int64_t)b * kQrThreads + threadIdx.x; e < (int64_t)d * d; e += (int64_t)G * kQrThreads) {
+    const int i = (int)(e / d), k = (int)(e % d);
+    const double diag = __ldcg(A + (int64_t)i * a.lda + i);
+    const double sgn = diag < 0.0 ? -1.0 : 1.0;
+    a.R[e] = k >= i ? sgn * __ldcg(A + (int64_t)i * a.lda + k) : 0.0;
+  }
+}
+
+// Column k of R^{-1}: back substitution R x = e_k, one warp per column.
+__global__ void __launch_bounds__(256) k_tri_inv(const double *R, int d, double *Rinv, DevState *st) {
+  extern __shared__ double sx[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int k = blockIdx.x * 8 + warp;
+  if (k >= d) return;
+  double *x = sx + (size_t)warp * d;
+  for (int i = k; i >= 0; --i) {
+    double s = 0.0;
+    for (int l = i + 1 + lane; l <= k; l += 32) s = fma(R[(size_t)i * d + l], x[l], s);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    const double rii = R[(size_t)i * d + i];
+    const double xi = ((i == k ? 1.0 : 0.0) - s) / rii;
+    if (lane == 0) x[i] = xi;
+    __syncwarp();
+    if (rii == 0.0 && lane == 0) atomicOr(&st->status, ST_NUMERIC);
+  }
+  for (int i = lane; i < d; i += 32) Rinv[(size_t)i * d + k] = i <= k ? x[i] : 0.0;
+}
+
+// Hinv[i][k] = sum_{l >= max(i,k)} Rinv[i][l] Rinv[k][l], 32 x 32 output tiles.
+__global__ void __launch_bounds__(256) k_form_hinv(const double *Rinv, int d, double *Hinv) {
+  __shared__ double sa[32][33], sb[32][33];
+  const int ti = blockIdx.y, tk = blockIdx.x;
+  if (tk < ti) return;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 rows of threads
+  double acc[4] = {0, 0, 0, 0};
+  const int lstart = tk * 32;  // Rinv[k][l] = 0 for l < k, and k >= tk*32 >= i
+  for (int l0 = lstart; l0 < d; l0 += 32) {
+    for (int rr = ty; rr < 32; rr += 8) {
+      const int gi = ti * 32 + rr, gk = tk * 32 + rr, gl = l0 + tx;
+      sa[rr][tx] = (gi < d && gl < d) ? Rinv[(size_t)gi * d + gl] : 0.0;
+      sb[rr][tx] = (gk < d && gl < d) ? Rinv[(size_t)gk * d + gl] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int rr = ty + 8 * q;
+      double s = acc[q];
+      for (int l = 0; l < 32; ++l) s = fma(sa[rr][l], sb[tx][l], s);
+      acc[q] = s;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int gi = ti * 32 + ty + 8 * q, gk = tk * 32 + tx;
+    if (gi < d && gk < d) {
+      Hinv[(size_t)gi * d + gk] = acc[q];
+      Hinv[(size_t)gk * d + gi] = acc[q];
+    }
+  }
+}
+
+template <class T> __device__ __forceinline__ double to_d(T v) { return (double)v; }
+template <> __device__ __forceinline__ double to_d<__nv_bfloat16>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+
+template <class T>
+__global__ void k_gather(const T *U, int64_t ldu, int64_t row0, int64_t r, int d, double scale, double *A) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= r * d) return;
+  const int64_t i = e / d;
+  const int c = (int)(e % d);
+  A[e] = scale * to_d(U[(row0 + i) * ldu + c]);
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int qr_grid(int64_t r, int nsm) {
+  int64_t g = (r + 7) / 8;  // at least ~8 rows per CTA
+  if (g > nsm) g = nsm;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+size_t qr_ws_bytes(int64_t r, int d, int nsm) {
+  const int G = qr_grid(r, nsm);
+  return align256(2 * (size_t)G * d * 8) + 2 * align256(2 * (size_t)d * 8) + align256((size_t)d * d * 8);
+}
+
+cudaError_t launch_gather_hessian_rows(int prec, const void *U, int64_t ldu, int64_t row0, int64_t r, int d,
+                                       double scale, double *A, cudaStream_t s) {
+  const int64_t n = r * d;
+  const unsigned grid = (unsigned)((n + 255) / 256);
+  if (prec == SLSE_PREC_FP64)
+    k_gather<double><<<grid, 256, 0, s>>>(static_cast<const double *>(U), ldu, row0, r, d, scale, A);
+  else
+    k_gather<__nv_bfloat16><<<grid, 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(U), ldu, row0, r, d, scale, A);
+  return cudaGetLastError();
+}
+
+// A is overwritten (it must be a scratch copy).  ws: qr_ws_bytes(r, d).
+cudaError_t launch_qr(double *A, int64_t r, int d, int64_t lda, double *R, double *Hinv, void *ws, DevState *st,
+                      cudaStream_t s) {
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  int G = qr_grid(r, nsm);
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qr, kQrThreads, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  char *p = static_cast<char *>(ws);
+  size_t off = 0;
+  QrArgs a;
+  a.A = A;
+  a.r = r;
+  a.lda = lda;
+  a.d = d;
+  a.R = R;
+  a.red = reinterpret_cast<double *>(p + off); off += align256(2 * (size_t)G * d * 8);
+  a.fin = reinterpret_cast<double *>(p + off); off += align256(2 * (size_t)d * 8);
+  a.piv = reinterpret_cast<double *>(p + off); off += align256(2 * (size_t)d * 8);
+  double *Rinv = reinterpret_cast<double *>(p + off); off += align256((size_t)d * d * 8);
+  a.st = st;
+  void *args[] = {&a};
+  e = cudaLaunchCooperativeKernel((const void *)k_qr, dim3(G), dim3(kQrThreads), args, 0, s);
+  if (e != cudaSuccess) return e;
+  if (Hinv) {
+    const size_t smem = (size_t)8 * d * sizeof(double);
+    e = cudaFuncSetAttribute(k_tri_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_tri_inv<<<(d + 7) / 8, 256, smem, s>>>(R, d, Rinv, st);
+    const int nt = (d + 31) / 32;
+    k_form_hinv<<<dim3(nt, nt), 256, 0, s>>>(Rinv, d, Hinv);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace slse

@@ -1,0 +1,159 @@
+// Internal declarations shared by the CUDA translation units of the SLSE-FRS library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/slse.h"
+
+namespace slse {
+
+// ----------------------------------------------------------------------------------
+// Device status word (bit flags), written by kernels, read by the host at the end.
+enum : unsigned {
+  ST_TIMEOUT = 1u,   // a bounded spin gave up
+  ST_NUMERIC = 2u,   // NaN/Inf seen, or zero pivot
+  ST_NOTCONV = 4u,   // hit T with tol > 0
+};
+
+// Iteration state living in device memory (one per fit).
+struct DevState {
+  int iter;            // number of M-IHS iterations done
+  int done;            // stage-2 stop flag (tol met or T reached)
+  int rebase;          // mixed path: next 2nd-stage pass recomputes the base residual
+  int rebases;         // count of rebase passes
+  unsigned status;     // ST_* bits
+  unsigned upd_count;  // last-block counter of the update kernel
+  unsigned bar_count;  // grid barrier (QR)
+  unsigned bar_gen;
+  double rel_step;     // last ||b+ - b|| / ||b+||
+  double pad[3];
+};
+
+// ----------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11).  Counter (c0..c3), key (k0, k1).
+struct U4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                            uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
+// Draw streams (counter word c2): signs D, permutation P, sampling order sigma.
+enum { STREAM_D = 0, STREAM_P = 1, STREAM_SIGMA = 2 };
+
+// ----------------------------------------------------------------------------------
+// Error-free transformations (Knuth TwoSum; FMA-based TwoProd), FP32.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+  p = a * b;
+  e = fmaf(a, b, -p);
+}
+
+// ----------------------------------------------------------------------------------
+// Bounded grid barrier for cooperative launches.  All CTAs of the grid must call it
+// the same number of times.  Gives up after ~1 s and raises ST_TIMEOUT; returns false
+// when the grid should stop (timeout here or in another CTA).
+__device__ __forceinline__ bool grid_barrier(DevState *st, unsigned nblocks) {
+  __syncthreads();
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    volatile unsigned *genp = &st->bar_gen;
+    const unsigned g = *genp;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&st->bar_count, 1u);
+    int ok = 1;
+    if (arrived == nblocks - 1) {
+      st->bar_count = 0;
+      __threadfence();
+      atomicAdd(&st->bar_gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*genp == g) {
+        __nanosleep(64);
+        if (++spins > (1ll << 24)) { atomicOr(&st->status, ST_TIMEOUT); ok = 0; break; }
+        if (((volatile unsigned *)&st->status)[0] & ST_TIMEOUT) { ok = 0; break; }
+      }
+    }
+    __threadfence();
+    if (((volatile unsigned *)&st->status)[0] & ST_TIMEOUT) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ----------------------------------------------------------------------------------
+// Host-side launchers implemented in the .cu files.
+
+// draws.cu
+size_t draws_ws_bytes(int64_t Np);
+cudaError_t launch_draws(int64_t Np, uint64_t seed, int32_t *Psd /*N', sign-folded P*/,
+                         int32_t *P /*nullable*/, int32_t *sigma, int8_t *D /*nullable*/,
+                         void *ws, cudaStream_t s);
+cudaError_t launch_pos_map(const int32_t *sigma, int64_t Np, int64_t s0, int64_t s1, int32_t *pos,
+                           cudaStream_t s);
+
+// srht.cu
+struct SrhtPlan {
+  int logN;         // log2 N'
+  int log1, log2;   // pass split: n1 = 2^log1 groups-by-stride, n2 = 2^log2 rows per pass-1 group
+  bool single;      // one pass (N' small)
+};
+SrhtPlan srht_plan(int64_t Np);
+// Sketch of [X|Y] into sampled rows: out row pos[k] (if >= 0) gets scale * (H D P X_pad)[k].
+// W (intermediate, N' x ldw of the output type) is unused for single-pass plans.
+cudaError_t launch_srht(const SrhtPlan &pl, int prec, int xdtype, const void *X, int64_t ldx,
+                        const void *Y, int64_t N, int d, const int32_t *Psd, const int32_t *pos,
+                        void *W, void *WY, int64_t ldw, void *U, void *V, int64_t ldu, double scale,
+                        cudaStream_t s);
+
+// grad.cu
+enum GradMode { GM_F64 = 0, GM_MIXED = 1, GM_STAGE1_BF16 = 2, GM_STAGE1_F64 = 3 };
+int grad_grid(int nsm);
+cudaError_t launch_grad(int mode, int xdtype, const void *X, int64_t ldx, const void *Y, int64_t nrows,
+                        int d, const double *beta_ring, DevState *st, const float *delta32, float *r0,
+                        double *beta0, double *partials, int nblk, int check_done, cudaStream_t s);
+cudaError_t launch_reduce(const double *partials, int nblk, int d, double scale, double *g,
+                          DevState *st, int check_done, cudaStream_t s);
+struct UpdateArgs {
+  const double *g;
+  const double *Hinv;
+  double *beta_ring;   // 3 x d
+  double *beta0;       // mixed: base point
+  float *delta32;      // mixed: fl32(beta - beta0)
+  double *hist;        // trace, nullable
+  int hist_cap;
+  int d;
+  double mu, eta;
+  int first;           // momentum reset for this iteration
+  int stage2;          // check stopping
+  double thr;          // relative-step threshold (stage 2, > 0 to enable)
+  int T;               // iteration cap
+  int mixed;           // maintain delta32 / rebase flag
+  int check_done;
+};
+cudaError_t launch_update(const UpdateArgs &a, DevState *st, cudaStream_t s);
+cudaError_t launch_copy_beta(const double *beta_ring, DevState *st, int d, double *out, cudaStream_t s);
+
+// linalg.cu
+size_t qr_ws_bytes(int64_t r, int d, int nsm);
+cudaError_t launch_gather_hessian_rows(int prec, const void *U, int64_t ldu, int64_t row0, int64_t r,
+                                       int d, double scale, double *A, cudaStream_t s);
+cudaError_t launch_qr(double *A, int64_t r, int d, int64_t lda, double *R, double *Hinv, void *ws,
+                      DevState *st, cudaStream_t s);
+
+}  // namespace slse

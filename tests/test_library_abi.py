@@ -1,0 +1,92 @@
+"""CPU checks of the C ABI: the library builds, loads, exports every function that
+include/slse.h declares, and its host-only helpers agree with the oracle.  No kernel
+is launched here (no GPU in this environment)."""
+import ctypes
+import math
+import os
+import re
+import shutil
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "slse.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(slse_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    import __graft_entry__
+    path = __graft_entry__._build_module().build()
+    return ctypes.CDLL(path)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "slse_fit" in names and "slse_sketch" in names and "slse_grad" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_the_header():
+    import paper_2509_06856_gb300 as slse
+    assert sorted(slse.EXPORTED) == _declared()
+
+
+def test_host_helpers_match_oracle(lib):
+    import paper_2509_06856_gb300 as slse
+    from oracle import slse as osl
+    for om, mp, mi, d in [(1 / 16, 1024, 2048, 64), (1.0, 4096, 8192, 64), (0.25, 200, 400, 50)]:
+        assert slse.ai_bound(om, mp, mi, d) == pytest.approx(osl.ai_bound(om, mp, mi, d), rel=1e-14)
+    assert math.isnan(slse.ai_bound(0.5, 10, 20, 64))
+    for N, d in [(1 << 20, 64), (20000, 50), (1 << 22, 512), (100, 64)]:
+        a = slse.default_schedule(N, d)
+        b = osl.default_schedule(N, d)
+        assert a.m == b.m and a.a == b.a and a.r == b.r and a.T == b.T
+        assert a.mu == pytest.approx(b.mu, rel=1e-15) and a.eta == pytest.approx(b.eta, rel=1e-15)
+    assert slse.status_string(0) == "ok" and slse.version() >= 100
+
+
+def test_invalid_arguments_rejected_before_any_launch(lib):
+    import paper_2509_06856_gb300 as slse
+    beta = (ctypes.c_double * 4)()
+    bad = [
+        slse.CProblem(0, 4, slse.F64, 1, 4, 1),        # N = 0
+        slse.CProblem(10, 0, slse.F64, 1, 4, 1),       # d = 0
+        slse.CProblem(10, 4, slse.F64, 1, 3, 1),       # ldx < d
+        slse.CProblem(3, 4, slse.F64, 1, 4, 1),        # d > N
+        slse.CProblem(10, 4, 7, 1, 4, 1),              # bad dtype
+        slse.CProblem(10, 4, slse.F64, None, 4, 1),    # null X
+        slse.CProblem(10, 600, slse.F64, 1, 600, 1),   # d above this build's limit
+        slse.CProblem(1 << 27, 4, slse.F64, 1, 4, 1),  # N' above 2^26
+    ]
+    for p in bad:
+        assert lib.slse_fit(ctypes.byref(p), None, ctypes.c_uint64(0), beta, None, None, None,
+                            ctypes.c_size_t(0), None) == slse.EINVAL
+        assert slse._lib.slse_workspace_size(ctypes.byref(p), None, slse.OP_FIT, 0) == 0
+    good = slse.CProblem(100, 4, slse.F64, 256, 4, 512)
+    sch = slse.Schedule(m=[64, 32], a=[2, 2], r=24, mu=0.7, eta=0.1).to_c()  # not ascending
+    assert slse._lib.slse_fit(ctypes.byref(good), ctypes.byref(sch), 0, beta, None, None, None, 0, None) == slse.EINVAL
+    sch = slse.Schedule(m=[32], a=[2], r=2, mu=0.7, eta=0.1).to_c()          # r < d
+    assert slse._lib.slse_fit(ctypes.byref(good), ctypes.byref(sch), 0, beta, None, None, None, 0, None) == slse.EINVAL
+    sch = slse.Schedule(m=[32], a=[2], r=24, mu=0.7, eta=0.1, prec="mixed_bf16").to_c()  # mixed needs F32
+    assert slse._lib.slse_fit(ctypes.byref(good), ctypes.byref(sch), 0, beta, None, None, None, 0, None) == slse.EINVAL
+    assert slse._lib.slse_draws(0, 0, 1, 1, None, None, 0, None) == slse.EINVAL
+    assert slse._lib.slse_qr(1, 3, 4, 4, 1, None, None, 0, None) == slse.EINVAL   # r < d
+
+
+def test_workspace_size_is_monotone_in_problem_size(lib):
+    import paper_2509_06856_gb300 as slse
+    sizes = []
+    for N in (1 << 12, 1 << 16, 1 << 20):
+        p = slse.CProblem(N, 64, slse.F32, 256, 64, 512)
+        sch = slse.default_schedule(N, 64, prec="mixed_bf16").to_c()
+        sizes.append(slse._lib.slse_workspace_size(ctypes.byref(p), ctypes.byref(sch), slse.OP_FIT, 0))
+    assert 0 < sizes[0] < sizes[1] < sizes[2]
