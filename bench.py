@@ -1,0 +1,415 @@
+#!/usr/bin/env python
+"""Benchmark of the SLSE-FRS hot path on one GB300: time to reach a relative error of
+1e-8 in beta-hat (mixed-precision path) and the HBM throughput of its dominant kernel,
+with the plain FP64 GPU path measured beside it.
+
+Workload: N = 2^22 rows, d = 512 columns, X stored FP32 (8.6 GB, larger than L2),
+rows i.i.d. N(0, Sigma) with Sigma_ij = 0.5^|i-j|, beta ~ N(0, I), noise sd 0.1;
+the paper's schedule rule (r = 6d, m_1 = 8d doubling to N/2, a_i = 2, T = 100).
+Each timed step is one slse_fit call with a fresh sketch seed.  The accuracy
+reference is the CPU oracle's OLS estimate (FP64 normal equations; cond(X) ~ 3).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Prints one JSON line (rank 0).  Multi-GPU runs are independent replicas.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-8 rel-err β̂ (ms) & HBM GB/s, mixed vs FP64 GPU, N=2^22 d=512"
+TARGET = 1e-8
+WORKLOAD = "AR(1) rho=0.5 Gaussian rows, N=2^22, d=512, X fp32, sigma=0.1, beta~N(0,I)"
+FALLBACK_HBM = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--log2n", type=int, default=22)
+    ap.add_argument("--d", type=int, default=512)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--sample-log2n", type=int, default=15)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline timing (accuracy reference still runs)")
+    return ap.parse_args()
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0
+    import torch.distributed as dist
+    backend = "nccl"
+    dist.init_process_group(backend=backend)
+    return dist.get_rank(), ws, int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(v, ws):
+    if ws <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(v, ws):
+    if ws <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() in ("active", "1"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- helpers
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            v = json.load(f).get("hbm_gbs")
+        if v:
+            return float(v), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_HBM, "fallback"
+
+
+def profile_traffic(kernel_key, source_files):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            prof = json.load(f)
+    except (OSError, ValueError):
+        return None
+    ent = prof.get(kernel_key)
+    if not ent:
+        return None
+    h = hashlib.sha256()
+    for sf in source_files:
+        with open(os.path.join(ROOT, sf), "rb") as f:
+            h.update(f.read())
+    if ent.get("source_sha256") != h.hexdigest():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def make_data(log2n, d):
+    import workloads
+    return workloads.cfg3(N=1 << log2n, d=d, seed=1003)
+
+
+def first_crossing(hist, ms, bh, target):
+    nb = np.linalg.norm(bh)
+    errs = np.linalg.norm(hist - bh[None, :], axis=1) / nb
+    idx = np.nonzero(errs <= target)[0]
+    if idx.size == 0:
+        return None, float(errs[-1]) if errs.size else float("nan")
+    return float(ms[idx[0]]), float(errs[idx[0]])
+
+
+# ----------------------------------------------------------------------------- oracle legs
+def cpu_leg(X, Y, log2n, d, sample_log2n, time_it):
+    """The only place the benchmark runs the oracle: the accuracy reference (OLS of the
+    full workload) and, optionally, the oracle's own SLSE-FRS timed on a bounded sample."""
+    from oracle import linalg, slse as osl
+    t0 = time.time()
+    bh = linalg.ols_normal(X, Y)
+    t_ref = time.time() - t0
+    base = None
+    if time_it:
+        ns = 1 << sample_log2n
+        Xs, Ys = X[:ns].astype(np.float64), Y[:ns].astype(np.float64)
+        sched = osl.default_schedule(ns, d, T=100, tol=1e-9)
+        t0 = time.time()
+        osl.slse_fit(Xs, Ys, sched, seed=0)
+        dt = time.time() - t0
+        scale = (1 << log2n) / ns
+        base = {"value": dt * 1000.0 * scale, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+                "sample": f"oracle slse_fit (FP64, numpy) on the first 2^{sample_log2n} rows of the workload "
+                          f"(d={d}, same schedule rule), wall time x {scale:.0f} (linear in N)",
+                "sample_seconds": dt}
+    return bh, t_ref, base
+
+
+def run_reference(args, rank, ws):
+    if rank != 0:
+        return
+    from oracle import slse as osl
+    import workloads
+    d = args.d
+    ns = 1 << args.sample_log2n
+    p = workloads.cfg3(N=ns, d=d, seed=1003)
+    Xs, Ys = p["X"].astype(np.float64), p["Y"].astype(np.float64)
+    sched = osl.default_schedule(ns, d, T=100, tol=1e-9)
+    for w in range(args.warmup):
+        osl.slse_fit(Xs, Ys, sched, seed=100 + w)
+    times = []
+    for k in range(args.steps):
+        t0 = time.time()
+        osl.slse_fit(Xs, Ys, sched, seed=k)
+        times.append(time.time() - t0)
+    scale = (1 << args.log2n) / ns
+    val = statistics.mean(times) * 1000.0 * scale
+    sample = (f"oracle slse_fit (FP64, numpy) per step on a 2^{args.sample_log2n}-row sample of the workload "
+              f"(d={d}, same schedule rule), wall time x {scale:.0f} (linear in N)")
+    out = {"metric": METRIC, "value": val, "unit": "ms", "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": statistics.mean(times) * 1000.0, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": WORKLOAD, "N": 1 << args.log2n, "d": d, "sample_rows": ns},
+           "cpu_baseline": {"value": val, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle", "sample": sample},
+           "e2e": {"value": val, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args, rank, ws, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    import paper_2509_06856_gb300 as slse
+
+    N, d = 1 << args.log2n, args.d
+    t0 = time.time()
+    data = make_data(args.log2n, d)
+    X, Y = data["X"], data["Y"]
+    t_gen = time.time() - t0
+
+    Xh = torch.empty((N, d), dtype=torch.float32, pin_memory=True)
+    Yh = torch.empty(N, dtype=torch.float32, pin_memory=True)
+    Xh.numpy()[:] = X
+    Yh.numpy()[:] = Y
+    Xd = Xh.cuda()
+    Yd = Yh.cuda()
+
+    # accuracy reference (and CPU baseline at N = 1) from the oracle, rank 0
+    bh, t_ref, cpu_base = (None, None, None)
+    if rank == 0:
+        bh, t_ref, cpu_base = cpu_leg(X, Y, args.log2n, d, args.sample_log2n, time_it=(ws == 1 and not args.no_cpu))
+
+    sched = slse.default_schedule(N, d, prec="mixed_bf16", T=100, tol=5e-9)
+    wsz = slse.workspace_size(Xd, Yd, slse.OP_FIT, sched)
+    wbuf = slse.alloc_workspace(wsz)
+    cap = sched.T
+
+    for w in range(max(3, args.warmup)):
+        slse.fit(Xd, Yd, sched, seed=1000 + w, workspace=wbuf, trace_cap=cap)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    results = []
+    e0.record()
+    for k in range(args.steps):
+        results.append(slse.fit(Xd, Yd, sched, seed=k, workspace=wbuf, trace_cap=cap))
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+
+    # time-to-accuracy from the per-iteration CUDA events of each fit
+    tta, errs_final, crossed = [], [], True
+    for r in results:
+        hist = r.beta_hist.cpu().numpy() if rank == 0 else None
+        if rank == 0:
+            t, e = first_crossing(hist, np.array(r.ms_hist), bh, TARGET)
+            if t is None:
+                crossed = False
+                t = r.report["ms_total"]
+            tta.append(t)
+            errs_final.append(float(np.linalg.norm(r.beta - bh) / np.linalg.norm(bh)))
+    value_local = statistics.mean(tta) if rank == 0 else 0.0
+    value = reduce_max(value_local, ws)
+    ms_per_step = reduce_max(ms_total / args.steps, ws)
+    launches = int(reduce_sum(sum(r.report["kernels"] for r in results), ws))
+
+    # dominant kernel: 2nd-stage gradient vs the two sketch passes (summed CUDA-event times)
+    rep = results[-1].report
+    k_times = {
+        "grad_stage2": (rep["ms_grad2"], rep["n_grad2"], rep["bytes_grad2"]),
+        "srht_pass1": (rep["ms_srht_pass1"], 1, N * (d + 1) * 4.0 + N * (d + 1) * 2.0),
+        "srht_pass2": (rep["ms_srht_pass2"], 1, N * (d + 1) * 2.0 + (sched.m[-1] + sched.r) * (d + 1) * 2.0),
+    }
+    peak, peak_kind = measured_hbm_peak()
+    kernels_gbs = {}
+    for k, (ms, n, by) in k_times.items():
+        if ms > 0 and n > 0:
+            kernels_gbs[k] = {"ms_per_launch": ms / n, "launches": n, "alg_bytes_per_launch": by,
+                              "gbs": by / (ms / n) / 1e6, "frac_of_" + peak_kind: by / (ms / n) / 1e6 / peak}
+    dom = max(k_times, key=lambda k: k_times[k][0])
+    ms_d, n_d, by_d = k_times[dom]
+    achieved = by_d / (ms_d / n_d) / 1e6
+    src = {"grad_stage2": ["paper_2509_06856_gb300/csrc/grad.cu"],
+           "srht_pass1": ["paper_2509_06856_gb300/csrc/srht.cu"],
+           "srht_pass2": ["paper_2509_06856_gb300/csrc/srht.cu"]}[dom]
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": profile_traffic(dom, src), "kernel": dom, "peak_source": peak_kind,
+                "frac_of_nominal_8000": achieved / 8000.0}
+
+    # FP64 GPU path on the same workload (X widened exactly to FP64 in the kernels)
+    fp64 = None
+    if args.fp64_steps > 0:
+        s64 = slse.default_schedule(N, d, prec="fp64", T=100, tol=1e-11)
+        w64 = slse.alloc_workspace(slse.workspace_size(Xd, Yd, slse.OP_FIT, s64))
+        slse.fit(Xd, Yd, s64, seed=999, workspace=w64, trace_cap=cap)
+        t8, t10, tot, fin = [], [], [], []
+        for k in range(args.fp64_steps):
+            r = slse.fit(Xd, Yd, s64, seed=k, workspace=w64, trace_cap=cap)
+            if rank == 0:
+                h = r.beta_hist.cpu().numpy()
+                a8, _ = first_crossing(h, np.array(r.ms_hist), bh, 1e-8)
+                a10, _ = first_crossing(h, np.array(r.ms_hist), bh, 1e-10)
+                t8.append(a8)
+                t10.append(a10)
+                tot.append(r.report["ms_total"])
+                fin.append(float(np.linalg.norm(r.beta - bh) / np.linalg.norm(bh)))
+        del w64
+        if rank == 0:
+            r64 = r.report
+            fp64 = {"time_to_1e-8_ms": statistics.mean(t8) if all(v is not None for v in t8) else None,
+                    "time_to_1e-10_ms": statistics.mean(t10) if all(v is not None for v in t10) else None,
+                    "ms_per_fit": statistics.mean(tot), "final_rel_err": max(fin),
+                    "phases_ms": {k: r64[k] for k in ("ms_draws", "ms_sketch", "ms_qr", "ms_stage1", "ms_stage2")},
+                    "grad_stage2_ms_per_pass": r64["ms_grad2"] / max(1, r64["n_grad2"]),
+                    "iters": [r64["iters_stage1"], r64["iters_stage2"]]}
+        torch.cuda.empty_cache()
+
+    # end to end through the public API with pinned host inputs (copy inside the call)
+    e2e = None
+    if args.e2e_steps > 0:
+        wsz_h = slse.workspace_size(Xh, Yh, slse.OP_FIT, sched)
+        wh = slse.alloc_workspace(wsz_h)
+        slse.fit(Xh, Yh, sched, seed=2000, workspace=wh, trace_cap=cap)
+        ev = []
+        for k in range(args.e2e_steps):
+            r = slse.fit(Xh, Yh, sched, seed=k, workspace=wh, trace_cap=cap)
+            if rank == 0:
+                t, _ = first_crossing(r.beta_hist.cpu().numpy(), np.array(r.ms_hist), bh, TARGET)
+                ev.append((t if t is not None else r.report["ms_total"], r.report["ms_copy_in"]))
+        del wh
+        if rank == 0:
+            e2e = {"value": reduce_max(statistics.mean(v for v, _ in ev), 1), "unit": "ms",
+                   "h2d_bytes_per_step": int(Xh.numel() * 4 + Yh.numel() * 4), "d2h_bytes_per_step": d * 8,
+                   "ms_copy_in": statistics.mean(c for _, c in ev),
+                   "how": "slse_fit with pinned host X, Y: H2D copy on a side stream overlapped with the draws, "
+                          "time from the call's first CUDA event to the first iterate within 1e-8"}
+
+    if rank != 0:
+        return
+    out = {
+        "metric": METRIC, "value": value, "unit": "ms", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "d": d, "X_dtype": "fp32", "precision": "mixed_bf16",
+                   "schedule": f"m={sched.m[0]}..{sched.m[-1]} (x2), a_i=2, r={sched.r}, T=100, tol=5e-9",
+                   "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (X is 8.6 GB)", "seeds": f"sketch seeds 0..{args.steps - 1}"},
+        "roofline": roofline,
+        "cpu_baseline": cpu_base,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "accuracy": {"target": TARGET, "crossed_every_step": crossed, "final_rel_err_max": max(errs_final),
+                     "reference": "oracle OLS, FP64 normal equations", "reference_seconds": t_ref},
+        "fp64": fp64,
+        "phases_ms": {k: rep[k] for k in ("ms_draws", "ms_sketch", "ms_srht_pass1", "ms_srht_pass2", "ms_qr",
+                                          "ms_stage1", "ms_stage2", "ms_total")},
+        "iters": [rep["iters_stage1"], rep["iters_stage2"]], "rebases": rep["rebases"],
+        "kernels": kernels_gbs, "data_gen_seconds": t_gen,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    rank, ws, local_rank = dist_init()
+    if args.impl == "reference":
+        run_reference(args, rank, ws)
+    else:
+        run_ours(args, rank, ws, local_rank)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

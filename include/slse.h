@@ -31,7 +31,7 @@
  *   deterministic estimate (all reductions have a fixed order).
  * - Gradient sign: g = X^T (Y - X beta), i.e. minus the paper's
  *   nabla f = X^T (X beta - Y) (Sec. 1); the M-IHS step adds mu H-hat^{-1} g.
- * - Kernel limits of this build: 1 <= d <= 512, d <= N, N' = 2^ceil(log2 N) <= 2^26.
+ * - Kernel limits of this build: 1 <= d <= 512, d <= N, N' = 2^ceil(log2 N) <= 2^24.
  */
 #ifndef SLSE_H
 #define SLSE_H
@@ -71,9 +71,10 @@ typedef struct {
   int64_t N;       /* rows, N >= d */
   int32_t d;       /* columns, 1 <= d <= 512 */
   int32_t dtype;   /* slse_dtype of X and Y: SLSE_F64 or SLSE_F32 */
-  const void *X;   /* device, N x d row-major, leading dimension ldx */
+  const void *X;   /* N x d row-major, leading dimension ldx: device memory, or (slse_fit only)
+                      host memory, pinned or pageable, which slse_fit copies into its workspace */
   int64_t ldx;     /* >= d */
-  const void *Y;   /* device, N, same dtype as X */
+  const void *Y;   /* N, same dtype and the same kind of memory as X */
 } slse_problem;
 
 typedef struct {
@@ -90,10 +91,16 @@ typedef struct {
 } slse_schedule;
 
 typedef struct {
-  double ms_draws, ms_sketch, ms_qr, ms_stage1, ms_stage2, ms_total; /* CUDA-event times */
+  double ms_copy_in;      /* host inputs only: CUDA-event time of the host-to-device copy (overlaps ms_draws) */
+  double ms_draws, ms_sketch, ms_qr, ms_stage1, ms_stage2, ms_total; /* CUDA-event phase times */
+  double ms_srht_pass1, ms_srht_pass2; /* the two sketch passes (pass 2 is 0 for single-pass sizes) */
+  double ms_grad2;        /* summed CUDA-event time of the 2nd-stage gradient launches */
+  int32_t n_grad2;        /* number of those launches that did a full pass */
+  int32_t kernels;        /* kernel launches made by the call */
   int32_t iters_stage1, iters_stage2;
   double final_rel_step;  /* ||b_T - b_{T-1}|| / ||b_T|| of the last iteration */
   double bytes_moved;     /* algorithmic HBM bytes of the sketch passes and gradient passes */
+  double bytes_grad2;     /* algorithmic HBM bytes of one 2nd-stage gradient pass */
   int32_t rebases;        /* mixed path: number of 2nd-stage residual re-bases */
   int32_t status;
 } slse_report;
@@ -114,7 +121,9 @@ size_t slse_workspace_size(const slse_problem *prob, const slse_schedule *sched,
 /* Algorithm 2 end to end (paper Sec. 3).  seed selects the random draws D, P and the
  * sampling order (Philox4x32-10).  beta_out: host, d doubles.  report, trace: nullable.
  * Synchronous: returns after beta_out is written.  sched == NULL selects the paper's
- * experimental defaults (slse_default_schedule) in FP64. */
+ * experimental defaults (slse_default_schedule) in FP64.  With host X and Y the copy to the
+ * device runs on a side stream while the random draws run on `stream`; the workspace then
+ * also holds the device copy (slse_workspace_size accounts for it). */
 slse_status slse_fit(const slse_problem *prob, const slse_schedule *sched, uint64_t seed,
                      double *beta_out, slse_report *report, slse_trace *trace,
                      void *workspace, size_t ws_bytes, slse_stream_t stream);

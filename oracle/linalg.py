@@ -81,6 +81,23 @@ def ols(X: np.ndarray, Y: np.ndarray, block_rows: int = 1 << 16, textbook: bool 
     return solve_upper(Rf[:d, :d], Rf[:d, d])
 
 
+def ols_normal(X: np.ndarray, Y: np.ndarray, block_rows: int = 1 << 16) -> np.ndarray:
+    """beta-hat = (X^T X)^{-1} X^T Y written out (Sec. 1): the Gram matrix and X^T Y are
+    accumulated in FP64 over row blocks (numpy matmul as the library primitive) and the
+    d x d system is solved by Cholesky.  Its error grows like cond(X)^2 * u, so it serves
+    only well-conditioned inputs (cond(X) ~ 3 for the AR(1) workload: ~1e-15); the QR
+    route ``ols`` is the general oracle."""
+    N, d = X.shape
+    G = np.zeros((d, d))
+    b = np.zeros(d)
+    for lo in range(0, N, block_rows):
+        Xb = np.asarray(X[lo:lo + block_rows], np.float64)
+        G += Xb.T @ Xb
+        b += Xb.T @ np.asarray(Y[lo:lo + block_rows], np.float64)
+    L = np.linalg.cholesky(G)
+    return solve_upper(L.T, solve_lower(L, b))
+
+
 def ols_normal_longdouble(X: np.ndarray, Y: np.ndarray) -> np.ndarray:
     """Brute-force OLS from the normal equations X^T X beta = X^T Y, formed and solved
     by Gaussian elimination with partial pivoting in extended precision (np.longdouble).

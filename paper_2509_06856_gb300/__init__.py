@@ -45,11 +45,13 @@ class CSchedule(ctypes.Structure):
 
 
 class CReport(ctypes.Structure):
-    _fields_ = [("ms_draws", ctypes.c_double), ("ms_sketch", ctypes.c_double), ("ms_qr", ctypes.c_double),
-                ("ms_stage1", ctypes.c_double), ("ms_stage2", ctypes.c_double), ("ms_total", ctypes.c_double),
+    _fields_ = [("ms_copy_in", ctypes.c_double), ("ms_draws", ctypes.c_double), ("ms_sketch", ctypes.c_double),
+                ("ms_qr", ctypes.c_double), ("ms_stage1", ctypes.c_double), ("ms_stage2", ctypes.c_double),
+                ("ms_total", ctypes.c_double), ("ms_srht_pass1", ctypes.c_double), ("ms_srht_pass2", ctypes.c_double),
+                ("ms_grad2", ctypes.c_double), ("n_grad2", ctypes.c_int32), ("kernels", ctypes.c_int32),
                 ("iters_stage1", ctypes.c_int32), ("iters_stage2", ctypes.c_int32),
                 ("final_rel_step", ctypes.c_double), ("bytes_moved", ctypes.c_double),
-                ("rebases", ctypes.c_int32), ("status", ctypes.c_int32)]
+                ("bytes_grad2", ctypes.c_double), ("rebases", ctypes.c_int32), ("status", ctypes.c_int32)]
 
 
 class CTrace(ctypes.Structure):
@@ -208,7 +210,7 @@ def fit(X, Y, schedule: Schedule | None = None, seed: int = 0, workspace=None, t
     hist = None
     ms = None
     if trace_cap > 0:
-        hist = torch.zeros((trace_cap, p.d), dtype=torch.float64, device=X.device)
+        hist = torch.zeros((trace_cap, p.d), dtype=torch.float64, device=X.device if X.is_cuda else "cuda")
         ms = (ctypes.c_float * trace_cap)()
         tr = CTrace(hist.data_ptr(), ctypes.cast(ms, ctypes.POINTER(ctypes.c_float)), trace_cap, 0)
     ws_ptr, ws_len = (workspace.data_ptr(), workspace.numel() * workspace.element_size()) if workspace is not None \

@@ -15,7 +15,7 @@ namespace {
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 constexpr size_t kStateBytes = 4096;  // DevState + per-CTA partials of the update kernel
-constexpr int64_t kMaxNp = int64_t(1) << 26;
+constexpr int64_t kMaxNp = int64_t(1) << 24;
 
 int num_sms() {
   int dev = 0, n = 0;
@@ -28,6 +28,16 @@ int64_t padded(int64_t N) {
   int64_t p = 1;
   while (p < N) p <<= 1;
   return p;
+}
+
+// Host memory (pinned or pageable) as opposed to device or managed memory.
+bool is_host_pointer(const void *ptr) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
 }
 
 bool valid_problem(const slse_problem *p) {
@@ -92,6 +102,8 @@ struct FitLayout {
   int64_t Np, n_samp, h0, ldu;
   SrhtPlan sp;
   int nblk;
+  bool host_in;
+  size_t o_xin, o_yin;
   size_t o_state, o_psd, o_sigma, o_pos, o_big, o_wy, o_u, o_v, o_A, o_R, o_Hinv, o_qr, o_part, o_g, o_ring,
       o_b0, o_d32, o_out, o_r0;
   size_t total;
@@ -134,6 +146,12 @@ FitLayout fit_layout(const slse_problem *p, const Sched &s, int nsm) {
   L.o_d32 = w.take((size_t)d * 4);
   L.o_out = w.take((size_t)d * 8);
   L.o_r0 = w.take(s.prec == SLSE_PREC_MIXED_BF16 ? (size_t)p->N * 4 : 0);
+  L.host_in = is_host_pointer(p->X);
+  if (L.host_in) {
+    const size_t bx = p->dtype == SLSE_F64 ? 8 : 4;
+    L.o_xin = w.take((size_t)p->N * d * bx);
+    L.o_yin = w.take((size_t)p->N * bx);
+  }
   L.total = w.total;
   return L;
 }
@@ -271,15 +289,18 @@ int grad_blocks(int64_t rows, int maxblk) {
   return (int)b;
 }
 
-slse_status fit_impl(const slse_problem *p, const Sched &s, uint64_t seed, double *beta_out, slse_report *rep,
+slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, double *beta_out, slse_report *rep,
                      slse_trace *tr, void *ws_user, size_t ws_bytes, cudaStream_t st) {
   const int nsm = num_sms();
   if (nsm <= 0) return SLSE_ECUDA;
-  const FitLayout L = fit_layout(p, s, nsm);
+  const FitLayout L = fit_layout(pin, s, nsm);
+  if (is_host_pointer(pin->Y) != L.host_in) return SLSE_EINVAL;  // X and Y in the same kind of memory
   Workspace W;
   slse_status a = acquire(W, ws_user, ws_bytes, L.total, st);
   if (a != SLSE_OK) return a;
   char *base = static_cast<char *>(W.ptr);
+  slse_problem prob = *pin;  // device view of the inputs
+  const slse_problem *p = &prob;
   DevState *dst = reinterpret_cast<DevState *>(base + L.o_state);
   int32_t *Psd = reinterpret_cast<int32_t *>(base + L.o_psd);
   int32_t *sigma = reinterpret_cast<int32_t *>(base + L.o_sigma);
@@ -302,11 +323,12 @@ slse_status fit_impl(const slse_problem *p, const Sched &s, uint64_t seed, doubl
   const int d = p->d;
   const bool mixed = s.prec == SLSE_PREC_MIXED_BF16;
   const int T = s.T;
+  int kernels = 0;
 
   Events E;
-  cudaEvent_t e_start = E.make(), e_draws = E.make(), e_sketch = E.make(), e_qr = E.make(), e_s1 = E.make(),
-              e_end = E.make();
-  if (!e_start || !e_end) return SLSE_ECUDA;
+  cudaEvent_t e_start = E.make(), e_draws = E.make(), e_mid = E.make(), e_sketch = E.make(), e_qr = E.make(),
+              e_s1 = E.make(), e_end = E.make(), e_copied = E.make();
+  if (!e_start || !e_end || !e_mid || !e_copied) return SLSE_ECUDA;
   const int hist_cap = tr ? (tr->cap < T ? tr->cap : T) : 0;
   std::vector<cudaEvent_t> e_it;
   if (tr && tr->ms_hist)
@@ -321,19 +343,46 @@ slse_status fit_impl(const slse_problem *p, const Sched &s, uint64_t seed, doubl
   };
 
   CK(cudaEventRecord(e_start, st));
+  // host inputs: copy into the workspace on a side stream, overlapped with the draws
+  struct SideStream {
+    cudaStream_t h = nullptr;
+    ~SideStream() {
+      if (h) cudaStreamDestroy(h);
+    }
+  } side;
+  if (L.host_in) {
+    const size_t bx = p->dtype == SLSE_F64 ? 8 : 4;
+    void *xd = base + L.o_xin;
+    void *yd = base + L.o_yin;
+    CK(cudaStreamCreateWithFlags(&side.h, cudaStreamNonBlocking));
+    CK(cudaStreamWaitEvent(side.h, e_start, 0));
+    CK(cudaMemcpy2DAsync(xd, (size_t)d * bx, pin->X, (size_t)pin->ldx * bx, (size_t)d * bx, (size_t)p->N,
+                         cudaMemcpyHostToDevice, side.h));
+    CK(cudaMemcpyAsync(yd, pin->Y, (size_t)p->N * bx, cudaMemcpyHostToDevice, side.h));
+    CK(cudaEventRecord(e_copied, side.h));
+    prob.X = xd;
+    prob.Y = yd;
+    prob.ldx = d;
+  }
   k_init_state<<<1, 32, 0, st>>>(dst, 0);
   CK(cudaGetLastError());
+  ++kernels;
   // a1: random draws
   CK(launch_draws(L.Np, seed, Psd, nullptr, sigma, nullptr, big, st));
-  CK(launch_pos_map(sigma, L.Np, 0, L.n_samp, pos, st));
+  kernels += 9;
+  CK(launch_pos_map(sigma, L.Np, 0, L.n_samp, L.sp.single ? L.sp.logN : L.sp.log2, pos, st));
+  kernels += 1;
   CK(cudaEventRecord(e_draws, st));
-  // a2-a4: SRHT into the sampled rows (unscaled by the sketch size: U = Z[sigma] with Z = H D P X / sqrt(N'))
+  if (L.host_in) CK(cudaStreamWaitEvent(st, e_copied, 0));
+  // a2-a4: SRHT into the sampled rows (U = Z[sigma] with Z = H D P X / sqrt(N'); sketch scales applied later)
   CK(launch_srht(L.sp, s.prec, p->dtype, p->X, p->ldx, p->Y, p->N, d, Psd, pos, big, WY, L.ldu, U, V, L.ldu,
-                 1.0 / std::sqrt((double)L.Np), st));
+                 1.0 / std::sqrt((double)L.Np), st, L.sp.single ? nullptr : e_mid));
+  kernels += L.sp.single ? 1 : 2;
   CK(cudaEventRecord(e_sketch, st));
-  // a5: QR of S-hat X = sqrt(N'/r) U[h0 : h0 + r]
+  // a5: QR of S-hat X = sqrt(N'/r) U[h0 : h0 + r], then H-hat^{-1} = R^{-1} R^{-T}
   CK(launch_gather_hessian_rows(s.prec, U, L.ldu, L.h0, s.r, d, std::sqrt((double)L.Np / (double)s.r), A, st));
   CK(launch_qr(A, s.r, d, d, R, Hinv, qrws, dst, st));
+  kernels += 4;
   CK(cudaEventRecord(e_qr, st));
   CK(cudaMemsetAsync(ring, 0, (size_t)3 * d * 8, st));
 
@@ -342,7 +391,7 @@ slse_status fit_impl(const slse_problem *p, const Sched &s, uint64_t seed, doubl
   ua.hist = tr ? tr->beta_hist : nullptr; ua.hist_cap = hist_cap; ua.d = d; ua.mu = s.mu; ua.eta = s.eta;
   ua.T = T;
 
-  // a8 stage 1: a_i M-IHS steps on each nested sketch
+  // a8 stage 1: a_i M-IHS steps on each nested sketch (prefix of the sampled rows)
   int t = 0;
   for (size_t i = 0; i < s.m.size() && t < T; ++i) {
     const int64_t m = s.m[i];
@@ -354,16 +403,21 @@ slse_status fit_impl(const slse_problem *p, const Sched &s, uint64_t seed, doubl
       ua.first = (j == 0 && s.momentum_reset) || t == 0;
       ua.stage2 = 0; ua.thr = 0.0; ua.mixed = 0; ua.check_done = 0;
       CK(launch_update(ua, dst, st));
+      kernels += 3;
       CK(mark_iter(t));
       ++t;
     }
   }
   const int t1 = t;
   CK(cudaEventRecord(e_s1, st));
-  // a8 stage 2: full-data M-IHS steps until the relative step is small or T is reached
+  // a8 stage 2: full-data M-IHS steps until the relative step is small or T is reached.
+  // Iteration k+1 is enqueued before the stop flag of iteration k is read back; its
+  // kernels return at once when the flag is already set.
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> e_grad;
   if (t < T) {
     k_set_stage2<<<1, 32, 0, st>>>(dst, mixed ? 1 : 0);
     CK(cudaGetLastError());
+    ++kernels;
     DevState *mb = t_mailbox.get();
     if (!mb) return SLSE_ECUDA;
     const double rho = std::sqrt((double)d / (double)s.r);
@@ -372,12 +426,18 @@ slse_status fit_impl(const slse_problem *p, const Sched &s, uint64_t seed, doubl
     cudaEvent_t e_flag[2] = {E.make(), E.make()};
     if (!e_flag[0] || !e_flag[1]) return SLSE_ECUDA;
     for (int k = 0; t + k < T; ++k) {
+      cudaEvent_t g0 = E.make(), g1 = E.make();
+      if (!g0 || !g1) return SLSE_ECUDA;
+      CK(cudaEventRecord(g0, st));
       CK(launch_grad(mixed ? GM_MIXED : GM_F64, p->dtype, p->X, p->ldx, p->Y, p->N, d, ring, dst, d32, r0, b0,
                      part, nb, 1, st));
+      CK(cudaEventRecord(g1, st));
+      e_grad.emplace_back(g0, g1);
       CK(launch_reduce(part, nb, d, 1.0, g, dst, 1, st));
       ua.first = (k == 0 && s.momentum_reset) || (t + k) == 0;
       ua.stage2 = 1; ua.thr = thr; ua.mixed = mixed ? 1 : 0; ua.check_done = 1;
       CK(launch_update(ua, dst, st));
+      kernels += mixed ? 4 : 3;
       CK(mark_iter(t + k));
       CK(cudaMemcpyAsync(&mb[k & 1], dst, sizeof(DevState), cudaMemcpyDeviceToHost, st));
       CK(cudaEventRecord(e_flag[k & 1], st));
@@ -388,6 +448,7 @@ slse_status fit_impl(const slse_problem *p, const Sched &s, uint64_t seed, doubl
     }
   }
   CK(launch_copy_beta(ring, dst, d, outb, st));
+  ++kernels;
   DevState *mb = t_mailbox.get();
   if (!mb) return SLSE_ECUDA;
   CK(cudaMemcpyAsync(&mb[2], dst, sizeof(DevState), cudaMemcpyDeviceToHost, st));
@@ -397,12 +458,22 @@ slse_status fit_impl(const slse_problem *p, const Sched &s, uint64_t seed, doubl
   const DevState fin = mb[2];
   slse_status status = status_from_bits(fin.status);
   if (rep) {
+    rep->ms_copy_in = L.host_in ? ms_between(e_start, e_copied) : 0.0;
     rep->ms_draws = ms_between(e_start, e_draws);
     rep->ms_sketch = ms_between(e_draws, e_sketch);
+    rep->ms_srht_pass1 = L.sp.single ? rep->ms_sketch : ms_between(e_draws, e_mid);
+    rep->ms_srht_pass2 = L.sp.single ? 0.0 : ms_between(e_mid, e_sketch);
     rep->ms_qr = ms_between(e_sketch, e_qr);
     rep->ms_stage1 = ms_between(e_qr, e_s1);
     rep->ms_total = ms_between(e_start, e_end);
-    rep->ms_stage2 = rep->ms_total - rep->ms_draws - rep->ms_sketch - rep->ms_qr - rep->ms_stage1;
+    rep->ms_stage2 = rep->ms_total - ms_between(e_start, e_s1);
+    // gradient launches that ran a full pass (the speculative one after the stop returns at once)
+    const int full = fin.iter - t1;
+    double mg = 0.0;
+    for (int k = 0; k < full && k < (int)e_grad.size(); ++k) mg += ms_between(e_grad[k].first, e_grad[k].second);
+    rep->ms_grad2 = mg;
+    rep->n_grad2 = full;
+    rep->kernels = kernels;
     rep->iters_stage1 = t1;
     rep->iters_stage2 = fin.iter - t1;
     rep->final_rel_step = fin.rel_step;
@@ -412,7 +483,9 @@ slse_status fit_impl(const slse_problem *p, const Sched &s, uint64_t seed, doubl
     if (L.sp.single) bytes += (double)p->N * (d + 1) * bx + (double)L.n_samp * (d + 1) * bu;
     else bytes += (double)p->N * (d + 1) * bx + 2.0 * (double)L.Np * (d + 1) * bu + (double)L.n_samp * (d + 1) * bu;
     for (size_t i = 0; i < s.m.size(); ++i) bytes += (double)s.a[i] * (double)s.m[i] * (d + 1) * bu;
-    bytes += (double)(fin.iter - t1) * (double)p->N * (d + 1) * bx;
+    // a 2nd-stage pass reads X and one N-vector (Y in FP64 / rebase passes, r0 otherwise)
+    rep->bytes_grad2 = (double)p->N * d * bx + (double)p->N * (mixed ? 4.0 : bx);
+    bytes += (double)full * rep->bytes_grad2;
     rep->bytes_moved = bytes;
     rep->status = status;
   }
@@ -477,6 +550,7 @@ slse_status slse_fit(const slse_problem *prob, const slse_schedule *sched, uint6
 slse_status slse_sketch(const slse_problem *prob, int32_t kind, int32_t prec, uint64_t seed, int64_t m, void *SX,
                         int64_t ldsx, void *SY, void *workspace, size_t ws_bytes, slse_stream_t stream) {
   if (!valid_problem(prob) || !SX || !SY) return SLSE_EINVAL;
+  if (is_host_pointer(prob->X) || is_host_pointer(prob->Y)) return SLSE_EINVAL;
   if (kind != SLSE_SRHT) return SLSE_EINVAL;
   if (prec != SLSE_PREC_FP64 && prec != SLSE_PREC_MIXED_BF16) return SLSE_EINVAL;
   if (prec == SLSE_PREC_MIXED_BF16 && prob->dtype != SLSE_F32) return SLSE_EINVAL;
@@ -492,15 +566,16 @@ slse_status slse_sketch(const slse_problem *prob, int32_t kind, int32_t prec, ui
   int32_t *sigma = reinterpret_cast<int32_t *>(base + L.o_sigma);
   int32_t *pos = reinterpret_cast<int32_t *>(base + L.o_pos);
   CK(launch_draws(Np, seed, Psd, nullptr, sigma, nullptr, base + L.o_big, st));
-  CK(launch_pos_map(sigma, Np, 0, m, pos, st));
+  CK(launch_pos_map(sigma, Np, 0, m, L.sp.single ? L.sp.logN : L.sp.log2, pos, st));
   CK(launch_srht(L.sp, prec, prob->dtype, prob->X, prob->ldx, prob->Y, prob->N, prob->d, Psd, pos, base + L.o_big,
-                 base + L.o_wy, L.ldw, SX, SY, ldsx, 1.0 / std::sqrt((double)m), st));
+                 base + L.o_wy, L.ldw, SX, SY, ldsx, 1.0 / std::sqrt((double)m), st, nullptr));
   return SLSE_OK;
 }
 
 slse_status slse_grad(const slse_problem *prob, const double *beta, double *g_out, int32_t prec, void *workspace,
                       size_t ws_bytes, slse_stream_t stream) {
   if (!valid_problem(prob) || !beta || !g_out) return SLSE_EINVAL;
+  if (is_host_pointer(prob->X) || is_host_pointer(prob->Y) || is_host_pointer(beta)) return SLSE_EINVAL;
   if (prec != SLSE_PREC_FP64 && prec != SLSE_PREC_MIXED_BF16) return SLSE_EINVAL;
   if (prec == SLSE_PREC_MIXED_BF16 && prob->dtype != SLSE_F32) return SLSE_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;

@@ -129,10 +129,14 @@ __global__ void k_fold_signs(int64_t Np, uint32_t k0, uint32_t k1, const int32_t
   if (D_out) D_out[j] = neg ? (int8_t)-1 : (int8_t)1;
 }
 
-__global__ void k_pos_scatter(const int32_t *sigma, int64_t s0, int64_t s1, int32_t *pos) {
+// pos is stored "pass-2-major": output row k = k1 n2 + k2 lives at index k2 n1 + k1, so
+// the rows one pass-2 group writes are contiguous.  log2 = log2 n2 (= log2 N' for one pass).
+__global__ void k_pos_scatter(const int32_t *sigma, int64_t s0, int64_t s1, int log1, int log2, int32_t *pos) {
   const int64_t s = s0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= s1) return;
-  pos[sigma[s]] = (int32_t)s;
+  const int64_t k = sigma[s];
+  const int64_t idx = ((k & ((int64_t(1) << log2) - 1)) << log1) | (k >> log2);
+  pos[idx] = (int32_t)s;
 }
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -202,11 +206,13 @@ cudaError_t launch_draws(int64_t Np, uint64_t seed, int32_t *Psd, int32_t *P, in
   return sort_stream(Np, seed, STREAM_SIGMA, w, sigma, s);
 }
 
-cudaError_t launch_pos_map(const int32_t *sigma, int64_t Np, int64_t s0, int64_t s1, int32_t *pos, cudaStream_t s) {
+cudaError_t launch_pos_map(const int32_t *sigma, int64_t Np, int64_t s0, int64_t s1, int log2, int32_t *pos,
+                           cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(pos, 0xFF, 4 * (size_t)Np, s);
   if (e != cudaSuccess || s1 <= s0) return e;
   const int T = 256;
-  k_pos_scatter<<<(unsigned)((s1 - s0 + T - 1) / T), T, 0, s>>>(sigma, s0, s1, pos);
+  const int log1 = log2_exact(Np) - log2;
+  k_pos_scatter<<<(unsigned)((s1 - s0 + T - 1) / T), T, 0, s>>>(sigma, s0, s1, log1, log2, pos);
   return cudaGetLastError();
 }
 

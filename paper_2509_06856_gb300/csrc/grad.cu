@@ -157,8 +157,13 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_f64(const GradArgs a) {
 }
 
 // ---------------------------------------------------------------- 1st stage on BF16 sketch
-template <int VW, int VMAX>
-__global__ void __launch_bounds__(kGradThreads) k_grad_bf16(const GradArgs a) {
+// RPW consecutive rows per warp iteration (independent loads in flight); the BF16
+// words stay packed in registers and are widened at use (exact).
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
+
+template <int VMAX, int RPW>
+__global__ void __launch_bounds__(kGradThreads, 2) k_grad_bf16v(const GradArgs a) {
   __shared__ double sm[kWarps][512];
   if (a.check_done && a.st->done) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -167,161 +172,260 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_bf16(const GradArgs a) {
   const double *beta = a.beta_ring + (size_t)(a.st->iter % 3) * d;
   const __nv_bfloat16 *U = static_cast<const __nv_bfloat16 *>(a.X);
   const __nv_bfloat16 *V = static_cast<const __nv_bfloat16 *>(a.Y);
-  float b[VMAX][VW], g[VMAX][VW];
+  float b[VMAX][8], g[VMAX][8];
 #pragma unroll
   for (int v = 0; v < VMAX; ++v)
 #pragma unroll
-    for (int e = 0; e < VW; ++e) {
-      const int col = (v * 32 + lane) * VW + e;
+    for (int e = 0; e < 8; ++e) {
+      const int col = (v * 32 + lane) * 8 + e;
       b[v][e] = col < d ? (float)beta[col] : 0.f;
       g[v][e] = 0.f;
     }
-  for (int64_t i = gw; i < a.nrows; i += nw) {
-    const __nv_bfloat16 *row = U + i * a.ldx;
-    float x[VMAX][VW];
+  for (int64_t i0 = gw * RPW; i0 < a.nrows; i0 += nw * RPW) {
+    uint4 raw[RPW][VMAX];
+    float y[RPW];
 #pragma unroll
-    for (int v = 0; v < VMAX; ++v) {
-      const int col0 = (v * 32 + lane) * VW;
-      float t[VW];
-      if constexpr (VW == 8) {
-        if (col0 < d) load_bf16x8(row + col0, t);
-        else {
+    for (int q = 0; q < RPW; ++q) {
+      const int64_t i = i0 + q;
+      const bool rv = i < a.nrows;
 #pragma unroll
-          for (int e = 0; e < VW; ++e) t[e] = 0.f;
-        }
-      } else {
-        t[0] = col0 < d ? __bfloat162float(row[col0]) : 0.f;
+      for (int v = 0; v < VMAX; ++v) {
+        const int col0 = (v * 32 + lane) * 8;
+        raw[q][v] = (rv && col0 < d) ? __ldg(reinterpret_cast<const uint4 *>(U + i * a.ldx + col0))
+                                     : make_uint4(0u, 0u, 0u, 0u);
       }
-#pragma unroll
-      for (int e = 0; e < VW; ++e) x[v][e] = (col0 + e < d) ? t[e] : 0.f;
+      y[q] = rv ? __bfloat162float(V[i]) : 0.f;
     }
-    float s = 0.f;
+    float s[RPW];
 #pragma unroll
-    for (int v = 0; v < VMAX; ++v)
+    for (int q = 0; q < RPW; ++q) {
+      float acc = 0.f;
 #pragma unroll
-      for (int e = 0; e < VW; ++e) s = fmaf(x[v][e], b[v][e], s);
-    s = warp_sum(s);
-    const float r = __bfloat162float(V[i]) - s;
+      for (int v = 0; v < VMAX; ++v) {
+        const uint32_t w[4] = {raw[q][v].x, raw[q][v].y, raw[q][v].z, raw[q][v].w};
 #pragma unroll
-    for (int v = 0; v < VMAX; ++v)
+        for (int k = 0; k < 4; ++k) {
+          acc = fmaf(bf_lo(w[k]), b[v][2 * k], acc);
+          acc = fmaf(bf_hi(w[k]), b[v][2 * k + 1], acc);
+        }
+      }
+      s[q] = acc;
+    }
 #pragma unroll
-      for (int e = 0; e < VW; ++e) g[v][e] = fmaf(x[v][e], r, g[v][e]);
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+      const float r = y[q] - s[q];  // padding columns are zero words, padding rows are zero
+#pragma unroll
+      for (int v = 0; v < VMAX; ++v) {
+        const uint32_t w[4] = {raw[q][v].x, raw[q][v].y, raw[q][v].z, raw[q][v].w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          g[v][2 * k] = fmaf(bf_lo(w[k]), r, g[v][2 * k]);
+          g[v][2 * k + 1] = fmaf(bf_hi(w[k]), r, g[v][2 * k + 1]);
+        }
+      }
+    }
   }
 #pragma unroll
   for (int v = 0; v < VMAX; ++v)
 #pragma unroll
-    for (int e = 0; e < VW; ++e) {
-      const int col = (v * 32 + lane) * VW + e;
+    for (int e = 0; e < 8; ++e) {
+      const int col = (v * 32 + lane) * 8 + e;
       if (col < d) sm[warp][col] = (double)g[v][e];
     }
   cta_partial(sm, d, a.partials + (size_t)blockIdx.x * d);
 }
 
-// ---------------------------------------------------------------- mixed 2nd stage (X F32)
-template <int VW, int VMAX>
-__global__ void __launch_bounds__(kGradThreads) k_grad_mixed(const GradArgs a) {
+// Scalar-load variant for sketches whose rows are not 16-byte aligned.
+template <int VMAX>
+__global__ void __launch_bounds__(kGradThreads) k_grad_bf16s(const GradArgs a) {
   __shared__ double sm[kWarps][512];
   if (a.check_done && a.st->done) return;
-  const int rebase = a.st->rebase;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * kWarps + warp, nw = (int64_t)gridDim.x * kWarps;
+  const int d = a.d;
+  const double *beta = a.beta_ring + (size_t)(a.st->iter % 3) * d;
+  const __nv_bfloat16 *U = static_cast<const __nv_bfloat16 *>(a.X);
+  const __nv_bfloat16 *V = static_cast<const __nv_bfloat16 *>(a.Y);
+  float b[VMAX], g[VMAX];
+#pragma unroll
+  for (int v = 0; v < VMAX; ++v) {
+    const int col = v * 32 + lane;
+    b[v] = col < d ? (float)beta[col] : 0.f;
+    g[v] = 0.f;
+  }
+  for (int64_t i = gw; i < a.nrows; i += nw) {
+    float x[VMAX];
+#pragma unroll
+    for (int v = 0; v < VMAX; ++v) {
+      const int col = v * 32 + lane;
+      x[v] = col < d ? __bfloat162float(U[i * a.ldx + col]) : 0.f;
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int v = 0; v < VMAX; ++v) s = fmaf(x[v], b[v], s);
+    s = warp_sum(s);
+    const float r = __bfloat162float(V[i]) - s;
+#pragma unroll
+    for (int v = 0; v < VMAX; ++v) g[v] = fmaf(x[v], r, g[v]);
+  }
+#pragma unroll
+  for (int v = 0; v < VMAX; ++v) {
+    const int col = v * 32 + lane;
+    if (col < d) sm[warp][col] = (double)g[v];
+  }
+  cta_partial(sm, d, a.partials + (size_t)blockIdx.x * d);
+}
+
+// ---------------------------------------------------------------- mixed 2nd stage (X F32)
+// REBASE = 1: error-free residual against beta (FP64) and r0 written; REBASE = 0:
+// residual r0 - x . delta32.  The host launches both; the one whose mode does not
+// match st->rebase returns at once.  The two-word accumulators (hi, lo) of each
+// warp live in shared memory (float2 per column), folded every kFlushRows rows.
+template <int VW, int VMAX, int REBASE, int RPW>
+__global__ void __launch_bounds__(kGradThreads, 2) k_grad_mixed(const GradArgs a) {
+  __shared__ __align__(16) double sm[kWarps][512];
+  if (a.check_done && a.st->done) return;
+  if ((a.st->rebase != 0) != (REBASE != 0)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * kWarps + warp, nw = (int64_t)gridDim.x * kWarps;
   const int d = a.d;
   const double *beta = a.beta_ring + (size_t)(a.st->iter % 3) * d;
   const float *X = static_cast<const float *>(a.X);
   const float *Y = static_cast<const float *>(a.Y);
-  float bh[VMAX][VW], bl[VMAX][VW];
-  float gacc[VMAX][VW], ghi[VMAX][VW], glo[VMAX][VW];
+  float2 *acc = reinterpret_cast<float2 *>(&sm[warp][0]);  // (hi, lo) per column, this warp only
+  for (int c = lane; c < 512; c += 32) acc[c] = make_float2(0.f, 0.f);
+  float bh[VMAX][VW], bl[REBASE ? VMAX : 1][VW];
+  float gacc[VMAX][VW];
 #pragma unroll
   for (int v = 0; v < VMAX; ++v)
 #pragma unroll
     for (int e = 0; e < VW; ++e) {
       const int col = (v * 32 + lane) * VW + e;
-      if (rebase) {
+      if constexpr (REBASE) {
         const double bd = col < d ? beta[col] : 0.0;
         bh[v][e] = (float)bd;
         bl[v][e] = (float)(bd - (double)bh[v][e]);
       } else {
         bh[v][e] = col < d ? a.delta32[col] : 0.f;
-        bl[v][e] = 0.f;
       }
-      gacc[v][e] = 0.f; ghi[v][e] = 0.f; glo[v][e] = 0.f;
+      gacc[v][e] = 0.f;
     }
+  __syncwarp();
   int nacc = 0;
-  for (int64_t i = gw; i < a.nrows; i += nw) {
-    const float *row = X + i * a.ldx;
-    float x[VMAX][VW];
+  for (int64_t i0 = gw * RPW; i0 < a.nrows; i0 += nw * RPW) {
+    float x[RPW][VMAX][VW];
+    float yr[RPW];
 #pragma unroll
-    for (int v = 0; v < VMAX; ++v) {
-      const int col0 = (v * 32 + lane) * VW;
-      float t[VW];
-      if (col0 < d) Vec<float, VW>::load(row + col0, t, true);
-      else {
+    for (int q = 0; q < RPW; ++q) {
+      const int64_t i = i0 + q;
+      const bool rv = i < a.nrows;
+      const float *row = X + (rv ? i : 0) * a.ldx;
 #pragma unroll
-        for (int e = 0; e < VW; ++e) t[e] = 0.f;
-      }
+      for (int v = 0; v < VMAX; ++v) {
+        const int col0 = (v * 32 + lane) * VW;
+        float t[VW];
+        if (rv && col0 < d) Vec<float, VW>::load(row + col0, t, true);
+        else {
 #pragma unroll
-      for (int e = 0; e < VW; ++e) x[v][e] = (col0 + e < d) ? t[e] : 0.f;
-    }
-    float r;
-    if (rebase) {
-      // Dot2 (Ogita, Rump, Oishi 2005): s + c = x . (bh + bl) with error-free products/sums
-      float s = 0.f, c = 0.f;
-#pragma unroll
-      for (int v = 0; v < VMAX; ++v)
-#pragma unroll
-        for (int e = 0; e < VW; ++e) {
-          float p, pe, se;
-          two_prod(x[v][e], bh[v][e], p, pe);
-          two_sum(s, p, s, se);
-          c = fmaf(x[v][e], bl[v][e], c + (pe + se));
+          for (int e = 0; e < VW; ++e) t[e] = 0.f;
         }
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const float s2 = __shfl_xor_sync(0xffffffffu, s, off);
-        const float c2 = __shfl_xor_sync(0xffffffffu, c, off);
-        float e;
-        two_sum(s, s2, s, e);
-        c = (c + c2) + e;
+        for (int e = 0; e < VW; ++e) x[q][v][e] = (col0 + e < d) ? t[e] : 0.f;
       }
-      float rh, re;
-      two_sum(Y[i], -s, rh, re);
-      r = rh + (re - c);
-      if (a.r0 && lane == 0) a.r0[i] = r;
+      yr[q] = rv ? (REBASE ? __ldcs(Y + i) : __ldcs(a.r0 + i)) : 0.f;
+    }
+    float r[RPW];
+    if constexpr (REBASE) {
+      // Dot2 (Ogita, Rump, Oishi 2005): s + c = x . (bh + bl) with error-free products/sums
+      float s[RPW], c[RPW];
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) {
+        s[q] = 0.f;
+        c[q] = 0.f;
+#pragma unroll
+        for (int v = 0; v < VMAX; ++v)
+#pragma unroll
+          for (int e = 0; e < VW; ++e) {
+            float p, pe, se;
+            two_prod(x[q][v][e], bh[v][e], p, pe);
+            two_sum(s[q], p, s[q], se);
+            c[q] = fmaf(x[q][v][e], bl[v][e], c[q] + (pe + se));
+          }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+          const float s2 = __shfl_xor_sync(0xffffffffu, s[q], off);
+          const float c2 = __shfl_xor_sync(0xffffffffu, c[q], off);
+          float e;
+          two_sum(s[q], s2, s[q], e);
+          c[q] = (c[q] + c2) + e;
+        }
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) {
+        float rh, re;
+        two_sum(yr[q], -s[q], rh, re);
+        r[q] = rh + (re - c[q]);
+        if (a.r0 && lane == 0 && i0 + q < a.nrows) a.r0[i0 + q] = r[q];
+      }
     } else {
-      float s = 0.f;
+      float s[RPW];
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) {
+        s[q] = 0.f;
+#pragma unroll
+        for (int v = 0; v < VMAX; ++v)
+#pragma unroll
+          for (int e = 0; e < VW; ++e) s[q] = fmaf(x[q][v][e], bh[v][e], s[q]);
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) r[q] = yr[q] - s[q];
+    }
+#pragma unroll
+    for (int q = 0; q < RPW; ++q)
 #pragma unroll
       for (int v = 0; v < VMAX; ++v)
 #pragma unroll
-        for (int e = 0; e < VW; ++e) s = fmaf(x[v][e], bh[v][e], s);
-      s = warp_sum(s);
-      r = __ldg(a.r0 + i) - s;
-    }
-#pragma unroll
-    for (int v = 0; v < VMAX; ++v)
-#pragma unroll
-      for (int e = 0; e < VW; ++e) gacc[v][e] = fmaf(x[v][e], r, gacc[v][e]);
-    if (++nacc == kFlushRows) {
+        for (int e = 0; e < VW; ++e) gacc[v][e] = fmaf(x[q][v][e], r[q], gacc[v][e]);
+    nacc += RPW;
+    if (nacc >= kFlushRows) {
       nacc = 0;
 #pragma unroll
       for (int v = 0; v < VMAX; ++v)
 #pragma unroll
         for (int e = 0; e < VW; ++e) {
-          float s, err;
-          two_sum(ghi[v][e], gacc[v][e], s, err);
-          ghi[v][e] = s;
-          glo[v][e] += err;
+          const int col = (v * 32 + lane) * VW + e;
+          if (col < 512) {
+            float2 h = acc[col];
+            float sum, err;
+            two_sum(h.x, gacc[v][e], sum, err);
+            acc[col] = make_float2(sum, h.y + err);
+          }
           gacc[v][e] = 0.f;
         }
     }
   }
+  // fold the remainder and convert each (hi, lo) pair in place to one double
 #pragma unroll
   for (int v = 0; v < VMAX; ++v)
 #pragma unroll
     for (int e = 0; e < VW; ++e) {
       const int col = (v * 32 + lane) * VW + e;
-      if (col < d) sm[warp][col] = ((double)ghi[v][e] + (double)gacc[v][e]) + (double)glo[v][e];
+      if (col < 512) {
+        const float2 h = acc[col];
+        sm[warp][col] = ((double)h.x + (double)gacc[v][e]) + (double)h.y;
+      }
     }
-  if (rebase && a.beta0 && blockIdx.x == 0) {
+  if (REBASE && a.beta0 && blockIdx.x == 0) {
     for (int c = threadIdx.x; c < d; c += blockDim.x) a.beta0[c] = beta[c];
     if (threadIdx.x == 0) a.st->rebases += 1;
   }
@@ -461,12 +565,17 @@ cudaError_t launch_grad(int mode, int xdtype, const void *X, int64_t ldx, const 
         return launch1(k_grad_f64<float, 1, 16>, nblk, a, s);
       }
     case GM_STAGE1_BF16:
-      if (ldx % 8 == 0 && aligned(X, ldx, 2, 8)) return launch1(k_grad_bf16<8, 2>, nblk, a, s);
-      return launch1(k_grad_bf16<1, 16>, nblk, a, s);
-    case GM_MIXED:
+      // the sketch buffer's padding columns are never written: the vector path requires
+      // d % 8 == 0 so that no padding word is read
+      if (d % 8 == 0 && ldx % 8 == 0 && aligned(X, ldx, 2, 8)) return launch1(k_grad_bf16v<2, 4>, nblk, a, s);
+      return launch1(k_grad_bf16s<16>, nblk, a, s);
+    case GM_MIXED: {
       if (xdtype != SLSE_F32) return cudaErrorInvalidValue;
-      if (d % 4 == 0 && aligned(X, ldx, 4, 4)) return launch1(k_grad_mixed<4, 4>, nblk, a, s);
-      return launch1(k_grad_mixed<1, 16>, nblk, a, s);
+      const bool vec = d % 4 == 0 && aligned(X, ldx, 4, 4);
+      cudaError_t e = vec ? launch1(k_grad_mixed<4, 4, 1, 2>, nblk, a, s) : launch1(k_grad_mixed<1, 16, 1, 1>, nblk, a, s);
+      if (e != cudaSuccess) return e;
+      return vec ? launch1(k_grad_mixed<4, 4, 0, 2>, nblk, a, s) : launch1(k_grad_mixed<1, 16, 0, 1>, nblk, a, s);
+    }
     default:
       return cudaErrorInvalidValue;
   }

@@ -20,39 +20,66 @@ struct QrArgs {
   int64_t r, lda;
   int d;
   double *R;
+  double *Rt;    // R^T (d x d), nullable
   double *red;   // 2 x G x d
   double *fin;   // 2 x d
   double *piv;   // 2 x d
   DevState *st;
 };
 
+// Rows of each CTA live in shared memory for the whole factorisation (SMEM = true)
+// when they fit; otherwise they stay in global memory.
+template <bool SMEM>
 __global__ void __launch_bounds__(kQrThreads) k_qr(const QrArgs a) {
+  extern __shared__ double sA[];
   const int G = gridDim.x, b = blockIdx.x;
   const int d = a.d;
   const int64_t r = a.r;
   const int64_t rb0 = (r * b) / G, rb1 = (r * (b + 1)) / G;
+  const int nr = (int)(rb1 - rb0);
   double *A = a.A;
+  // own row i lives at rowp(i)[0..d)
+  const int64_t ld = SMEM ? d : a.lda;
+  double *own = SMEM ? sA : A + rb0 * a.lda;
+  if (SMEM) {
+    for (int64_t e = threadIdx.x; e < (int64_t)nr * d; e += kQrThreads)
+      sA[e] = A[(rb0 + e / d) * a.lda + e % d];
+    __syncthreads();
+  }
   for (int j = 0; j < d; ++j) {
     const int nc = d - j;
     const int buf = j & 1;
     double *red = a.red + (size_t)buf * G * d;
     double *fin = a.fin + (size_t)buf * d;
     double *piv = a.piv + (size_t)buf * d;
-    const int64_t lo = rb0 > j ? rb0 : j;
+    const int lo = (int)((rb0 > j ? rb0 : j) - rb0);
+    const bool has_j = j >= rb0 && j < rb1;
     // phase 1: partial dot products of column j with columns j..d-1 over own rows
     for (int c = threadIdx.x; c < nc; c += kQrThreads) {
       double s = 0.0;
-      for (int64_t i = lo; i < rb1; ++i) s = fma(A[i * a.lda + j], A[i * a.lda + j + c], s);
+      for (int i = lo; i < nr; ++i) s = fma(own[i * ld + j], own[i * ld + j + c], s);
       red[(size_t)b * d + c] = s;
-      if (j >= rb0 && j < rb1) piv[c] = A[(int64_t)j * a.lda + j + c];
+      if (has_j) piv[c] = own[(j - rb0) * ld + j + c];
     }
     if (!grid_barrier(a.st, G)) return;
-    // phase 2: CTA b sums a slice of the columns over all CTAs (fixed order)
-    const int c0 = (int)(((int64_t)nc * b) / G), c1 = (int)(((int64_t)nc * (b + 1)) / G);
-    for (int c = c0 + threadIdx.x; c < c1; c += kQrThreads) {
-      double s = 0.0;
-      for (int q = 0; q < G; ++q) s += __ldcg(red + (size_t)q * d + c);
-      fin[c] = s;
+    // phase 2: CTA b sums a slice of the columns over all CTAs; each column is summed by
+    // 64 threads (strided partials, then a fixed-order shuffle/shared-memory tree)
+    {
+      __shared__ double s_red[kQrThreads / 32];
+      const int c0 = (int)(((int64_t)nc * b) / G), c1 = (int)(((int64_t)nc * (b + 1)) / G);
+      const int sub = threadIdx.x & 63, grp = threadIdx.x >> 6;
+      for (int cb = c0; cb < c1; cb += kQrThreads / 64) {
+        const int c = cb + grp;
+        double s = 0.0;
+        if (c < c1)
+          for (int q = sub; q < G; q += 64) s += __ldcg(red + (size_t)q * d + c);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (sub == 0 && c < c1) fin[c] = s_red[2 * grp] + s_red[2 * grp + 1];
+        __syncthreads();
+      }
     }
     if (!grid_barrier(a.st, G)) return;
     // phase 3: Householder reflector from column j, applied to own rows
@@ -64,49 +91,80 @@ __global__ void __launch_bounds__(kQrThreads) k_qr(const QrArgs a) {
       const double vj = ajj - alpha;
       const double tau = 1.0 / (nrm * (nrm + fabs(ajj)));  // 2 / v^T v
       for (int c = 1 + threadIdx.x; c < nc; c += kQrThreads) {
-        const double w = __ldcg(fin + c) - alpha * __ldcg(piv + c);  // v^T A[:, j+c]
-        const double tw = tau * w;
-        for (int64_t i = lo; i < rb1; ++i) {
-          const double vi = (i == j) ? vj : A[i * a.lda + j];
-          A[i * a.lda + j + c] -= vi * tw;
+        const double tw = tau * (__ldcg(fin + c) - alpha * __ldcg(piv + c));  // tau * v^T A[:, j+c]
+        for (int i = lo; i < nr; ++i) {
+          const double vi = (i + rb0 == j) ? vj : own[i * ld + j];
+          own[i * ld + j + c] -= vi * tw;
         }
       }
       __syncthreads();
-      if (threadIdx.x == 0 && j >= rb0 && j < rb1) A[(int64_t)j * a.lda + j] = alpha;
+      if (threadIdx.x == 0 && has_j) own[(j - rb0) * ld + j] = alpha;
     } else if (threadIdx.x == 0 && b == 0) {
       atomicOr(&a.st->status, ST_NUMERIC);
     }
     __syncthreads();
   }
+  if (SMEM) {  // rows < d hold R: write them back
+    for (int64_t e = threadIdx.x; e < (int64_t)nr * d; e += kQrThreads) {
+      const int64_t i = rb0 + e / d;
+      if (i < d) A[i * a.lda + e % d] = sA[e];
+    }
+  }
   if (!grid_barrier(a.st, G)) return;
-  // R = upper triangle of A[0:d, 0:d] with rows scaled to a non-negative diagonal
+  // R = upper triangle of A[0:d, 0:d] with rows scaled to a non-negative diagonal; Rt = R^T
   for (int64_t e = (int64_t)b * kQrThreads + threadIdx.x; e < (int64_t)d * d; e += (int64_t)G * kQrThreads) {
     const int i = (int)(e / d), k = (int)(e % d);
     const double diag = __ldcg(A + (int64_t)i * a.lda + i);
     const double sgn = diag < 0.0 ? -1.0 : 1.0;
-    a.R[e] = k >= i ? sgn * __ldcg(A + (int64_t)i * a.lda + k) : 0.0;
+    const double v = k >= i ? sgn * __ldcg(A + (int64_t)i * a.lda + k) : 0.0;
+    a.R[e] = v;
+    if (a.Rt) a.Rt[(int64_t)k * d + i] = v;
   }
 }
 
-// Column k of R^{-1}: back substitution R x = e_k, one warp per column.
-__global__ void __launch_bounds__(256) k_tri_inv(const double *R, int d, double *Rinv, DevState *st) {
-  extern __shared__ double sx[];
+// Column k of R^{-1} by column sweep: x_i = b_i / R_ii, then b[0:i) -= x_i R[0:i, i],
+// for i = k..0, one warp per column.  b is spread over the lanes (b[32t + lane] in
+// register t); the critical path per step is one shuffle and one multiply.
+__global__ void __launch_bounds__(256) k_tri_inv_sweep(const double *R, const double *Rt, int d, double *Rinv,
+                                                       DevState *st) {
+  __shared__ double s_rdiag[512];
+  for (int i = threadIdx.x; i < d; i += blockDim.x) {
+    const double rii = R[(size_t)i * d + i];
+    if (rii == 0.0) atomicOr(&st->status, ST_NUMERIC);
+    s_rdiag[i] = 1.0 / rii;
+  }
+  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int k = blockIdx.x * 8 + warp;
   if (k >= d) return;
-  double *x = sx + (size_t)warp * d;
-  for (int i = k; i >= 0; --i) {
-    double s = 0.0;
-    for (int l = i + 1 + lane; l <= k; l += 32) s = fma(R[(size_t)i * d + l], x[l], s);
+  double bv[16], xv[16];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    const double rii = R[(size_t)i * d + i];
-    const double xi = ((i == k ? 1.0 : 0.0) - s) / rii;
-    if (lane == 0) x[i] = xi;
-    __syncwarp();
-    if (rii == 0.0 && lane == 0) atomicOr(&st->status, ST_NUMERIC);
+  for (int t = 0; t < 16; ++t) {
+    bv[t] = (32 * t + lane == k) ? 1.0 : 0.0;
+    xv[t] = 0.0;
   }
-  for (int i = lane; i < d; i += 32) Rinv[(size_t)i * d + k] = i <= k ? x[i] : 0.0;
+#pragma unroll
+  for (int t = 15; t >= 0; --t) {
+    if (32 * t > k) continue;
+    const int top = (k - 32 * t) < 31 ? (k - 32 * t) : 31;
+#pragma unroll 4
+    for (int ln = top; ln >= 0; --ln) {
+      const int i = 32 * t + ln;
+      const double xi = __shfl_sync(0xffffffffu, bv[t], ln) * s_rdiag[i];
+      if (lane == ln) xv[t] = xi;
+      const double *col = Rt + (size_t)i * d;  // column i of R
+#pragma unroll
+      for (int tt = 0; tt <= t; ++tt) {
+        const int l = 32 * tt + lane;
+        if (l < i) bv[tt] = fma(-xi, col[l], bv[tt]);
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < 16; ++t) {
+    const int l = 32 * t + lane;
+    if (l < d) Rinv[(size_t)l * d + k] = l <= k ? xv[t] : 0.0;
+  }
 }
 
 // Hinv[i][k] = sum_{l >= max(i,k)} Rinv[i][l] Rinv[k][l], 32 x 32 output tiles.
@@ -168,7 +226,7 @@ int qr_grid(int64_t r, int nsm) {
 
 size_t qr_ws_bytes(int64_t r, int d, int nsm) {
   const int G = qr_grid(r, nsm);
-  return align256(2 * (size_t)G * d * 8) + 2 * align256(2 * (size_t)d * 8) + align256((size_t)d * d * 8);
+  return align256(2 * (size_t)G * d * 8) + 2 * align256(2 * (size_t)d * 8) + 2 * align256((size_t)d * d * 8);
 }
 
 cudaError_t launch_gather_hessian_rows(int prec, const void *U, int64_t ldu, int64_t row0, int64_t r, int d,
@@ -190,9 +248,18 @@ cudaError_t launch_qr(double *A, int64_t r, int d, int64_t lda, double *R, doubl
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  int G = qr_grid(r, nsm);
+  const int G = qr_grid(r, nsm);
+  const int64_t nr_max = (r + G - 1) / G;
+  const size_t smem = (size_t)nr_max * d * sizeof(double);
+  const bool use_smem = smem <= (size_t)200 * 1024;
+  auto kern = use_smem ? k_qr<true> : k_qr<false>;
+  const size_t dyn = use_smem ? smem : 0;
+  if (use_smem) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+  }
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qr, kQrThreads, 0);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kQrThreads, dyn);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   char *p = static_cast<char *>(ws);
@@ -207,15 +274,13 @@ cudaError_t launch_qr(double *A, int64_t r, int d, int64_t lda, double *R, doubl
   a.fin = reinterpret_cast<double *>(p + off); off += align256(2 * (size_t)d * 8);
   a.piv = reinterpret_cast<double *>(p + off); off += align256(2 * (size_t)d * 8);
   double *Rinv = reinterpret_cast<double *>(p + off); off += align256((size_t)d * d * 8);
+  a.Rt = reinterpret_cast<double *>(p + off); off += align256((size_t)d * d * 8);
   a.st = st;
   void *args[] = {&a};
-  e = cudaLaunchCooperativeKernel((const void *)k_qr, dim3(G), dim3(kQrThreads), args, 0, s);
+  e = cudaLaunchCooperativeKernel((const void *)kern, dim3(G), dim3(kQrThreads), args, dyn, s);
   if (e != cudaSuccess) return e;
   if (Hinv) {
-    const size_t smem = (size_t)8 * d * sizeof(double);
-    e = cudaFuncSetAttribute(k_tri_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_tri_inv<<<(d + 7) / 8, 256, smem, s>>>(R, d, Rinv, st);
+    k_tri_inv_sweep<<<(d + 7) / 8, 256, 0, s>>>(R, a.Rt, d, Rinv, st);
     const int nt = (d + 31) / 32;
     k_form_hinv<<<dim3(nt, nt), 256, 0, s>>>(Rinv, d, Hinv);
   }

@@ -83,9 +83,9 @@ __device__ __forceinline__ bool grid_barrier(DevState *st, unsigned nblocks) {
     } else {
       long long spins = 0;
       while (*genp == g) {
-        __nanosleep(64);
-        if (++spins > (1ll << 24)) { atomicOr(&st->status, ST_TIMEOUT); ok = 0; break; }
-        if (((volatile unsigned *)&st->status)[0] & ST_TIMEOUT) { ok = 0; break; }
+        if (spins > 512) __nanosleep(32);
+        if (++spins > (1ll << 25)) { atomicOr(&st->status, ST_TIMEOUT); ok = 0; break; }
+        if ((spins & 255) == 0 && (((volatile unsigned *)&st->status)[0] & ST_TIMEOUT)) { ok = 0; break; }
       }
     }
     __threadfence();
@@ -104,7 +104,9 @@ size_t draws_ws_bytes(int64_t Np);
 cudaError_t launch_draws(int64_t Np, uint64_t seed, int32_t *Psd /*N', sign-folded P*/,
                          int32_t *P /*nullable*/, int32_t *sigma, int8_t *D /*nullable*/,
                          void *ws, cudaStream_t s);
-cudaError_t launch_pos_map(const int32_t *sigma, int64_t Np, int64_t s0, int64_t s1, int32_t *pos,
+// pos[idx(k)] = s for k = sigma[s], s in [s0, s1), -1 elsewhere; idx(k) = (k mod n2) n1 + k div n2
+// with n2 = 2^log2 (the pass-1 group size; log2 = log2 N' for single-pass plans).
+cudaError_t launch_pos_map(const int32_t *sigma, int64_t Np, int64_t s0, int64_t s1, int log2, int32_t *pos,
                            cudaStream_t s);
 
 // srht.cu
@@ -119,7 +121,7 @@ SrhtPlan srht_plan(int64_t Np);
 cudaError_t launch_srht(const SrhtPlan &pl, int prec, int xdtype, const void *X, int64_t ldx,
                         const void *Y, int64_t N, int d, const int32_t *Psd, const int32_t *pos,
                         void *W, void *WY, int64_t ldw, void *U, void *V, int64_t ldu, double scale,
-                        cudaStream_t s);
+                        cudaStream_t s, cudaEvent_t ev_mid /* nullable: recorded between the passes */);
 
 // grad.cu
 enum GradMode { GM_F64 = 0, GM_MIXED = 1, GM_STAGE1_BF16 = 2, GM_STAGE1_F64 = 3 };

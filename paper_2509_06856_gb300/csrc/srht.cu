@@ -46,6 +46,7 @@ struct GroupArgs {
   int d;
   int nslab;
   int logq;
+  int vec_in, vec_out;  // 1: rows allow VEC-wide vector access
   double scale;
 };
 
@@ -57,45 +58,76 @@ template <class Ts, class Tin> __device__ __forceinline__ Ts load_cvt(const Tin 
   if constexpr (sizeof(Ts) == 8) return (Ts)(*p);
   else return to_f<Tin>(*p);
 }
-template <> __device__ __forceinline__ double load_cvt<double, __nv_bfloat16>(const __nv_bfloat16 *p) {
-  return (double)__bfloat162float(*p);
-}
 
 template <class Tout, class Ts> __device__ __forceinline__ void store_cvt(Tout *p, Ts v) {
   if constexpr (sizeof(Tout) == 2) *p = __float2bfloat16_rn((float)v);
   else *p = (Tout)v;
 }
 
-template <class Ts, class Tin>
-__device__ __forceinline__ Ts load_elem(const GroupArgs &a, int64_t g, int64_t rho, int col) {
-  const int64_t j = rho * a.istride + g * a.igstride;
-  int64_t src = j;
-  bool neg = false;
-  if (a.Psd) {
-    const int32_t v = __ldg(a.Psd + j);
-    neg = v < 0;
-    src = neg ? (int64_t)(~v) : (int64_t)v;
-    if (src >= a.N) return Ts(0);
+// VEC consecutive elements of type Tin as working type Ts (one vector load).
+template <class Tin, class Ts, int VEC>
+__device__ __forceinline__ void load_vec(const Tin *p, Ts (&o)[VEC]) {
+  if constexpr (sizeof(Tin) == 4 && VEC == 4) {
+    const float4 t = __ldcs(reinterpret_cast<const float4 *>(p));
+    o[0] = (Ts)t.x; o[1] = (Ts)t.y; o[2] = (Ts)t.z; o[3] = (Ts)t.w;
+  } else if constexpr (sizeof(Tin) == 2 && VEC == 4) {
+    const uint2 t = __ldcs(reinterpret_cast<const uint2 *>(p));
+    o[0] = (Ts)__uint_as_float(t.x << 16); o[1] = (Ts)__uint_as_float(t.x & 0xFFFF0000u);
+    o[2] = (Ts)__uint_as_float(t.y << 16); o[3] = (Ts)__uint_as_float(t.y & 0xFFFF0000u);
+  } else if constexpr (sizeof(Tin) == 8 && VEC == 2) {
+    const double2 t = __ldcs(reinterpret_cast<const double2 *>(p));
+    o[0] = (Ts)t.x; o[1] = (Ts)t.y;
+  } else if constexpr (sizeof(Tin) == 4 && VEC == 2) {
+    const float2 t = __ldcs(reinterpret_cast<const float2 *>(p));
+    o[0] = (Ts)t.x; o[1] = (Ts)t.y;
+  } else if constexpr (sizeof(Tin) == 2 && VEC == 2) {
+    const uint32_t t = __ldcs(reinterpret_cast<const unsigned int *>(p));
+    o[0] = (Ts)__uint_as_float(t << 16); o[1] = (Ts)__uint_as_float(t & 0xFFFF0000u);
+  } else {
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) o[e] = load_cvt<Ts>(p + e);
   }
-  Ts x;
-  if (col < a.d) x = load_cvt<Ts>(static_cast<const Tin *>(a.in) + src * a.ldin + col);
-  else if (col == a.d) x = load_cvt<Ts>(static_cast<const Tin *>(a.in_y) + src);
-  else x = Ts(0);
-  return neg ? -x : x;
 }
 
-template <class Tout, class Ts>
-__device__ __forceinline__ void store_elem(const GroupArgs &a, int64_t g, int64_t kappa, int col, Ts v) {
-  if (col > a.d) return;
-  const int64_t k = kappa * a.ostride + g * a.ogstride;
-  int64_t dst = k;
-  if (a.pos) {
-    dst = __ldg(a.pos + k);
-    if (dst < 0) return;
+template <class Tout, class Ts, int VEC>
+__device__ __forceinline__ void store_vec(Tout *p, const Ts (&v)[VEC]) {
+  if constexpr (sizeof(Tout) == 2 && VEC == 4) {
+    const __nv_bfloat162 lo = __floats2bfloat162_rn((float)v[0], (float)v[1]);
+    const __nv_bfloat162 hi = __floats2bfloat162_rn((float)v[2], (float)v[3]);
+    uint2 t;
+    t.x = *reinterpret_cast<const uint32_t *>(&lo);
+    t.y = *reinterpret_cast<const uint32_t *>(&hi);
+    *reinterpret_cast<uint2 *>(p) = t;
+  } else if constexpr (sizeof(Tout) == 8 && VEC == 2) {
+    *reinterpret_cast<double2 *>(p) = make_double2((double)v[0], (double)v[1]);
+  } else {
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) store_cvt(p + e, v[e]);
   }
-  v = v * (Ts)a.scale;
-  if (col < a.d) store_cvt(static_cast<Tout *>(a.out) + dst * a.ldout + col, v);
-  else store_cvt(static_cast<Tout *>(a.out_y) + dst, v);
+}
+
+// VEC-wide copy between registers and (distributed) shared memory, 16 bytes at a time.
+template <class Ts, int VEC> __device__ __forceinline__ void smem_load(const Ts *p, Ts (&o)[VEC]) {
+  if constexpr (sizeof(Ts) == 4 && VEC == 4) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+  } else if constexpr (sizeof(Ts) == 8 && VEC == 2) {
+    const double2 t = *reinterpret_cast<const double2 *>(p);
+    o[0] = t.x; o[1] = t.y;
+  } else {
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) o[e] = p[e];
+  }
+}
+template <class Ts, int VEC> __device__ __forceinline__ void smem_store(Ts *p, const Ts (&v)[VEC]) {
+  if constexpr (sizeof(Ts) == 4 && VEC == 4) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else if constexpr (sizeof(Ts) == 8 && VEC == 2) {
+    *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+  } else {
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) p[e] = v[e];
+  }
 }
 
 template <int R, class T> __device__ __forceinline__ void fwht_regs(T (&v)[R]) {
@@ -112,92 +144,237 @@ template <int R, class T> __device__ __forceinline__ void fwht_regs(T (&v)[R]) {
   }
 }
 
-// Group transform: 2^LOGM rows x C columns per CTA, Q = 2^logq CTAs per cluster.
-template <class Tin, class Ts, class Tout, int LOGM, int C, int NT>
-__global__ void __launch_bounds__(NT) k_group(const GroupArgs a) {
+// Group transform of the X columns: 2^LOGM rows x C columns per CTA, Q CTAs per
+// cluster (the group has 2^LOGM * Q rows).  The Y column goes through k_ycol.  Stages:
+//   A: the top S0 = min(5, LOGM) bits of the CTA-local row index, in registers, loaded
+//      from HBM with VA-column vector loads (row offsets and signs staged in shared memory);
+//   B: the remaining low LOGM - S0 bits, VB columns per thread, through the shared tile;
+//   O: the Q cluster bits (rows held by the Q CTAs, read through distributed shared
+//      memory), then scaling, conversion and VO-column vector stores.
+template <class Tin, class Ts, class Tout, int LOGM, int Q, int C, int VA, int VB, int VO, int NT>
+__global__ void __launch_bounds__(NT, 2) k_group(const GroupArgs a) {
   constexpr int M = 1 << LOGM;
-  constexpr int S1 = LOGM <= 5 ? 0 : LOGM / 2;   // low-bit stage
-  constexpr int S0 = LOGM - S1;                  // high-bit stage (first, loads from HBM)
+  constexpr int S0 = LOGM < 5 ? LOGM : 5;
+  constexpr int S1 = LOGM - S0;
   constexpr int RA = 1 << S0, RB = 1 << S1;
+  constexpr int MQ = M / Q;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Ts *tile = reinterpret_cast<Ts *>(smem_raw);
+  int64_t *s_off = reinterpret_cast<int64_t *>(smem_raw + (size_t)M * C * sizeof(Ts));
+  Ts *s_mul = reinterpret_cast<Ts *>(s_off + M);
+  int32_t *s_dst = reinterpret_cast<int32_t *>(s_mul + M);
 
-  const int Q = 1 << a.logq;
-  const int rank = (int)(blockIdx.x & (unsigned)(Q - 1));
-  const int64_t item = (int64_t)(blockIdx.x >> a.logq);
+  const int rank = (int)(blockIdx.x % Q);
+  const int64_t item = (int64_t)(blockIdx.x / Q);
   const int slab = (int)(item % a.nslab);
   const int64_t g = item / a.nslab;
   const int col0 = slab * C;
   const int64_t rho0 = (int64_t)rank * M;
-  const bool direct_out = (Q == 1) && (S1 == 0);
+  const int d = a.d;
+  const Tin *in = static_cast<const Tin *>(a.in);
 
-  // stage A: bits [S1, LOGM) of the local row index; loads the group rows from HBM
-  for (int it = threadIdx.x; it < (C << S1); it += NT) {
-    const int c = it % C, b = it / C;
-    Ts v[RA];
+  // input rows of this CTA: element offset of the row and sign (0 for padding rows)
+  for (int l = threadIdx.x; l < M; l += NT) {
+    const int64_t j = (rho0 + l) * a.istride + g * a.igstride;
+    int64_t src = j;
+    Ts mul = Ts(1);
+    if (a.Psd) {
+      const int32_t v = __ldg(a.Psd + j);
+      src = v < 0 ? (int64_t)(~v) : (int64_t)v;
+      mul = v < 0 ? Ts(-1) : Ts(1);
+      if (src >= a.N) { src = 0; mul = Ts(0); }
+    }
+    s_off[l] = src * a.ldin;
+    s_mul[l] = mul;
+  }
+  // output rows written in stage O: kappa = q M + rank MQ + l', l' < MQ
+  if (a.pos) {
+    for (int e = threadIdx.x; e < M; e += NT) {
+      const int q = e / MQ, lq = e % MQ;
+      const int64_t kappa = (int64_t)q * M + rank * MQ + lq;
+      s_dst[e] = __ldg(a.pos + kappa * a.ostride + g * a.ogstride);
+    }
+  }
+  __syncthreads();
+
+  // stage A
+  const bool fast_in = a.vec_in && col0 + C <= d;
+  for (int it = threadIdx.x; it < ((C / VA) << S1); it += NT) {
+    const int cq = it % (C / VA), b = it / (C / VA);
+    const int col = col0 + cq * VA;
+    Ts v[VA][RA];
+    if (fast_in) {
 #pragma unroll
-    for (int k = 0; k < RA; ++k) v[k] = load_elem<Ts, Tin>(a, g, rho0 + b + (k << S1), col0 + c);
-    fwht_regs<RA, Ts>(v);
-    if (direct_out) {
+      for (int k = 0; k < RA; ++k) {
+        Ts t[VA];
+        load_vec<Tin, Ts, VA>(in + s_off[b + (k << S1)] + col, t);
 #pragma unroll
-      for (int k = 0; k < RA; ++k) store_elem<Tout, Ts>(a, g, rho0 + b + (k << S1), col0 + c, v[k]);
+        for (int e = 0; e < VA; ++e) v[e][k] = t[e];
+      }
     } else {
 #pragma unroll
-      for (int k = 0; k < RA; ++k) tile[(b + (k << S1)) * C + c] = v[k];
+      for (int k = 0; k < RA; ++k) {
+        const int64_t off = s_off[b + (k << S1)];
+#pragma unroll
+        for (int e = 0; e < VA; ++e) v[e][k] = col + e < d ? load_cvt<Ts>(in + off + col + e) : Ts(0);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < RA; ++k) {
+      const Ts mul = s_mul[b + (k << S1)];
+#pragma unroll
+      for (int e = 0; e < VA; ++e) v[e][k] *= mul;
+    }
+#pragma unroll
+    for (int e = 0; e < VA; ++e) fwht_regs<RA, Ts>(v[e]);
+#pragma unroll
+    for (int k = 0; k < RA; ++k) {
+      Ts t[VA];
+#pragma unroll
+      for (int e = 0; e < VA; ++e) t[e] = v[e][k];
+      smem_store<Ts, VA>(tile + (b + (k << S1)) * C + cq * VA, t);
     }
   }
+  // stage B
   if constexpr (S1 > 0) {
     __syncthreads();
-    // stage B: bits [0, S1)
-    for (int it = threadIdx.x; it < (C << S0); it += NT) {
-      const int c = it % C, b = it / C;
-      Ts v[RB];
+    for (int it = threadIdx.x; it < ((C / VB) << S0); it += NT) {
+      const int cq = it % (C / VB), b = it / (C / VB);
+      Ts v[VB][RB];
 #pragma unroll
-      for (int k = 0; k < RB; ++k) v[k] = tile[((b << S1) + k) * C + c];
-      fwht_regs<RB, Ts>(v);
-      if (Q == 1) {
+      for (int k = 0; k < RB; ++k) {
+        Ts t[VB];
+        smem_load<Ts, VB>(tile + ((b << S1) + k) * C + cq * VB, t);
 #pragma unroll
-        for (int k = 0; k < RB; ++k) store_elem<Tout, Ts>(a, g, rho0 + (b << S1) + k, col0 + c, v[k]);
+        for (int e = 0; e < VB; ++e) v[e][k] = t[e];
+      }
+#pragma unroll
+      for (int e = 0; e < VB; ++e) fwht_regs<RB, Ts>(v[e]);
+#pragma unroll
+      for (int k = 0; k < RB; ++k) {
+        Ts t[VB];
+#pragma unroll
+        for (int e = 0; e < VB; ++e) t[e] = v[e][k];
+        smem_store<Ts, VB>(tile + ((b << S1) + k) * C + cq * VB, t);
+      }
+    }
+  }
+  // stage O
+  if constexpr (Q > 1) cg::this_cluster().sync();
+  else __syncthreads();
+  const Ts *rt[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    if constexpr (Q > 1) rt[q] = cg::this_cluster().map_shared_rank(tile, q);
+    else rt[q] = tile;
+  }
+  Tout *out = static_cast<Tout *>(a.out);
+  const Ts scale = (Ts)a.scale;
+  const bool fast_out = a.vec_out && col0 + C <= d;
+  for (int it = threadIdx.x; it < (C / VO) * MQ; it += NT) {
+    const int cq = it % (C / VO), lq = it / (C / VO);
+    const int l = rank * MQ + lq;
+    const int col = col0 + cq * VO;
+    Ts v[VO][Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      Ts t[VO];
+      smem_load<Ts, VO>(rt[q] + l * C + cq * VO, t);
+#pragma unroll
+      for (int e = 0; e < VO; ++e) v[e][q] = t[e];
+    }
+    if constexpr (Q > 1) {
+#pragma unroll
+      for (int e = 0; e < VO; ++e) fwht_regs<Q, Ts>(v[e]);
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int64_t kappa = (int64_t)q * M + l;
+      const int64_t dst = a.pos ? (int64_t)s_dst[q * MQ + lq] : kappa * a.ostride + g * a.ogstride;
+      if (dst < 0) continue;
+      Ts o[VO];
+#pragma unroll
+      for (int e = 0; e < VO; ++e) o[e] = v[e][q] * scale;
+      if (fast_out) {
+        store_vec<Tout, Ts, VO>(out + dst * a.ldout + col, o);
       } else {
 #pragma unroll
-        for (int k = 0; k < RB; ++k) tile[((b << S1) + k) * C + c] = v[k];
+        for (int e = 0; e < VO; ++e)
+          if (col + e < d) store_cvt(out + dst * a.ldout + col + e, o[e]);
       }
     }
   }
-  if (Q > 1) {
-    // cluster stage: the top logq bits of the group row index live in different CTAs
-    cg::cluster_group cl = cg::this_cluster();
-    cl.sync();
-    const int MQ = M >> a.logq;
-    for (int it = threadIdx.x; it < MQ * C; it += NT) {
-      const int c = it % C;
-      const int l = rank * MQ + it / C;
-      Ts v[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        if (q < Q) v[q] = cl.map_shared_rank(tile, q)[l * C + c];
-      }
-#pragma unroll
-      for (int hh = 0; hh < 3; ++hh) {
-        const int h = 1 << hh;
-        if (h < Q) {
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            if (q + h < 8 && (q & h) == 0 && q + h < Q) {
-              const Ts x = v[q], y = v[q + h];
-              v[q] = x + y;
-              v[q + h] = x - y;
-            }
-          }
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        if (q < Q) store_elem<Tout, Ts>(a, g, (int64_t)q * M + l, col0 + c, v[q]);
-      }
+  if constexpr (Q > 1) cg::this_cluster().sync();
+}
+
+// The Y column of one group (2^L <= 4096 rows) per CTA, in shared memory: gather
+// (with signs) or strided read, butterflies level by level, scaled store to the
+// sampled rows.
+template <class Tin, class Ts, class Tout>
+__global__ void __launch_bounds__(512) k_ycol(const GroupArgs a, int L) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Ts *t = reinterpret_cast<Ts *>(smem_raw);
+  const int n = 1 << L;
+  const int64_t g = blockIdx.x;
+  const Tin *in_y = static_cast<const Tin *>(a.in_y);
+  for (int rho = threadIdx.x; rho < n; rho += blockDim.x) {
+    const int64_t j = rho * a.istride + g * a.igstride;
+    Ts v;
+    if (a.Psd) {
+      const int32_t c = __ldg(a.Psd + j);
+      const int64_t src = c < 0 ? (int64_t)(~c) : (int64_t)c;
+      v = src < a.N ? load_cvt<Ts>(in_y + src) : Ts(0);
+      if (c < 0) v = -v;
+    } else {
+      v = load_cvt<Ts>(in_y + j);
     }
-    cl.sync();
+    t[rho] = v;
   }
+  __syncthreads();
+  for (int h = 1; h < n; h <<= 1) {
+    for (int p = threadIdx.x; p < n / 2; p += blockDim.x) {
+      const int i = (p / h) * 2 * h + (p % h);
+      const Ts x = t[i], y = t[i + h];
+      t[i] = x + y;
+      t[i + h] = x - y;
+    }
+    __syncthreads();
+  }
+  Tout *out_y = static_cast<Tout *>(a.out_y);
+  for (int kap = threadIdx.x; kap < n; kap += blockDim.x) {
+    const int64_t k = kap * a.ostride + g * a.ogstride;
+    const int64_t dst = a.pos ? (int64_t)__ldg(a.pos + k) : k;
+    if (dst >= 0) store_cvt(out_y + dst, t[kap] * (Ts)a.scale);
+  }
+}
+
+// Scalar element access for the single-pass kernel (gather through Psd on input,
+// sample map on output).
+template <class Ts, class Tin>
+__device__ __forceinline__ Ts load_elem(const GroupArgs &a, int64_t rho, int col) {
+  int64_t src = rho;
+  bool neg = false;
+  if (a.Psd) {
+    const int32_t v = __ldg(a.Psd + rho);
+    neg = v < 0;
+    src = neg ? (int64_t)(~v) : (int64_t)v;
+    if (src >= a.N) return Ts(0);
+  }
+  Ts x;
+  if (col < a.d) x = load_cvt<Ts>(static_cast<const Tin *>(a.in) + src * a.ldin + col);
+  else if (col == a.d) x = load_cvt<Ts>(static_cast<const Tin *>(a.in_y) + src);
+  else x = Ts(0);
+  return neg ? -x : x;
+}
+
+template <class Tout, class Ts>
+__device__ __forceinline__ void store_elem(const GroupArgs &a, int64_t kappa, int col, Ts v) {
+  if (col > a.d) return;
+  const int64_t dst = a.pos ? (int64_t)__ldg(a.pos + kappa) : kappa;
+  if (dst < 0) return;
+  v = v * (Ts)a.scale;
+  if (col < a.d) store_cvt(static_cast<Tout *>(a.out) + dst * a.ldout + col, v);
+  else store_cvt(static_cast<Tout *>(a.out_y) + dst, v);
 }
 
 // Small transforms (N' <= 2^9): one CTA per column slab holds all N' rows; the
@@ -211,7 +388,7 @@ __global__ void __launch_bounds__(NT) k_small(const GroupArgs a, int logn) {
   const int col0 = slab * C;
   for (int it = threadIdx.x; it < n * C; it += NT) {
     const int c = it % C, rho = it / C;
-    tile[rho * C + c] = load_elem<Ts, Tin>(a, 0, rho, col0 + c);
+    tile[rho * C + c] = load_elem<Ts, Tin>(a, rho, col0 + c);
   }
   __syncthreads();
   for (int h = 1; h < n; h <<= 1) {
@@ -226,18 +403,19 @@ __global__ void __launch_bounds__(NT) k_small(const GroupArgs a, int logn) {
   }
   for (int it = threadIdx.x; it < n * C; it += NT) {
     const int c = it % C, kappa = it / C;
-    store_elem<Tout, Ts>(a, 0, kappa, col0 + c, tile[kappa * C + c]);
+    store_elem<Tout, Ts>(a, kappa, col0 + c, tile[kappa * C + c]);
   }
 }
 
-template <class Tin, class Ts, class Tout, int LOGM, int C>
-cudaError_t launch_group_t(const GroupArgs &a, int64_t ngroups, cudaStream_t s) {
+template <class Tin, class Ts, class Tout, int LOGM, int Q, int C, int VA, int VB, int VO>
+cudaError_t launch_group_t(const GroupArgs &a0, int64_t ngroups, cudaStream_t s) {
   constexpr int NT = 256;
-  const size_t smem = (size_t)(1 << LOGM) * C * sizeof(Ts);
-  auto kern = k_group<Tin, Ts, Tout, LOGM, C, NT>;
+  GroupArgs a = a0;
+  a.nslab = (a.d + C - 1) / C;
+  const size_t smem = (size_t)(1 << LOGM) * (C * sizeof(Ts) + 8 + sizeof(Ts) + 4);
+  auto kern = k_group<Tin, Ts, Tout, LOGM, Q, C, VA, VB, VO, NT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int Q = 1 << a.logq;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(ngroups * a.nslab * Q));
   cfg.blockDim = dim3(NT);
@@ -253,21 +431,30 @@ cudaError_t launch_group_t(const GroupArgs &a, int64_t ngroups, cudaStream_t s) 
   return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
-template <class Tin, class Ts, class Tout, int C>
-cudaError_t launch_pass_t(const GroupArgs &a0, int L, int64_t ngroups, cudaStream_t s) {
-  // L = log2 of the group size; LOGM = min(L, 9) (10 for L = 13), LOGQ = L - LOGM <= 3
-  GroupArgs a = a0;
-  int logm = L <= 9 ? L : (L >= 13 ? 10 : 9);
-  a.logq = L - logm;
-  switch (logm) {
-    case 5: return launch_group_t<Tin, Ts, Tout, 5, C>(a, ngroups, s);
-    case 6: return launch_group_t<Tin, Ts, Tout, 6, C>(a, ngroups, s);
-    case 7: return launch_group_t<Tin, Ts, Tout, 7, C>(a, ngroups, s);
-    case 8: return launch_group_t<Tin, Ts, Tout, 8, C>(a, ngroups, s);
-    case 9: return launch_group_t<Tin, Ts, Tout, 9, C>(a, ngroups, s);
-    case 10: return launch_group_t<Tin, Ts, Tout, 10, C>(a, ngroups, s);
+// One pass over groups of 2^L rows: the X columns by k_group (256-byte row segments:
+// 64 FP32 / 32 FP64 columns, 256 rows per CTA, clusters of up to 8 CTAs; for L = 12
+// 128-byte segments and 512 rows per CTA), the Y column by k_ycol.
+template <class Tin, class Ts, class Tout, int VA, int VB, int VO>
+cudaError_t launch_pass_t(const GroupArgs &a, int L, int64_t ngroups, cudaStream_t s) {
+  constexpr int CW = 256 / (int)sizeof(Ts);  // columns per 256-byte segment
+  cudaError_t e;
+  switch (L) {
+    case 5: e = launch_group_t<Tin, Ts, Tout, 5, 1, CW, VA, VB, VO>(a, ngroups, s); break;
+    case 6: e = launch_group_t<Tin, Ts, Tout, 6, 1, CW, VA, VB, VO>(a, ngroups, s); break;
+    case 7: e = launch_group_t<Tin, Ts, Tout, 7, 1, CW, VA, VB, VO>(a, ngroups, s); break;
+    case 8: e = launch_group_t<Tin, Ts, Tout, 8, 1, CW, VA, VB, VO>(a, ngroups, s); break;
+    case 9: e = launch_group_t<Tin, Ts, Tout, 8, 2, CW, VA, VB, VO>(a, ngroups, s); break;
+    case 10: e = launch_group_t<Tin, Ts, Tout, 8, 4, CW, VA, VB, VO>(a, ngroups, s); break;
+    case 11: e = launch_group_t<Tin, Ts, Tout, 8, 8, CW, VA, VB, VO>(a, ngroups, s); break;
+    case 12: e = launch_group_t<Tin, Ts, Tout, 9, 8, CW / 2, VA, VB, VO>(a, ngroups, s); break;
     default: return cudaErrorInvalidValue;
   }
+  if (e != cudaSuccess) return e;
+  const size_t ysm = (size_t)(1 << L) * sizeof(Ts);
+  auto ykern = k_ycol<Tin, Ts, Tout>;
+  if ((e = cudaFuncSetAttribute(ykern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ysm)) != cudaSuccess) return e;
+  ykern<<<(unsigned)ngroups, 512, ysm, s>>>(a, L);
+  return cudaGetLastError();
 }
 
 template <class Tin, class Ts, class Tout, int C>
@@ -282,14 +469,18 @@ cudaError_t launch_small_t(const GroupArgs &a, int logn, cudaStream_t s) {
 }
 
 // Dispatch on (input type, working type, output type).
-template <class Tin, class Ts, class Tout, int C>
+template <class Tin, class Ts, class Tout, int C, int VA, int VB, int VO>
 cudaError_t run_plan(const SrhtPlan &pl, const void *X, int64_t ldx, const void *Y, int64_t N, int d,
                      const int32_t *Psd, const int32_t *pos, void *W, void *WY, int64_t ldw, void *U,
                      void *V, int64_t ldu, double scale, cudaStream_t s,
-                     cudaError_t (*pass2)(const GroupArgs &, int, int64_t, cudaStream_t)) {
+                     cudaError_t (*pass2)(const GroupArgs &, int, int64_t, cudaStream_t), cudaEvent_t ev_mid) {
   GroupArgs a = {};
   a.d = d;
   a.nslab = (d + 1 + C - 1) / C;
+  auto vec_ok = [](const void *p, int64_t ld, size_t eb, int v) {
+    return reinterpret_cast<uintptr_t>(p) % (v * eb) == 0 && ld % v == 0;
+  };
+  a.vec_in = vec_ok(X, ldx, sizeof(Tin), VA) ? 1 : 0;
   a.N = N;
   a.Psd = Psd;
   a.in = X;
@@ -309,16 +500,20 @@ cudaError_t run_plan(const SrhtPlan &pl, const void *X, int64_t ldx, const void 
   a.out = W; a.ldout = ldw; a.out_y = WY; a.pos = nullptr;
   a.ostride = 1; a.ogstride = n2;
   a.scale = 1.0;
-  cudaError_t e = launch_pass_t<Tin, Ts, Tout, C>(a, pl.log2, n1, s);
+  a.vec_out = vec_ok(W, ldw, sizeof(Tout), VO) ? 1 : 0;
+  cudaError_t e = launch_pass_t<Tin, Ts, Tout, VA, VB, VO>(a, pl.log2, n1, s);
   if (e != cudaSuccess) return e;
+  if (ev_mid && (e = cudaEventRecord(ev_mid, s)) != cudaSuccess) return e;
   // pass 2: groups g = k2 (n2 of them), rows rho = j1 at stride n2, outputs kappa = k1
   GroupArgs b = a;
   b.Psd = nullptr;
   b.N = 0;
   b.in = W; b.ldin = ldw; b.in_y = WY;
+  b.vec_in = vec_ok(W, ldw, sizeof(Tout), VA) ? 1 : 0;
+  b.vec_out = vec_ok(U, ldu, sizeof(Tout), VO) ? 1 : 0;
   b.istride = n2; b.igstride = 1;
   b.out = U; b.ldout = ldu; b.out_y = V; b.pos = pos;
-  b.ostride = n2; b.ogstride = 1;
+  b.ostride = 1; b.ogstride = n1;  // pos is stored pass-2-major: entry (k2, k1) at k2 n1 + k1
   b.scale = scale;
   return pass2(b, pl.log1, n2, s);
 }
@@ -338,17 +533,18 @@ SrhtPlan srht_plan(int64_t Np) {
 
 cudaError_t launch_srht(const SrhtPlan &pl, int prec, int xdtype, const void *X, int64_t ldx, const void *Y,
                         int64_t N, int d, const int32_t *Psd, const int32_t *pos, void *W, void *WY,
-                        int64_t ldw, void *U, void *V, int64_t ldu, double scale, cudaStream_t s) {
+                        int64_t ldw, void *U, void *V, int64_t ldu, double scale, cudaStream_t s,
+                        cudaEvent_t ev_mid) {
   using bf16 = __nv_bfloat16;
   if (prec == SLSE_PREC_FP64) {
-    auto p2 = &launch_pass_t<double, double, double, 16>;
+    auto p2 = &launch_pass_t<double, double, double, 1, 2, 2>;
     if (xdtype == SLSE_F64)
-      return run_plan<double, double, double, 16>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale, s, p2);
-    return run_plan<float, double, double, 16>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale, s, p2);
+      return run_plan<double, double, double, 16, 1, 2, 2>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale, s, p2, ev_mid);
+    return run_plan<float, double, double, 16, 1, 2, 2>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale, s, p2, ev_mid);
   }
   if (prec == SLSE_PREC_MIXED_BF16 && xdtype == SLSE_F32) {
-    auto p2 = &launch_pass_t<bf16, float, bf16, 32>;
-    return run_plan<float, float, bf16, 32>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale, s, p2);
+    auto p2 = &launch_pass_t<bf16, float, bf16, 2, 4, 4>;
+    return run_plan<float, float, bf16, 32, 2, 4, 4>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale, s, p2, ev_mid);
   }
   return cudaErrorInvalidValue;
 }

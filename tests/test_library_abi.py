@@ -65,7 +65,7 @@ def test_invalid_arguments_rejected_before_any_launch(lib):
         slse.CProblem(10, 4, 7, 1, 4, 1),              # bad dtype
         slse.CProblem(10, 4, slse.F64, None, 4, 1),    # null X
         slse.CProblem(10, 600, slse.F64, 1, 600, 1),   # d above this build's limit
-        slse.CProblem(1 << 27, 4, slse.F64, 1, 4, 1),  # N' above 2^26
+        slse.CProblem((1 << 24) + 1, 4, slse.F64, 1, 4, 1),  # N' above 2^24
     ]
     for p in bad:
         assert lib.slse_fit(ctypes.byref(p), None, ctypes.c_uint64(0), beta, None, None, None,

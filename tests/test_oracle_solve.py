@@ -58,6 +58,18 @@ def test_ols_normal_equations_and_noiseless_recovery():
     assert np.linalg.norm(rec - b) / np.linalg.norm(b) < 1e4 * 1e4 * u
 
 
+def test_ols_normal_equations_route_on_well_conditioned_data():
+    # the written-out definition (X^T X)^{-1} X^T Y agrees with the QR route to cond^2 * u
+    p = workloads.cfg3(N=20000, d=64, seed=2)
+    X, Y = p["X"].astype(np.float64), p["Y"].astype(np.float64)
+    a = linalg.ols_normal(X, Y, block_rows=3000)
+    b = linalg.ols(X, Y)
+    np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-13)
+    q = workloads.gaussian(40, 5, seed=3)
+    np.testing.assert_allclose(linalg.ols_normal(q["X"], q["Y"]), linalg.ols_normal_longdouble(q["X"], q["Y"]),
+                               rtol=1e-12)
+
+
 def test_ols_square_orthogonal():
     Q = workloads.haar_orthogonal(20, 4)
     y = np.random.default_rng(2).standard_normal(20)
