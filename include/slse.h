@@ -142,6 +142,23 @@ slse_status slse_sketch(const slse_problem *prob, int32_t kind, int32_t prec, ui
 slse_status slse_grad(const slse_problem *prob, const double *beta, double *g_out, int32_t prec,
                       void *workspace, size_t ws_bytes, slse_stream_t stream);
 
+/* Residual-gradient pass that allocates nothing, for callers that cannot allocate device
+ * memory when they need a gradient (graph capture into a fixed memory plan, host
+ * applications that own every device allocation, loops that forbid allocation after
+ * start-up).  The paper has no counterpart: this is a deployment variant of slse_grad.
+ * Same arguments, result and tolerances as slse_grad, but its scratch (a status word and
+ * per-CTA partial gradients, 1 MiB + 4 KiB) is a fixed array inside the library that
+ * every GPU loading the library keeps until the process exits.  No cudaMalloc, cudaFree
+ * or allocating library call is made.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture.  All calls on a device share the one array: calls whose
+ * work may overlap on the GPU (different streams without ordering) race and must not be
+ * issued.  Each call clears the state it needs and overwrites every partial it reads.
+ * Limit: the per-CTA partials must fit in 1 MiB (d <= 512 always fits; fewer CTAs are
+ * used for large d); otherwise SLSE_ENOMEM.  Asynchronous on `stream`. */
+slse_status slse_grad_noalloc(const slse_problem *prob, const double *beta, double *g_out, int32_t prec,
+                              slse_stream_t stream);
+
 /* The random draws of the sketch (Sec. 3, matrices D, P and B) for N' = 2^ceil(log2 N):
  * P (device int32, N'): the permutation, row j of P X is X[P[j]];
  * sigma (device int32, N'): the sampling order, sketch i keeps rows sigma[0..m_i);

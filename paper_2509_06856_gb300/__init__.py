@@ -69,6 +69,8 @@ _lib.slse_sketch.restype = _i32
 _lib.slse_sketch.argtypes = [ctypes.POINTER(CProblem), _i32, _i32, _u64, _i64, _vp, _i64, _vp, _vp, _sz, _vp]
 _lib.slse_grad.restype = _i32
 _lib.slse_grad.argtypes = [ctypes.POINTER(CProblem), _vp, _vp, _i32, _vp, _sz, _vp]
+_lib.slse_grad_noalloc.restype = _i32
+_lib.slse_grad_noalloc.argtypes = [ctypes.POINTER(CProblem), _vp, _vp, _i32, _vp]
 _lib.slse_draws.restype = _i32
 _lib.slse_draws.argtypes = [_i64, _u64, _vp, _vp, _vp, _vp, _sz, _vp]
 _lib.slse_qr.restype = _i32
@@ -82,7 +84,7 @@ _lib.slse_status_string.restype = ctypes.c_char_p
 _lib.slse_status_string.argtypes = [_i32]
 _lib.slse_version.restype = _i32
 
-EXPORTED = ["slse_workspace_size", "slse_fit", "slse_sketch", "slse_grad", "slse_draws", "slse_qr",
+EXPORTED = ["slse_workspace_size", "slse_fit", "slse_sketch", "slse_grad", "slse_grad_noalloc", "slse_draws", "slse_qr",
             "slse_default_schedule", "slse_ai_bound", "slse_status_string", "slse_version"]
 
 
@@ -252,6 +254,20 @@ def grad(X, Y, beta, prec: str = "fp64", workspace=None, stream=None):
     ws_ptr, ws_len = (workspace.data_ptr(), workspace.numel()) if workspace is not None else (None, 0)
     st = _lib.slse_grad(ctypes.byref(p), b.data_ptr(), g.data_ptr(), PREC[prec], ws_ptr, ws_len, _stream(stream))
     _check(st, "slse_grad")
+    return g
+
+
+def grad_noalloc(X, Y, beta, prec: str = "fp64", stream=None):
+    """slse_grad_noalloc: the residual-gradient pass with the library's fixed scratch array,
+    for callers that cannot allocate device memory (the output tensor here is the caller's)."""
+    torch = _torch()
+    p = problem(X, Y)
+    b = beta if (torch.is_tensor(beta) and beta.is_cuda) else torch.as_tensor(np.asarray(beta, np.float64),
+                                                                                device=X.device)
+    b = b.to(torch.float64).contiguous()
+    g = torch.empty(p.d, dtype=torch.float64, device=X.device)
+    st = _lib.slse_grad_noalloc(ctypes.byref(p), b.data_ptr(), g.data_ptr(), PREC[prec], _stream(stream))
+    _check(st, "slse_grad_noalloc")
     return g
 
 

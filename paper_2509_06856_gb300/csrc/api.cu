@@ -10,12 +10,34 @@
 
 using namespace slse;
 
+// Host memory (pinned or pageable) as opposed to device or managed memory.
+bool slse::is_host_pointer(const void *ptr) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+bool slse::valid_problem(const slse_problem *p) {
+  if (!p || !p->X || !p->Y) return false;
+  if (p->N < 1 || p->d < 1 || p->d > 512 || p->d > p->N) return false;
+  if (p->ldx < p->d) return false;
+  if (p->dtype != SLSE_F64 && p->dtype != SLSE_F32) return false;
+  int64_t np = 1;
+  while (np < p->N) np <<= 1;
+  if (np > kMaxPaddedRows) return false;
+  return true;
+}
+
+
 namespace {
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 constexpr size_t kStateBytes = 4096;  // DevState + per-CTA partials of the update kernel
-constexpr int64_t kMaxNp = int64_t(1) << 24;
+constexpr int64_t kMaxNp = kMaxPaddedRows;
 
 int num_sms() {
   int dev = 0, n = 0;
@@ -28,25 +50,6 @@ int64_t padded(int64_t N) {
   int64_t p = 1;
   while (p < N) p <<= 1;
   return p;
-}
-
-// Host memory (pinned or pageable) as opposed to device or managed memory.
-bool is_host_pointer(const void *ptr) {
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
-    cudaGetLastError();
-    return true;
-  }
-  return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
-}
-
-bool valid_problem(const slse_problem *p) {
-  if (!p || !p->X || !p->Y) return false;
-  if (p->N < 1 || p->d < 1 || p->d > 512 || p->d > p->N) return false;
-  if (p->ldx < p->d) return false;
-  if (p->dtype != SLSE_F64 && p->dtype != SLSE_F32) return false;
-  if (padded(p->N) > kMaxNp) return false;
-  return true;
 }
 
 struct Sched {

@@ -97,7 +97,12 @@ __device__ __forceinline__ bool grid_barrier(DevState *st, unsigned nblocks) {
 }
 
 // ----------------------------------------------------------------------------------
-// Host-side launchers implemented in the .cu files.
+// Host-side helpers and launchers implemented in the .cu files.
+
+constexpr int64_t kMaxPaddedRows = int64_t(1) << 24;  // N' limit of this build
+// api.cu
+bool is_host_pointer(const void *ptr);
+bool valid_problem(const slse_problem *p);
 
 // draws.cu
 size_t draws_ws_bytes(int64_t Np);
