@@ -7,8 +7,8 @@
  * Y (N), return the OLS estimator beta-hat = argmin 1/2 ||Y - X beta||^2.
  * SLSE-FRS (Algorithm 2, Sec. 3) forms one randomized Hadamard transform of
  * [X | Y], takes nested row samples of growing size m_1 < ... < m_K from it, runs
- * a_i momentum-IHS (M-IHS) steps on each sketched subproblem (1st stage, Eq. 3.1)
- * and finishes with full-data M-IHS steps (2nd stage, Eq. 3.2).  Every M-IHS step
+ * a_i momentum-IHS (M-IHS) steps on each sketched subproblem (1st stage, Eq. (7))
+ * and finishes with full-data M-IHS steps (2nd stage, Eq. (8)).  Every M-IHS step
  * is preconditioned by the fixed sketched Hessian H-hat = (S-hat X)^T (S-hat X),
  * applied through the R factor of a QR of S-hat X (Appendix, implementation
  * details).
@@ -87,7 +87,8 @@ typedef struct {
   double tol;           /* 2nd stage stops when ||b+ - b|| <= tol (1-rho)/rho ||b+||, rho = sqrt(d/r); <= 0: run to T */
   int32_t kind;         /* slse_sketch_kind (only SLSE_SRHT in this build) */
   int32_t prec;         /* slse_precision */
-  int32_t momentum_reset; /* 1: beta_{-1} = beta_0 at the start of each subproblem and of the 2nd stage */
+  int32_t momentum_reset; /* 0: momentum carries across subproblems (Algorithm 2's global t);
+                             1: beta_{-1} = beta_0 at each subproblem and at the 2nd stage (proof of Thm 4.1) */
 } slse_schedule;
 
 typedef struct {
@@ -135,7 +136,7 @@ slse_status slse_sketch(const slse_problem *prob, int32_t kind, int32_t prec, ui
                         void *SX, int64_t ldsx, void *SY, void *workspace, size_t ws_bytes,
                         slse_stream_t stream);
 
-/* Residual-gradient pass g = X^T (Y - X beta) (Sec. 3, Eq. 3.2 and its FLOP count).
+/* Residual-gradient pass g = X^T (Y - X beta) (Sec. 3, Eq. (8) and its FLOP count).
  * beta: device d doubles; g_out: device d doubles.  prec FP64: FP64 arithmetic.
  * prec MIXED_BF16 (X F32): error-free FP32 residuals and compensated accumulation.
  * Asynchronous on `stream`. */
@@ -174,7 +175,8 @@ slse_status slse_qr(const double *A, int64_t r, int32_t d, int64_t lda, double *
                     void *workspace, size_t ws_bytes, slse_stream_t stream);
 
 /* The paper's experimental schedule (Sec. 5 preamble): r = 6d, eta = d/r, mu = (1-eta)^2,
- * m_1 = 8d doubling while m_i <= N'/2, a_i = 2, T = 100, tol = 0, FP64, momentum reset.
+ * m_1 = 8d doubling while m_i <= N'/2, a_i = 2, T = 100, tol = 0, FP64, momentum carried
+ * across subproblems as in Algorithm 2.
  * Writes at most cap entries into m_buf/a_buf (host) and points out->m/out->a at them.
  * Returns K (the number of sizes the schedule wants; > cap means truncated). */
 int32_t slse_default_schedule(int64_t N, int32_t d, slse_schedule *out, int64_t *m_buf, int32_t *a_buf,

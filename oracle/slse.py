@@ -8,7 +8,7 @@
   a_i >= log_3[((1 + omega) r(i-1, i) + 1) / omega],  r(i-1,i) = sqrt((m_i - d)/(m_{i-1} - d)).
 * ``grad``: g = X^T (Y - X beta).  This is minus the paper's gradient
   nabla f = X^T (X beta - Y) (Sec. 1); the update below adds mu H^{-1} g accordingly.
-* ``mihs_step``: the M-IHS update of Eqs. (3.1)/(3.2),
+* ``mihs_step``: the M-IHS update of Eqs. (7) and (8) (Sec. 3),
   beta_{t+1} = beta_t + mu H-hat^{-1} g_t + eta (beta_t - beta_{t-1}),
   with H-hat^{-1} v = R^{-1} R^{-T} v from S-hat X = Q R (Appendix, implementation details).
 * ``slse_fit``: Algorithm 2 step by step: one transform of [X|Y], nested prefixes of
@@ -17,9 +17,10 @@
 
 Readings taken where the paper is silent (listed in the design doc):
 * beta_0 = 0 (Thm 4.2 allows any beta_0).
-* Momentum is reset at the start of every subproblem and of the 2nd stage,
-  beta_{-1}^i = beta_0^i, as in the proof of Theorem 4.1; ``momentum_reset=False``
-  carries beta_{t-1} across subproblems as the global-t listing of Algorithm 2 reads.
+* Momentum follows the listing of Algorithm 2: one global iteration counter t, so
+  beta_{t-1} carries across subproblems and into the 2nd stage (default).
+  ``momentum_reset=True`` restarts it at every subproblem and at the 2nd stage,
+  beta_{-1}^i = beta_0^i, as the proof of Theorem 4.1 does.
 * The 2nd stage stops early when ||beta_{t+1} - beta_t|| <= tol (1 - rho)/rho ||beta_{t+1}||
   with rho = sqrt(d/r) (the M-IHS rate quoted in Sec. 1); tol <= 0 runs to T.
   T counts all iterations of both stages.
@@ -42,7 +43,7 @@ class Schedule:
     eta: float
     T: int = 100
     tol: float = 0.0
-    momentum_reset: bool = True
+    momentum_reset: bool = False
 
     @property
     def K(self):

@@ -118,7 +118,7 @@ class Schedule:
     T: int = 100
     tol: float = 0.0
     prec: str = "fp64"
-    momentum_reset: bool = True
+    momentum_reset: bool = False
     kind: int = SRHT
     _keep: list = field(default_factory=list, repr=False)
 

@@ -107,8 +107,8 @@ struct FitLayout {
   int nblk;
   bool host_in;
   size_t o_xin, o_yin;
-  size_t o_state, o_psd, o_sigma, o_pos, o_big, o_wy, o_u, o_v, o_A, o_R, o_Hinv, o_qr, o_part, o_g, o_ring,
-      o_b0, o_d32, o_out, o_r0;
+  size_t o_state, o_psd, o_sigma, o_pos, o_big, o_wy, o_u, o_v, o_A, o_R, o_Hinv, o_qr, o_chol, o_part, o_g,
+      o_ring, o_b0, o_d32, o_out, o_r0;
   size_t total;
 };
 
@@ -142,6 +142,7 @@ FitLayout fit_layout(const slse_problem *p, const Sched &s, int nsm) {
   L.o_R = w.take((size_t)d * d * 8);
   L.o_Hinv = w.take((size_t)d * d * 8);
   L.o_qr = w.take(qr_ws_bytes(s.r, d, nsm > 0 ? nsm : 152));
+  L.o_chol = w.take(s.prec == SLSE_PREC_MIXED_BF16 ? chol_ws_bytes(s.r, d) : 0);
   L.o_part = w.take((size_t)L.nblk * d * 8);
   L.o_g = w.take((size_t)d * 8);
   L.o_ring = w.take((size_t)3 * d * 8);
@@ -199,6 +200,9 @@ __global__ void k_init_state(DevState *st, int rebase) {
     z.rebase = rebase;
     *st = z;
   }
+}
+__global__ void k_clear_status(DevState *st) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) st->status = 0;
 }
 __global__ void k_set_stage2(DevState *st, int rebase) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -382,10 +386,30 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
                  1.0 / std::sqrt((double)L.Np), st, L.sp.single ? nullptr : e_mid));
   kernels += L.sp.single ? 1 : 2;
   CK(cudaEventRecord(e_sketch, st));
-  // a5: QR of S-hat X = sqrt(N'/r) U[h0 : h0 + r], then H-hat^{-1} = R^{-1} R^{-T}
-  CK(launch_gather_hessian_rows(s.prec, U, L.ldu, L.h0, s.r, d, std::sqrt((double)L.Np / (double)s.r), A, st));
-  CK(launch_qr(A, s.r, d, d, R, Hinv, qrws, dst, st));
-  kernels += 4;
+  // a5: R of S-hat X = sqrt(N'/r) U[h0 : h0 + r], then H-hat^{-1} = R^{-1} R^{-T}.  FP64 path:
+  // Householder QR.  Mixed path: FP64 Cholesky of the exactly accumulated Gram matrix of the
+  // BF16 rows (the same R), with the Householder QR as fallback on a non-positive pivot.
+  bool use_qr = !mixed;
+  if (mixed) {
+    CK(launch_gram_chol(U, L.ldu, L.h0, s.r, d, (double)L.Np / (double)s.r, R, Hinv, base + L.o_chol, dst, st));
+    const int nt = (d + 31) / 32;
+    kernels += 2 + 3 * nt + 2;
+    DevState *mb = t_mailbox.get();
+    if (!mb) return SLSE_ECUDA;
+    CK(cudaMemcpyAsync(&mb[3], dst, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (((volatile DevState *)&mb[3])->status & ST_NUMERIC) {
+      k_clear_status<<<1, 32, 0, st>>>(dst);
+      CK(cudaGetLastError());
+      ++kernels;
+      use_qr = true;
+    }
+  }
+  if (use_qr) {
+    CK(launch_gather_hessian_rows(s.prec, U, L.ldu, L.h0, s.r, d, std::sqrt((double)L.Np / (double)s.r), A, st));
+    CK(launch_qr(A, s.r, d, d, R, Hinv, qrws, dst, st));
+    kernels += 4;
+  }
   CK(cudaEventRecord(e_qr, st));
   CK(cudaMemsetAsync(ring, 0, (size_t)3 * d * 8, st));
 
@@ -657,7 +681,7 @@ int32_t slse_default_schedule(int64_t N, int32_t d, slse_schedule *out, int64_t 
   out->tol = 0.0;
   out->kind = SLSE_SRHT;
   out->prec = SLSE_PREC_FP64;
-  out->momentum_reset = 1;
+  out->momentum_reset = 0;  // Algorithm 2: one global counter t, momentum carries
   return K;
 }
 

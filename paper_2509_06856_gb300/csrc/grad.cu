@@ -1,5 +1,5 @@
 // Fused one-pass residual-gradient kernels and the M-IHS update (paper Sec. 3,
-// Eqs. 3.1 and 3.2; cost model "(4d+1) rows + 2d^2 + 5d" FLOPs per iteration).
+// Eqs. (7) and (8); cost model "(4d+1) rows + 2d^2 + 5d" FLOPs per iteration).
 //
 // g = sum_i x_i^T (y_i - x_i beta) over the rows of X (2nd stage) or over the first
 // m_i rows of the sampled sketch U (1st stage, scaled by N'/m_i).  One warp owns one

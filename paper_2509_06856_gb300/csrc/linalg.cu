@@ -201,6 +201,175 @@ __global__ void __launch_bounds__(256) k_form_hinv(const double *Rinv, int d, do
   }
 }
 
+// ---------------------------------------------------------------- Gram + Cholesky route
+// For the BF16 Hessian sketch (mixed path) R is obtained as the Cholesky factor of
+// G = (S-hat X)^T (S-hat X) (the R of a Householder QR with non-negative diagonal is the
+// same matrix).  G is accumulated from exact FP32 products of the BF16 entries with a
+// two-word (TwoSum) accumulator per entry, split over row ranges, and summed in FP64 in a
+// fixed order; the factorisation is FP64.
+
+constexpr int kTile = 32;
+
+__device__ __forceinline__ float bf16_to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// part[s][i][k] = sum over rows of split s of U[row][i] * U[row][k], upper tiles only.
+__global__ void __launch_bounds__(256) k_gram_bf16(const __nv_bfloat16 *U, int64_t ldu, int64_t row0, int64_t r,
+                                                   int d, int ksplit, double *part) {
+  __shared__ float sa[kTile][kTile + 1], sb[kTile][kTile + 1];
+  const int ti = blockIdx.y, tk = blockIdx.x, sp = blockIdx.z;
+  if (tk < ti) return;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t lo = (r * sp) / ksplit, hi = (r * (sp + 1)) / ksplit;
+  float sh[4] = {0, 0, 0, 0}, sl[4] = {0, 0, 0, 0};
+  for (int64_t k0 = lo; k0 < hi; k0 += kTile) {
+    for (int rr = ty; rr < kTile; rr += 8) {
+      const int64_t row = k0 + rr;
+      const int ci = ti * kTile + tx, ck = tk * kTile + tx;
+      const bool rv = row < hi;
+      sa[rr][tx] = (rv && ci < d) ? bf16_to_f(U[(row0 + row) * ldu + ci]) : 0.f;
+      sb[rr][tx] = (rv && ck < d) ? bf16_to_f(U[(row0 + row) * ldu + ck]) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int ii = ty + 8 * q;
+      float s = sh[q], c = sl[q];
+#pragma unroll 8
+      for (int rr = 0; rr < kTile; ++rr) {
+        const float p = sa[rr][ii] * sb[rr][tx];  // exact: 8-bit x 8-bit significands
+        float e;
+        two_sum(s, p, s, e);
+        c += e;
+      }
+      sh[q] = s;
+      sl[q] = c;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int gi = ti * kTile + ty + 8 * q, gk = tk * kTile + tx;
+    if (gi < d && gk < d) part[((size_t)sp * d + gi) * d + gk] = (double)sh[q] + (double)sl[q];
+  }
+}
+
+// G[i][k] = G[k][i] = scale * sum_s part[s][i][k] for i <= k.
+__global__ void k_gram_reduce(const double *part, int ksplit, int d, double scale, double *G) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)d * d) return;
+  const int i = (int)(e / d), k = (int)(e % d);
+  if (k < i) return;
+  double s = 0.0;
+  for (int sp = 0; sp < ksplit; ++sp) s += part[((size_t)sp * d + i) * d + k];
+  G[(size_t)i * d + k] = scale * s;
+  G[(size_t)k * d + i] = scale * s;
+}
+
+// Diagonal block [k0, k0+nb) of the right-looking blocked Cholesky (lower, in place),
+// plus the inverse of that block for the panel solve.
+__global__ void __launch_bounds__(256) k_potrf(double *A, int d, int k0, double *Linv, DevState *st) {
+  __shared__ double L[kTile][kTile + 1], I[kTile][kTile + 1];
+  const int nb = min(kTile, d - k0);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int rr = ty; rr < kTile; rr += 8) {
+    L[rr][tx] = (rr < nb && tx < nb) ? A[(size_t)(k0 + rr) * d + k0 + tx] : (rr == tx ? 1.0 : 0.0);
+    I[rr][tx] = rr == tx ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
+    const double piv = L[j][j];
+    if (!(piv > 0.0)) {
+      if (threadIdx.x == 0) atomicOr(&st->status, ST_NUMERIC);
+      return;
+    }
+    const double pj = sqrt(piv);
+    __syncthreads();
+    if (threadIdx.x < kTile) {
+      const int i = threadIdx.x;
+      if (i > j && i < nb) L[i][j] /= pj;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) L[j][j] = pj;
+    for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+      const int i = e / kTile, l = e % kTile;
+      if (i > j && l > j && l <= i && i < nb) L[i][l] -= L[i][j] * L[l][j];
+    }
+    __syncthreads();
+  }
+  // inverse of the lower-triangular block: forward substitution on the identity, one column per lane
+  if (threadIdx.x < kTile) {
+    const int c = threadIdx.x;
+    for (int i = 0; i < kTile; ++i) {
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int l = 0; l < i; ++l) s -= L[i][l] * I[l][c];
+      I[i][c] = (i < nb) ? s / L[i][i] : (i == c ? 1.0 : 0.0);
+    }
+  }
+  __syncthreads();
+  for (int rr = ty; rr < kTile; rr += 8) {
+    if (rr < nb && tx < nb) {
+      A[(size_t)(k0 + rr) * d + k0 + tx] = tx <= rr ? L[rr][tx] : 0.0;
+      Linv[rr * kTile + tx] = tx <= rr ? I[rr][tx] : 0.0;
+    }
+  }
+}
+
+// Panel below the diagonal block: A[i0:i0+32, k0:k0+nb] <- A * Linv^T.
+__global__ void __launch_bounds__(256) k_trsm(double *A, int d, int k0, const double *Linv) {
+  __shared__ double P[kTile][kTile + 1], T[kTile][kTile + 1];
+  const int nb = min(kTile, d - k0);
+  const int i0 = k0 + kTile * (1 + blockIdx.x);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int rr = ty; rr < kTile; rr += 8) {
+    P[rr][tx] = (i0 + rr < d && tx < nb) ? A[(size_t)(i0 + rr) * d + k0 + tx] : 0.0;
+    T[rr][tx] = (rr < nb && tx < nb) ? Linv[rr * kTile + tx] : 0.0;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int rr = ty + 8 * q;
+    double s = 0.0;
+    for (int l = 0; l < kTile; ++l) s = fma(P[rr][l], T[tx][l], s);  // (P Linv^T)[rr][tx]
+    if (i0 + rr < d && tx < nb) A[(size_t)(i0 + rr) * d + k0 + tx] = s;
+  }
+}
+
+// Trailing update of the lower triangle: A[bi, bj] -= L[bi, k] L[bj, k]^T for bj <= bi.
+__global__ void __launch_bounds__(256) k_syrk(double *A, int d, int k0) {
+  __shared__ double Li[kTile][kTile + 1], Lj[kTile][kTile + 1];
+  const int nb = min(kTile, d - k0);
+  const int base = k0 + kTile;
+  const int bi = blockIdx.y, bj = blockIdx.x;
+  if (bj > bi) return;
+  const int i0 = base + kTile * bi, j0 = base + kTile * bj;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int rr = ty; rr < kTile; rr += 8) {
+    Li[rr][tx] = (i0 + rr < d && tx < nb) ? A[(size_t)(i0 + rr) * d + k0 + tx] : 0.0;
+    Lj[rr][tx] = (j0 + rr < d && tx < nb) ? A[(size_t)(j0 + rr) * d + k0 + tx] : 0.0;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int rr = ty + 8 * q;
+    const int gi = i0 + rr, gj = j0 + tx;
+    if (gi < d && gj < d && gj <= gi) {
+      double s = 0.0;
+      for (int l = 0; l < kTile; ++l) s = fma(Li[rr][l], Lj[tx][l], s);
+      A[(size_t)gi * d + gj] -= s;
+    }
+  }
+}
+
+// R = L^T (upper, positive diagonal) and Rt = L (lower with zeros above).
+__global__ void k_chol_to_r(const double *A, int d, double *R, double *Rt) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)d * d) return;
+  const int i = (int)(e / d), k = (int)(e % d);
+  const double l = k <= i ? A[e] : 0.0;  // L[i][k]
+  Rt[e] = l;
+  R[(size_t)k * d + i] = l;
+}
+
 template <class T> __device__ __forceinline__ double to_d(T v) { return (double)v; }
 template <> __device__ __forceinline__ double to_d<__nv_bfloat16>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
 
@@ -282,6 +451,45 @@ cudaError_t launch_qr(double *A, int64_t r, int d, int64_t lda, double *R, doubl
   if (Hinv) {
     k_tri_inv_sweep<<<(d + 7) / 8, 256, 0, s>>>(R, a.Rt, d, Rinv, st);
     const int nt = (d + 31) / 32;
+    k_form_hinv<<<dim3(nt, nt), 256, 0, s>>>(Rinv, d, Hinv);
+  }
+  return cudaGetLastError();
+}
+
+size_t chol_ws_bytes(int64_t r, int d) {
+  const int ksplit = (int)((r + 255) / 256 < 8 ? (r + 255) / 256 : 8);
+  return align256((size_t)(ksplit > 0 ? ksplit : 1) * d * d * 8) + align256((size_t)d * d * 8) +
+         align256((size_t)kTile * kTile * 8) + 2 * align256((size_t)d * d * 8);
+}
+
+cudaError_t launch_gram_chol(const void *U, int64_t ldu, int64_t row0, int64_t r, int d, double scale2, double *R,
+                             double *Hinv, void *ws, DevState *st, cudaStream_t s) {
+  int ksplit = (int)((r + 255) / 256);
+  if (ksplit > 8) ksplit = 8;
+  if (ksplit < 1) ksplit = 1;
+  char *p = static_cast<char *>(ws);
+  size_t off = 0;
+  double *part = reinterpret_cast<double *>(p + off); off += align256((size_t)ksplit * d * d * 8);
+  double *G = reinterpret_cast<double *>(p + off); off += align256((size_t)d * d * 8);
+  double *Linv = reinterpret_cast<double *>(p + off); off += align256((size_t)kTile * kTile * 8);
+  double *Rinv = reinterpret_cast<double *>(p + off); off += align256((size_t)d * d * 8);
+  double *Rt = reinterpret_cast<double *>(p + off); off += align256((size_t)d * d * 8);
+  const int nt = (d + kTile - 1) / kTile;
+  k_gram_bf16<<<dim3(nt, nt, ksplit), 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(U), ldu, row0, r, d, ksplit, part);
+  const int64_t dd = (int64_t)d * d;
+  k_gram_reduce<<<(unsigned)((dd + 255) / 256), 256, 0, s>>>(part, ksplit, d, scale2, G);
+  for (int kb = 0; kb < nt; ++kb) {
+    const int k0 = kb * kTile;
+    k_potrf<<<1, 256, 0, s>>>(G, d, k0, Linv, st);
+    const int below = nt - kb - 1;
+    if (below > 0) {
+      k_trsm<<<below, 256, 0, s>>>(G, d, k0, Linv);
+      k_syrk<<<dim3(below, below), 256, 0, s>>>(G, d, k0);
+    }
+  }
+  k_chol_to_r<<<(unsigned)((dd + 255) / 256), 256, 0, s>>>(G, d, R, Rt);
+  if (Hinv) {
+    k_tri_inv_sweep<<<(d + 7) / 8, 256, 0, s>>>(R, Rt, d, Rinv, st);
     k_form_hinv<<<dim3(nt, nt), 256, 0, s>>>(Rinv, d, Hinv);
   }
   return cudaGetLastError();

@@ -152,7 +152,7 @@ template <int R, class T> __device__ __forceinline__ void fwht_regs(T (&v)[R]) {
 //   O: the Q cluster bits (rows held by the Q CTAs, read through distributed shared
 //      memory), then scaling, conversion and VO-column vector stores.
 template <class Tin, class Ts, class Tout, int LOGM, int Q, int C, int VA, int VB, int VO, int NT>
-__global__ void __launch_bounds__(NT, 2) k_group(const GroupArgs a) {
+__global__ void __launch_bounds__(NT, 3) k_group(const GroupArgs a) {
   constexpr int M = 1 << LOGM;
   constexpr int S0 = LOGM < 5 ? LOGM : 5;
   constexpr int S1 = LOGM - S0;
@@ -173,15 +173,17 @@ __global__ void __launch_bounds__(NT, 2) k_group(const GroupArgs a) {
   const int d = a.d;
   const Tin *in = static_cast<const Tin *>(a.in);
 
-  // input rows of this CTA: element offset of the row and sign (0 for padding rows)
+  // input rows of this CTA: element offset of the row and its multiplier (sign times the
+  // output scale; 0 for padding rows)
+  const Ts scale = (Ts)a.scale;
   for (int l = threadIdx.x; l < M; l += NT) {
     const int64_t j = (rho0 + l) * a.istride + g * a.igstride;
     int64_t src = j;
-    Ts mul = Ts(1);
+    Ts mul = scale;
     if (a.Psd) {
       const int32_t v = __ldg(a.Psd + j);
       src = v < 0 ? (int64_t)(~v) : (int64_t)v;
-      mul = v < 0 ? Ts(-1) : Ts(1);
+      mul = v < 0 ? -scale : scale;
       if (src >= a.N) { src = 0; mul = Ts(0); }
     }
     s_off[l] = src * a.ldin;
@@ -269,7 +271,6 @@ __global__ void __launch_bounds__(NT, 2) k_group(const GroupArgs a) {
     else rt[q] = tile;
   }
   Tout *out = static_cast<Tout *>(a.out);
-  const Ts scale = (Ts)a.scale;
   const bool fast_out = a.vec_out && col0 + C <= d;
   for (int it = threadIdx.x; it < (C / VO) * MQ; it += NT) {
     const int cq = it % (C / VO), lq = it / (C / VO);
@@ -294,7 +295,7 @@ __global__ void __launch_bounds__(NT, 2) k_group(const GroupArgs a) {
       if (dst < 0) continue;
       Ts o[VO];
 #pragma unroll
-      for (int e = 0; e < VO; ++e) o[e] = v[e][q] * scale;
+      for (int e = 0; e < VO; ++e) o[e] = v[e][q];
       if (fast_out) {
         store_vec<Tout, Ts, VO>(out + dst * a.ldout + col, o);
       } else {

@@ -159,6 +159,20 @@ def test_fit_fp64_iterates_match_oracle_cfg1(slse):
     assert res.report["iters_stage1"] == 12 and res.report["iters_stage2"] == 48
 
 
+def test_fit_fp64_iterates_match_oracle_momentum_reset(slse):
+    # the proof's reading (momentum restarted per subproblem) is an option of both sides
+    p = workloads.gaussian(8192, 24, seed=5)
+    X, Y = p["X"], p["Y"]
+    sched = slse.Schedule(m=[192, 384, 768, 1536], a=[3, 2, 2, 2], r=144, mu=(1 - 1 / 6) ** 2, eta=1 / 6, T=30,
+                          momentum_reset=True)
+    res = slse.fit(dev(X), dev(Y), sched, seed=4, trace_cap=30)
+    ores = osl.slse_fit(X, Y, osl.Schedule(m=sched.m, a=sched.a, r=sched.r, mu=sched.mu, eta=sched.eta, T=30,
+                                           momentum_reset=True), seed=4, trace=True)
+    bh = linalg.ols(X, Y)
+    for t, (a, b) in enumerate(zip(host(res.beta_hist), ores.trace)):
+        assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(bh), t
+
+
 @pytest.mark.parametrize("name,N,d,kappa", [("paper", 1 << 15, 32, 1e4), ("cfg2", 1 << 16, 64, 1e4)])
 def test_fit_fp64_reaches_ols(slse, name, N, d, kappa):
     p = workloads.paper(N, d, kappa=kappa, sigma2=1e-8, seed=1) if name == "paper" else \

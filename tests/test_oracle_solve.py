@@ -221,7 +221,7 @@ def test_noiseless_fit_recovers_beta():
     np.testing.assert_allclose(res.beta, p["beta_true"], rtol=1e-12, atol=1e-12)
 
 
-def test_tolerance_stop_and_momentum_carry_option():
+def test_tolerance_stop_and_momentum_reset_option():
     p = workloads.cfg1()
     s = slse.Schedule(m=[200 * 2 ** t for t in range(6)], a=[2] * 6, r=300, mu=(1 - 1 / 6) ** 2,
                       eta=1 / 6, T=100, tol=1e-10)
@@ -229,7 +229,7 @@ def test_tolerance_stop_and_momentum_carry_option():
     bh = linalg.ols(p["X"], p["Y"])
     assert res.converged and res.iters_stage1 + res.iters_stage2 < 100
     assert np.linalg.norm(res.beta - bh) <= 1e-9 * np.linalg.norm(bh)
-    s.momentum_reset = False
+    s.momentum_reset = True   # the proof's reading (Thm 4.1): restart momentum per subproblem
     s.tol = 0.0
     res2 = slse.slse_fit(p["X"], p["Y"], s, seed=0)
     assert np.linalg.norm(res2.beta - bh) <= 1e-12 * np.linalg.norm(bh)
