@@ -265,53 +265,59 @@ __global__ void k_gram_reduce(const double *part, int ksplit, int d, double scal
   G[(size_t)k * d + i] = scale * s;
 }
 
-// Diagonal block [k0, k0+nb) of the right-looking blocked Cholesky (lower, in place),
-// plus the inverse of that block for the panel solve.
-__global__ void __launch_bounds__(256) k_potrf(double *A, int d, int k0, double *Linv, DevState *st) {
-  __shared__ double L[kTile][kTile + 1], I[kTile][kTile + 1];
+// Diagonal block [k0, k0+nb) of the right-looking blocked Cholesky (lower, in place), and
+// the inverse of that block for the panel solve.  One warp: lane i keeps row i of the block
+// in registers; pivots use rsqrt, column entries travel by shuffle.  FP64 latency is long on
+// this part, so the dependent chain per column is kept to a few operations.  Rows past d
+// are identity rows.
+__global__ void __launch_bounds__(32) k_potrf(double *A, int d, int k0, double *Linv, DevState *st) {
+  __shared__ double s_rinv[kTile];
+  const int lane = threadIdx.x;
   const int nb = min(kTile, d - k0);
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int rr = ty; rr < kTile; rr += 8) {
-    L[rr][tx] = (rr < nb && tx < nb) ? A[(size_t)(k0 + rr) * d + k0 + tx] : (rr == tx ? 1.0 : 0.0);
-    I[rr][tx] = rr == tx ? 1.0 : 0.0;
-  }
-  __syncthreads();
-  for (int j = 0; j < nb; ++j) {
-    const double piv = L[j][j];
+  double a[kTile];
+#pragma unroll
+  for (int l = 0; l < kTile; ++l)
+    a[l] = (lane < nb && l <= lane && l < nb) ? A[(size_t)(k0 + lane) * d + k0 + l] : (l == lane ? 1.0 : 0.0);
+#pragma unroll
+  for (int j = 0; j < kTile; ++j) {
+    const double piv = __shfl_sync(0xffffffffu, a[j], j);
     if (!(piv > 0.0)) {
-      if (threadIdx.x == 0) atomicOr(&st->status, ST_NUMERIC);
+      if (lane == 0) atomicOr(&st->status, ST_NUMERIC);
       return;
     }
-    const double pj = sqrt(piv);
-    __syncthreads();
-    if (threadIdx.x < kTile) {
-      const int i = threadIdx.x;
-      if (i > j && i < nb) L[i][j] /= pj;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) L[j][j] = pj;
-    for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
-      const int i = e / kTile, l = e % kTile;
-      if (i > j && l > j && l <= i && i < nb) L[i][l] -= L[i][j] * L[l][j];
-    }
-    __syncthreads();
-  }
-  // inverse of the lower-triangular block: forward substitution on the identity, one column per lane
-  if (threadIdx.x < kTile) {
-    const int c = threadIdx.x;
-    for (int i = 0; i < kTile; ++i) {
-      double s = (i == c) ? 1.0 : 0.0;
-      for (int l = 0; l < i; ++l) s -= L[i][l] * I[l][c];
-      I[i][c] = (i < nb) ? s / L[i][i] : (i == c ? 1.0 : 0.0);
+    const double rs = rsqrt(piv);
+    if (lane == 0) s_rinv[j] = rs;  // 1 / L[j][j]
+    if (lane == j) a[j] = piv * rs;
+    else if (lane > j) a[j] *= rs;
+#pragma unroll
+    for (int l = j + 1; l < kTile; ++l) {
+      const double llj = __shfl_sync(0xffffffffu, a[j], l);  // L[l][j]
+      if (lane >= l) a[l] = fma(-a[j], llj, a[l]);
     }
   }
-  __syncthreads();
-  for (int rr = ty; rr < kTile; rr += 8) {
-    if (rr < nb && tx < nb) {
-      A[(size_t)(k0 + rr) * d + k0 + tx] = tx <= rr ? L[rr][tx] : 0.0;
-      Linv[rr * kTile + tx] = tx <= rr ? I[rr][tx] : 0.0;
+  __syncwarp();
+  // column `lane` of L^{-1} by column sweep: x_i = x_i / L[i][i]; x_l -= L[l][i] x_i (l > i)
+  double x[kTile];
+#pragma unroll
+  for (int l = 0; l < kTile; ++l) x[l] = (l == lane) ? 1.0 : 0.0;
+#pragma unroll
+  for (int i = 0; i < kTile; ++i) {
+    const double xi = x[i] * s_rinv[i];
+    x[i] = xi;
+#pragma unroll
+    for (int l = i + 1; l < kTile; ++l) {
+      const double lli = __shfl_sync(0xffffffffu, a[i], l);  // L[l][i]
+      x[l] = fma(-lli, xi, x[l]);
     }
   }
+  if (lane < nb) {
+#pragma unroll
+    for (int l = 0; l < kTile; ++l)
+      if (l < nb) A[(size_t)(k0 + lane) * d + k0 + l] = l <= lane ? a[l] : 0.0;
+  }
+#pragma unroll
+  for (int l = 0; l < kTile; ++l)
+    if (l < nb && lane < nb) Linv[l * kTile + lane] = l >= lane ? x[l] : 0.0;
 }
 
 // Panel below the diagonal block: A[i0:i0+32, k0:k0+nb] <- A * Linv^T.
@@ -480,7 +486,7 @@ cudaError_t launch_gram_chol(const void *U, int64_t ldu, int64_t row0, int64_t r
   k_gram_reduce<<<(unsigned)((dd + 255) / 256), 256, 0, s>>>(part, ksplit, d, scale2, G);
   for (int kb = 0; kb < nt; ++kb) {
     const int k0 = kb * kTile;
-    k_potrf<<<1, 256, 0, s>>>(G, d, k0, Linv, st);
+    k_potrf<<<1, 32, 0, s>>>(G, d, k0, Linv, st);
     const int below = nt - kb - 1;
     if (below > 0) {
       k_trsm<<<below, 256, 0, s>>>(G, d, k0, Linv);

@@ -151,10 +151,10 @@ template <int R, class T> __device__ __forceinline__ void fwht_regs(T (&v)[R]) {
 //   B: the remaining low LOGM - S0 bits, VB columns per thread, through the shared tile;
 //   O: the Q cluster bits (rows held by the Q CTAs, read through distributed shared
 //      memory), then scaling, conversion and VO-column vector stores.
-template <class Tin, class Ts, class Tout, int LOGM, int Q, int C, int VA, int VB, int VO, int NT>
-__global__ void __launch_bounds__(NT, 3) k_group(const GroupArgs a) {
+template <class Tin, class Ts, class Tout, int LOGM, int Q, int C, int VA, int VB, int VO, int NT, int MINB, int SA>
+__global__ void __launch_bounds__(NT, MINB) k_group(const GroupArgs a) {
   constexpr int M = 1 << LOGM;
-  constexpr int S0 = LOGM < 5 ? LOGM : 5;
+  constexpr int S0 = LOGM < SA ? LOGM : SA;
   constexpr int S1 = LOGM - S0;
   constexpr int RA = 1 << S0, RB = 1 << S1;
   constexpr int MQ = M / Q;
@@ -408,13 +408,13 @@ __global__ void __launch_bounds__(NT) k_small(const GroupArgs a, int logn) {
   }
 }
 
-template <class Tin, class Ts, class Tout, int LOGM, int Q, int C, int VA, int VB, int VO>
+template <class Tin, class Ts, class Tout, int LOGM, int Q, int C, int VA, int VB, int VO, int MINB = 3, int SA = 5>
 cudaError_t launch_group_t(const GroupArgs &a0, int64_t ngroups, cudaStream_t s) {
   constexpr int NT = 256;
   GroupArgs a = a0;
   a.nslab = (a.d + C - 1) / C;
   const size_t smem = (size_t)(1 << LOGM) * (C * sizeof(Ts) + 8 + sizeof(Ts) + 4);
-  auto kern = k_group<Tin, Ts, Tout, LOGM, Q, C, VA, VB, VO, NT>;
+  auto kern = k_group<Tin, Ts, Tout, LOGM, Q, C, VA, VB, VO, NT, MINB, SA>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -432,22 +432,23 @@ cudaError_t launch_group_t(const GroupArgs &a0, int64_t ngroups, cudaStream_t s)
   return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
-// One pass over groups of 2^L rows: the X columns by k_group (256-byte row segments:
-// 64 FP32 / 32 FP64 columns, 256 rows per CTA, clusters of up to 8 CTAs; for L = 12
-// 128-byte segments and 512 rows per CTA), the Y column by k_ycol.
+// One pass over groups of 2^L rows: the X columns by k_group, the Y column by k_ycol.
+// k_group works on 128-byte row segments (32 FP32 / 16 FP64 columns), 256 rows per CTA
+// (512 for L = 12) and clusters of up to 8 CTAs; stage A takes the top 4 row bits so
+// that 4 CTAs fit on an SM.
 template <class Tin, class Ts, class Tout, int VA, int VB, int VO>
 cudaError_t launch_pass_t(const GroupArgs &a, int L, int64_t ngroups, cudaStream_t s) {
-  constexpr int CW = 256 / (int)sizeof(Ts);  // columns per 256-byte segment
+  constexpr int CP = 128 / (int)sizeof(Ts);
   cudaError_t e;
   switch (L) {
-    case 5: e = launch_group_t<Tin, Ts, Tout, 5, 1, CW, VA, VB, VO>(a, ngroups, s); break;
-    case 6: e = launch_group_t<Tin, Ts, Tout, 6, 1, CW, VA, VB, VO>(a, ngroups, s); break;
-    case 7: e = launch_group_t<Tin, Ts, Tout, 7, 1, CW, VA, VB, VO>(a, ngroups, s); break;
-    case 8: e = launch_group_t<Tin, Ts, Tout, 8, 1, CW, VA, VB, VO>(a, ngroups, s); break;
-    case 9: e = launch_group_t<Tin, Ts, Tout, 8, 2, CW, VA, VB, VO>(a, ngroups, s); break;
-    case 10: e = launch_group_t<Tin, Ts, Tout, 8, 4, CW, VA, VB, VO>(a, ngroups, s); break;
-    case 11: e = launch_group_t<Tin, Ts, Tout, 8, 8, CW, VA, VB, VO>(a, ngroups, s); break;
-    case 12: e = launch_group_t<Tin, Ts, Tout, 9, 8, CW / 2, VA, VB, VO>(a, ngroups, s); break;
+    case 5: e = launch_group_t<Tin, Ts, Tout, 5, 1, CP, VA, VB, VO, 4, 4>(a, ngroups, s); break;
+    case 6: e = launch_group_t<Tin, Ts, Tout, 6, 1, CP, VA, VB, VO, 4, 4>(a, ngroups, s); break;
+    case 7: e = launch_group_t<Tin, Ts, Tout, 7, 1, CP, VA, VB, VO, 4, 4>(a, ngroups, s); break;
+    case 8: e = launch_group_t<Tin, Ts, Tout, 8, 1, CP, VA, VB, VO, 4, 4>(a, ngroups, s); break;
+    case 9: e = launch_group_t<Tin, Ts, Tout, 8, 2, CP, VA, VB, VO, 4, 4>(a, ngroups, s); break;
+    case 10: e = launch_group_t<Tin, Ts, Tout, 8, 4, CP, VA, VB, VO, 4, 4>(a, ngroups, s); break;
+    case 11: e = launch_group_t<Tin, Ts, Tout, 8, 8, CP, VA, VB, VO, 4, 4>(a, ngroups, s); break;
+    case 12: e = launch_group_t<Tin, Ts, Tout, 9, 8, CP, VA, VB, VO, 3, 4>(a, ngroups, s); break;
     default: return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;
@@ -538,14 +539,14 @@ cudaError_t launch_srht(const SrhtPlan &pl, int prec, int xdtype, const void *X,
                         cudaEvent_t ev_mid) {
   using bf16 = __nv_bfloat16;
   if (prec == SLSE_PREC_FP64) {
-    auto p2 = &launch_pass_t<double, double, double, 1, 2, 2>;
+    auto p2 = &launch_pass_t<double, double, double, 1, 1, 2>;
     if (xdtype == SLSE_F64)
-      return run_plan<double, double, double, 16, 1, 2, 2>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale, s, p2, ev_mid);
-    return run_plan<float, double, double, 16, 1, 2, 2>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale, s, p2, ev_mid);
+      return run_plan<double, double, double, 16, 1, 1, 2>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale, s, p2, ev_mid);
+    return run_plan<float, double, double, 16, 1, 1, 2>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale, s, p2, ev_mid);
   }
   if (prec == SLSE_PREC_MIXED_BF16 && xdtype == SLSE_F32) {
-    auto p2 = &launch_pass_t<bf16, float, bf16, 2, 4, 4>;
-    return run_plan<float, float, bf16, 32, 2, 4, 4>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale, s, p2, ev_mid);
+    auto p2 = &launch_pass_t<bf16, float, bf16, 2, 2, 4>;
+    return run_plan<float, float, bf16, 32, 2, 2, 4>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale, s, p2, ev_mid);
   }
   return cudaErrorInvalidValue;
 }
