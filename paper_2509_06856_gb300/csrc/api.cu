@@ -201,8 +201,10 @@ __global__ void k_init_state(DevState *st, int rebase) {
     *st = z;
   }
 }
-__global__ void k_clear_status(DevState *st) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) st->status = 0;
+// Clears the non-positive-pivot flag of the Cholesky route before the QR fallback; any
+// other status bit (a timeout) is kept for the final report.
+__global__ void k_clear_numeric(DevState *st) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) st->status &= ~ST_NUMERIC;
 }
 __global__ void k_set_stage2(DevState *st, int rebase) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -399,7 +401,7 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     CK(cudaMemcpyAsync(&mb[3], dst, sizeof(DevState), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (((volatile DevState *)&mb[3])->status & ST_NUMERIC) {
-      k_clear_status<<<1, 32, 0, st>>>(dst);
+      k_clear_numeric<<<1, 32, 0, st>>>(dst);
       CK(cudaGetLastError());
       ++kernels;
       use_qr = true;

@@ -144,6 +144,35 @@ template <int R, class T> __device__ __forceinline__ void fwht_regs(T (&v)[R]) {
   }
 }
 
+// Butterflies of VEC adjacent columns at once.  For FP32 pairs of columns go through the
+// packed two-lane FP32 instructions (add, and a - b as fma(b, -1, a): the same rounding
+// as a scalar subtraction), halving the instruction count of the transform.
+template <int R, int VEC, class T> __device__ __forceinline__ void fwht_cols(T (&v)[VEC][R]) {
+  if constexpr (sizeof(T) == 4 && VEC % 2 == 0) {
+    const float2 m1 = make_float2(-1.f, -1.f);
+#pragma unroll
+    for (int e = 0; e < VEC; e += 2) {
+#pragma unroll
+      for (int h = 1; h < R; h <<= 1) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+          if ((i & h) == 0) {
+            const float2 x = make_float2(v[e][i], v[e + 1][i]);
+            const float2 y = make_float2(v[e][i + h], v[e + 1][i + h]);
+            const float2 a = __fadd2_rn(x, y);
+            const float2 b = __ffma2_rn(y, m1, x);
+            v[e][i] = a.x; v[e + 1][i] = a.y;
+            v[e][i + h] = b.x; v[e + 1][i + h] = b.y;
+          }
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) fwht_regs<R, T>(v[e]);
+  }
+}
+
 // Group transform of the X columns: 2^LOGM rows x C columns per CTA, Q CTAs per
 // cluster (the group has 2^LOGM * Q rows).  The Y column goes through k_ycol.  Stages:
 //   A: the top S0 = min(5, LOGM) bits of the CTA-local row index, in registers, loaded
@@ -227,8 +256,7 @@ __global__ void __launch_bounds__(NT, MINB) k_group(const GroupArgs a) {
 #pragma unroll
       for (int e = 0; e < VA; ++e) v[e][k] *= mul;
     }
-#pragma unroll
-    for (int e = 0; e < VA; ++e) fwht_regs<RA, Ts>(v[e]);
+    fwht_cols<RA, VA, Ts>(v);
 #pragma unroll
     for (int k = 0; k < RA; ++k) {
       Ts t[VA];
@@ -250,8 +278,7 @@ __global__ void __launch_bounds__(NT, MINB) k_group(const GroupArgs a) {
 #pragma unroll
         for (int e = 0; e < VB; ++e) v[e][k] = t[e];
       }
-#pragma unroll
-      for (int e = 0; e < VB; ++e) fwht_regs<RB, Ts>(v[e]);
+      fwht_cols<RB, VB, Ts>(v);
 #pragma unroll
       for (int k = 0; k < RB; ++k) {
         Ts t[VB];
@@ -285,8 +312,7 @@ __global__ void __launch_bounds__(NT, MINB) k_group(const GroupArgs a) {
       for (int e = 0; e < VO; ++e) v[e][q] = t[e];
     }
     if constexpr (Q > 1) {
-#pragma unroll
-      for (int e = 0; e < VO; ++e) fwht_regs<Q, Ts>(v[e]);
+      fwht_cols<Q, VO, Ts>(v);
     }
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
@@ -436,18 +462,18 @@ cudaError_t launch_group_t(const GroupArgs &a0, int64_t ngroups, cudaStream_t s)
 // k_group works on 128-byte row segments (32 FP32 / 16 FP64 columns), 256 rows per CTA
 // (512 for L = 12) and clusters of up to 8 CTAs; stage A takes the top 4 row bits so
 // that 4 CTAs fit on an SM.
-template <class Tin, class Ts, class Tout, int VA, int VB, int VO>
+template <class Tin, class Ts, class Tout, int VA, int VB, int VO, int SLAB_BYTES = 128, int MB = 4>
 cudaError_t launch_pass_t(const GroupArgs &a, int L, int64_t ngroups, cudaStream_t s) {
-  constexpr int CP = 128 / (int)sizeof(Ts);
+  constexpr int CP = SLAB_BYTES / (int)sizeof(Ts);
   cudaError_t e;
   switch (L) {
-    case 5: e = launch_group_t<Tin, Ts, Tout, 5, 1, CP, VA, VB, VO, 4, 4>(a, ngroups, s); break;
-    case 6: e = launch_group_t<Tin, Ts, Tout, 6, 1, CP, VA, VB, VO, 4, 4>(a, ngroups, s); break;
-    case 7: e = launch_group_t<Tin, Ts, Tout, 7, 1, CP, VA, VB, VO, 4, 4>(a, ngroups, s); break;
-    case 8: e = launch_group_t<Tin, Ts, Tout, 8, 1, CP, VA, VB, VO, 4, 4>(a, ngroups, s); break;
-    case 9: e = launch_group_t<Tin, Ts, Tout, 8, 2, CP, VA, VB, VO, 4, 4>(a, ngroups, s); break;
-    case 10: e = launch_group_t<Tin, Ts, Tout, 8, 4, CP, VA, VB, VO, 4, 4>(a, ngroups, s); break;
-    case 11: e = launch_group_t<Tin, Ts, Tout, 8, 8, CP, VA, VB, VO, 4, 4>(a, ngroups, s); break;
+    case 5: e = launch_group_t<Tin, Ts, Tout, 5, 1, CP, VA, VB, VO, MB, 4>(a, ngroups, s); break;
+    case 6: e = launch_group_t<Tin, Ts, Tout, 6, 1, CP, VA, VB, VO, MB, 4>(a, ngroups, s); break;
+    case 7: e = launch_group_t<Tin, Ts, Tout, 7, 1, CP, VA, VB, VO, MB, 4>(a, ngroups, s); break;
+    case 8: e = launch_group_t<Tin, Ts, Tout, 8, 1, CP, VA, VB, VO, MB, 4>(a, ngroups, s); break;
+    case 9: e = launch_group_t<Tin, Ts, Tout, 8, 2, CP, VA, VB, VO, MB, 4>(a, ngroups, s); break;
+    case 10: e = launch_group_t<Tin, Ts, Tout, 8, 4, CP, VA, VB, VO, MB, 4>(a, ngroups, s); break;
+    case 11: e = launch_group_t<Tin, Ts, Tout, 8, 8, CP, VA, VB, VO, MB, 4>(a, ngroups, s); break;
     case 12: e = launch_group_t<Tin, Ts, Tout, 9, 8, CP, VA, VB, VO, 3, 4>(a, ngroups, s); break;
     default: return cudaErrorInvalidValue;
   }
