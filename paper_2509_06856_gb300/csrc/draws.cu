@@ -3,36 +3,57 @@
 // seed.  A permutation is the stable argsort of one 64-bit Philox key per index;
 // ties (probability ~ N'^2 / 2^65) go to the smaller index.
 //
-// GPU argsort of uniform keys: bucket by the top B = max(0, log2 N' - 10) key bits
-// (counting sort: histogram, scan, scatter), then sort each bucket (about 1024
-// entries) on (key, index) in shared memory with a bitonic network.  A bucket
-// larger than the shared-memory capacity is sorted by exact ranks instead, so the
-// result is the unique (key, index) order for every input.
+// GPU argsort of uniform keys, both permutations (P and sigma) in the same launches
+// (blockIdx.y = which one): bucket by the top B = max(0, log2 N' - 10) key bits
+// (counting sort: histogram, scan, scatter of the indices), then order each bucket
+// (about 1024 entries) in shared memory by a second counting sort on the next 8 key
+// bits followed by an insertion sort of each sub-bucket (about 4 entries) on the full
+// (key, index) pair.  Keys are recomputed from the index (Philox is cheaper than a
+// round trip through HBM).  A bucket larger than the shared-memory capacity is ordered
+// by exact ranks instead, so the result is the unique (key, index) order for every input.
 #include "slse_internal.cuh"
 
 namespace slse {
 namespace {
 
-constexpr int kSortCap = 4096;  // entries per bucket sorted in shared memory (48 KB)
-constexpr int kSortThreads = 512;
+constexpr int kSortCap = 2048;  // entries per bucket ordered in shared memory
+constexpr int kSortThreads = 256;
+constexpr int kSubBits = 8;
+constexpr int kSub = 1 << kSubBits;
 
 __host__ __device__ inline int bucket_bits(int logNp) { return logNp > 10 ? logNp - 10 : 0; }
 
-__global__ void k_keys_hist(int64_t Np, uint32_t k0, uint32_t k1, int stream, int B,
-                            unsigned long long *keys, unsigned *counts) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= Np) return;
+__device__ __forceinline__ unsigned long long sort_key(int64_t i, int stream, uint32_t k0, uint32_t k1) {
   const U4 r = philox4x32_10((uint32_t)i, (uint32_t)(i >> 32), (uint32_t)stream, 0u, k0, k1);
-  const unsigned long long key = ((unsigned long long)r.y << 32) | r.x;
-  keys[i] = key;
-  const unsigned b = B > 0 ? (unsigned)(key >> (64 - B)) : 0u;
-  atomicAdd(&counts[b], 1u);
+  return ((unsigned long long)r.y << 32) | r.x;
 }
 
-// Exclusive scan of nb counts by one CTA; writes offsets and cursor (= offsets).
-__global__ void k_scan(const unsigned *counts, int nb, unsigned *offsets, unsigned *cursor) {
+// Per-sort arrays: the two sorts (y = 0: P, y = 1: sigma) use separate copies.
+struct SortArrays {
+  uint32_t *tidx[2];
+  unsigned *counts[2], *offsets[2], *cursor[2];
+  int32_t *out[2];
+};
+
+__device__ __forceinline__ int sort_stream_id(int y) { return y == 0 ? STREAM_P : STREAM_SIGMA; }
+// Select one of the two per-sort pointers without indexing the kernel parameter at run time.
+template <class T> __device__ __forceinline__ T pick(T const (&a)[2], int y) { return y ? a[1] : a[0]; }
+
+__global__ void k_keys_hist(int64_t Np, uint32_t k0, uint32_t k1, int B, SortArrays w) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Np) return;
+  const int y = blockIdx.y;
+  const unsigned long long key = sort_key(i, sort_stream_id(y), k0, k1);
+  const unsigned b = B > 0 ? (unsigned)(key >> (64 - B)) : 0u;
+  atomicAdd(&pick(w.counts, y)[b], 1u);
+}
+
+// Exclusive scan of nb counts by one CTA per sort; writes offsets and cursor (= offsets).
+__global__ void k_scan(int nb, SortArrays w) {
   __shared__ unsigned s_part[1024];
   __shared__ unsigned s_carry;
+  const int y = blockIdx.x;
+  const unsigned *counts = pick(w.counts, y);
   if (threadIdx.x == 0) s_carry = 0;
   __syncthreads();
   for (int base = 0; base < nb; base += 1024) {
@@ -47,73 +68,110 @@ __global__ void k_scan(const unsigned *counts, int nb, unsigned *offsets, unsign
       __syncthreads();
     }
     const unsigned incl = s_part[threadIdx.x] + s_carry;
-    if (i < nb) { offsets[i] = incl - v; cursor[i] = incl - v; }
+    if (i < nb) { pick(w.offsets, y)[i] = incl - v; pick(w.cursor, y)[i] = incl - v; }
     __syncthreads();
     if (threadIdx.x == 1023) s_carry = incl;
     __syncthreads();
   }
 }
 
-__global__ void k_scatter(int64_t Np, int B, const unsigned long long *keys, unsigned *cursor,
-                          unsigned long long *tkeys, uint32_t *tidx) {
+__global__ void k_scatter(int64_t Np, uint32_t k0, uint32_t k1, int B, SortArrays w) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Np) return;
-  const unsigned long long key = keys[i];
+  const int y = blockIdx.y;
+  const unsigned long long key = sort_key(i, sort_stream_id(y), k0, k1);
   const unsigned b = B > 0 ? (unsigned)(key >> (64 - B)) : 0u;
-  const unsigned slot = atomicAdd(&cursor[b], 1u);
-  tkeys[slot] = key;
-  tidx[slot] = (uint32_t)i;
+  const unsigned slot = atomicAdd(&pick(w.cursor, y)[b], 1u);
+  pick(w.tidx, y)[slot] = (uint32_t)i;
 }
 
 __device__ __forceinline__ bool pair_gt(unsigned long long ka, uint32_t ia, unsigned long long kb, uint32_t ib) {
   return ka > kb || (ka == kb && ia > ib);
 }
 
-// One CTA per bucket; writes the sorted indices to out[offset .. offset + count).
-__global__ void __launch_bounds__(kSortThreads) k_bucket_sort(const unsigned *counts, const unsigned *offsets,
-                                                              const unsigned long long *tkeys,
-                                                              const uint32_t *tidx, int32_t *out) {
-  extern __shared__ unsigned char smem_raw[];
-  unsigned long long *sk = reinterpret_cast<unsigned long long *>(smem_raw);
-  uint32_t *si = reinterpret_cast<uint32_t *>(sk + kSortCap);
-  const unsigned cnt = counts[blockIdx.x];
-  const unsigned off = offsets[blockIdx.x];
+// One CTA per bucket (blockIdx.x) and sort (blockIdx.y); writes the ordered indices to
+// out[offset .. offset + count).
+__global__ void __launch_bounds__(kSortThreads) k_bucket_sort(uint32_t k0, uint32_t k1, int B, SortArrays w) {
+  static_assert(kSub == kSortThreads, "one sub-bucket per thread");
+  __shared__ unsigned long long s_k1[kSortCap];
+  __shared__ uint32_t s_i0[kSortCap], s_i1[kSortCap];
+  __shared__ unsigned s_cnt[kSub], s_start[kSub], s_cur[kSub];
+  const int y = blockIdx.y;
+  const int stream = sort_stream_id(y);
+  const unsigned cnt = pick(w.counts, y)[blockIdx.x];
+  const unsigned off = pick(w.offsets, y)[blockIdx.x];
+  const uint32_t *tidx = pick(w.tidx, y);
+  int32_t *out = pick(w.out, y);
   if (cnt == 0) return;
-  if (cnt <= (unsigned)kSortCap) {
-    unsigned n = 1;
-    while (n < cnt) n <<= 1;
-    for (unsigned t = threadIdx.x; t < n; t += blockDim.x) {
-      if (t < cnt) { sk[t] = tkeys[off + t]; si[t] = tidx[off + t]; }
-      else { sk[t] = ~0ull; si[t] = 0xFFFFFFFFu; }
-    }
-    __syncthreads();
-    for (unsigned k = 2; k <= n; k <<= 1) {
-      for (unsigned j = k >> 1; j > 0; j >>= 1) {
-        for (unsigned t = threadIdx.x; t < n; t += blockDim.x) {
-          const unsigned l = t ^ j;
-          if (l > t) {
-            const bool up = (t & k) == 0;
-            const bool gt = pair_gt(sk[t], si[t], sk[l], si[l]);
-            if (gt == up) {
-              const unsigned long long tk = sk[t]; sk[t] = sk[l]; sk[l] = tk;
-              const uint32_t ti = si[t]; si[t] = si[l]; si[l] = ti;
-            }
-          }
-        }
-        __syncthreads();
-      }
-    }
-    for (unsigned t = threadIdx.x; t < cnt; t += blockDim.x) out[off + t] = (int32_t)si[t];
-  } else {
+  if (cnt > (unsigned)kSortCap) {
     // exact rank of each entry among the bucket's distinct (key, index) pairs
     for (unsigned t = threadIdx.x; t < cnt; t += blockDim.x) {
-      const unsigned long long kt = tkeys[off + t];
       const uint32_t it = tidx[off + t];
+      const unsigned long long kt = sort_key(it, stream, k0, k1);
       unsigned rank = 0;
-      for (unsigned u = 0; u < cnt; ++u) rank += pair_gt(kt, it, tkeys[off + u], tidx[off + u]) ? 1u : 0u;
+      for (unsigned u = 0; u < cnt; ++u) {
+        const uint32_t iu = tidx[off + u];
+        rank += pair_gt(kt, it, sort_key(iu, stream, k0, k1), iu) ? 1u : 0u;
+      }
       out[off + rank] = (int32_t)it;
     }
+    return;
   }
+  const int shift = 64 - B - kSubBits;
+  for (int s = threadIdx.x; s < kSub; s += blockDim.x) s_cnt[s] = 0;
+  __syncthreads();
+  for (unsigned t = threadIdx.x; t < cnt; t += blockDim.x) {
+    const uint32_t i = tidx[off + t];
+    const unsigned long long key = sort_key(i, stream, k0, k1);
+    s_i0[t] = i;
+    atomicAdd(&s_cnt[(unsigned)(key >> shift) & (kSub - 1)], 1u);
+  }
+  __syncthreads();
+  // exclusive scan of the sub-bucket counts (kSub = kSortThreads entries, one per thread)
+  {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned v = s_cnt[threadIdx.x];
+    unsigned incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    __shared__ unsigned s_wsum[kSortThreads / 32];
+    if (lane == 31) s_wsum[wid] = incl;
+    __syncthreads();
+    unsigned base = 0;
+    for (int k = 0; k < wid; ++k) base += s_wsum[k];
+    s_start[threadIdx.x] = base + incl - v;
+    s_cur[threadIdx.x] = base + incl - v;
+  }
+  __syncthreads();
+  for (unsigned t = threadIdx.x; t < cnt; t += blockDim.x) {
+    const uint32_t i = s_i0[t];
+    const unsigned long long key = sort_key(i, stream, k0, k1);
+    const unsigned slot = atomicAdd(&s_cur[(unsigned)(key >> shift) & (kSub - 1)], 1u);
+    s_k1[slot] = key;
+    s_i1[slot] = i;
+  }
+  __syncthreads();
+  // insertion sort of sub-bucket s by one thread
+  {
+    const unsigned lo = s_start[threadIdx.x], n = s_cnt[threadIdx.x];
+    for (unsigned a = 1; a < n; ++a) {
+      const unsigned long long ka = s_k1[lo + a];
+      const uint32_t ia = s_i1[lo + a];
+      unsigned b = a;
+      while (b > 0 && pair_gt(s_k1[lo + b - 1], s_i1[lo + b - 1], ka, ia)) {
+        s_k1[lo + b] = s_k1[lo + b - 1];
+        s_i1[lo + b] = s_i1[lo + b - 1];
+        --b;
+      }
+      s_k1[lo + b] = ka;
+      s_i1[lo + b] = ia;
+    }
+  }
+  __syncthreads();
+  for (unsigned t = threadIdx.x; t < cnt; t += blockDim.x) out[off + t] = (int32_t)s_i1[t];
 }
 
 // Sign-folded permutation: Psd[j] = P[j] if D_j = +1, ~P[j] if D_j = -1.
@@ -141,69 +199,54 @@ __global__ void k_pos_scatter(const int32_t *sigma, int64_t s0, int64_t s1, int 
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-struct DrawsWs {
-  unsigned long long *keys, *tkeys;
-  uint32_t *tidx;
-  unsigned *counts, *offsets, *cursor;
-  int32_t *perm;
-};
-
-DrawsWs carve(void *ws, int64_t Np, int nb) {
-  char *p = static_cast<char *>(ws);
-  DrawsWs w;
-  size_t off = 0;
-  w.keys = reinterpret_cast<unsigned long long *>(p + off); off = align256(off + 8 * (size_t)Np);
-  w.tkeys = reinterpret_cast<unsigned long long *>(p + off); off = align256(off + 8 * (size_t)Np);
-  w.tidx = reinterpret_cast<uint32_t *>(p + off); off = align256(off + 4 * (size_t)Np);
-  w.perm = reinterpret_cast<int32_t *>(p + off); off = align256(off + 4 * (size_t)Np);
-  w.counts = reinterpret_cast<unsigned *>(p + off); off = align256(off + 4 * (size_t)nb);
-  w.offsets = reinterpret_cast<unsigned *>(p + off); off = align256(off + 4 * (size_t)nb);
-  w.cursor = reinterpret_cast<unsigned *>(p + off); off = align256(off + 4 * (size_t)nb);
-  return w;
-}
-
 int log2_exact(int64_t Np) {
   int l = 0;
   while ((int64_t(1) << l) < Np) ++l;
   return l;
 }
 
-cudaError_t sort_stream(int64_t Np, uint64_t seed, int stream, const DrawsWs &w, int32_t *out, cudaStream_t s) {
-  const int logNp = log2_exact(Np);
-  const int B = bucket_bits(logNp);
-  const int nb = 1 << B;
-  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-  const int T = 256;
-  const unsigned grid = (unsigned)((Np + T - 1) / T);
-  cudaError_t e = cudaMemsetAsync(w.counts, 0, 4 * (size_t)nb, s);
-  if (e != cudaSuccess) return e;
-  k_keys_hist<<<grid, T, 0, s>>>(Np, k0, k1, stream, B, w.keys, w.counts);
-  k_scan<<<1, 1024, 0, s>>>(w.counts, nb, w.offsets, w.cursor);
-  k_scatter<<<grid, T, 0, s>>>(Np, B, w.keys, w.cursor, w.tkeys, w.tidx);
-  const size_t smem = (size_t)kSortCap * (sizeof(unsigned long long) + sizeof(uint32_t));
-  k_bucket_sort<<<nb, kSortThreads, smem, s>>>(w.counts, w.offsets, w.tkeys, w.tidx, out);
-  return cudaGetLastError();
+// Workspace: per sort the scattered indices (N') and three bucket arrays; the
+// permutation P before sign folding (N').
+SortArrays carve(void *ws, int64_t Np, int nb, int32_t *sigma_out) {
+  char *p = static_cast<char *>(ws);
+  SortArrays w;
+  size_t off = 0;
+  for (int y = 0; y < 2; ++y) {
+    w.tidx[y] = reinterpret_cast<uint32_t *>(p + off); off = align256(off + 4 * (size_t)Np);
+    w.counts[y] = reinterpret_cast<unsigned *>(p + off); off = align256(off + 4 * (size_t)nb);
+    w.offsets[y] = reinterpret_cast<unsigned *>(p + off); off = align256(off + 4 * (size_t)nb);
+    w.cursor[y] = reinterpret_cast<unsigned *>(p + off); off = align256(off + 4 * (size_t)nb);
+  }
+  w.out[0] = reinterpret_cast<int32_t *>(p + off);
+  w.out[1] = sigma_out;
+  return w;
 }
 
 }  // namespace
 
 size_t draws_ws_bytes(int64_t Np) {
   const int nb = 1 << bucket_bits(log2_exact(Np));
-  return align256(8 * (size_t)Np) * 2 + align256(4 * (size_t)Np) * 2 + 3 * align256(4 * (size_t)nb) + 256;
+  return 2 * (align256(4 * (size_t)Np) + 3 * align256(4 * (size_t)nb)) + align256(4 * (size_t)Np) + 256;
 }
 
 cudaError_t launch_draws(int64_t Np, uint64_t seed, int32_t *Psd, int32_t *P, int32_t *sigma, int8_t *D,
                          void *ws, cudaStream_t s) {
-  const int nb = 1 << bucket_bits(log2_exact(Np));
-  DrawsWs w = carve(ws, Np, nb);
-  cudaError_t e = sort_stream(Np, seed, STREAM_P, w, w.perm, s);
-  if (e != cudaSuccess) return e;
+  const int logNp = log2_exact(Np);
+  const int B = bucket_bits(logNp);
+  const int nb = 1 << B;
+  SortArrays w = carve(ws, Np, nb, sigma);
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   const int T = 256;
   const unsigned grid = (unsigned)((Np + T - 1) / T);
-  k_fold_signs<<<grid, T, 0, s>>>(Np, (uint32_t)seed, (uint32_t)(seed >> 32), w.perm, Psd, P, D);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  return sort_stream(Np, seed, STREAM_SIGMA, w, sigma, s);
+  cudaError_t e;
+  for (int y = 0; y < 2; ++y)
+    if ((e = cudaMemsetAsync(w.counts[y], 0, 4 * (size_t)nb, s)) != cudaSuccess) return e;
+  k_keys_hist<<<dim3(grid, 2), T, 0, s>>>(Np, k0, k1, B, w);
+  k_scan<<<2, 1024, 0, s>>>(nb, w);
+  k_scatter<<<dim3(grid, 2), T, 0, s>>>(Np, k0, k1, B, w);
+  k_bucket_sort<<<dim3(nb, 2), kSortThreads, 0, s>>>(k0, k1, B, w);
+  k_fold_signs<<<grid, T, 0, s>>>(Np, k0, k1, w.out[0], Psd, P, D);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pos_map(const int32_t *sigma, int64_t Np, int64_t s0, int64_t s1, int log2, int32_t *pos,
