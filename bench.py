@@ -30,7 +30,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time-to-1e-8 rel-err β̂ (ms) & HBM GB/s, mixed vs FP64 GPU, N=2^22 d=512"
 TARGET = 1e-8
-WORKLOAD = "AR(1) rho=0.5 Gaussian rows, N=2^22, d=512, X fp32, sigma=0.1, beta~N(0,I)"
+def workload_name(log2n: int, d: int) -> str:
+    return f"AR(1) rho=0.5 Gaussian rows, N=2^{log2n}, d={d}, X fp32, sigma=0.1, beta~N(0,I)"
 FALLBACK_HBM = 6800.0
 
 
@@ -233,7 +234,7 @@ def run_reference(args, rank, ws):
     out = {"metric": METRIC, "value": val, "unit": "ms", "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": statistics.mean(times) * 1000.0, "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": WORKLOAD, "N": 1 << args.log2n, "d": d, "sample_rows": ns},
+           "config": {"workload": workload_name(args.log2n, d), "N": 1 << args.log2n, "d": d, "sample_rows": ns},
            "cpu_baseline": {"value": val, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle", "sample": sample},
            "e2e": {"value": val, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -379,7 +380,7 @@ def run_ours(args, rank, ws, local_rank):
         "metric": METRIC, "value": value, "unit": "ms", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": N, "d": d, "X_dtype": "fp32", "precision": "mixed_bf16",
+        "config": {"workload": workload_name(args.log2n, d), "N": N, "d": d, "X_dtype": "fp32", "precision": "mixed_bf16",
                    "schedule": f"m={sched.m[0]}..{sched.m[-1]} (x2), a_i=2, r={sched.r}, T=100, tol=5e-9",
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "l2": "inputs larger than L2 (X is 8.6 GB)", "seeds": f"sketch seeds 0..{args.steps - 1}"},
