@@ -14,6 +14,7 @@ Modules
 -------
 philox  - Philox4x32-10 (Salmon et al., SC'11), the generator both sides use.
 sketch  - random draws D, P, sigma; Walsh-Hadamard transform; SRHT (Sec. 3).
+countsketch - the CountSketch family (Sec. 2; the SLSE-FRS-CS experiment of Sec. 5).
 linalg  - Householder QR, OLS via QR (Sec. 1), triangular solves.
 slse    - schedules, a_i bound (Thm 4.3), gradient, M-IHS update, Algorithm 2.
 
@@ -22,4 +23,4 @@ Parity status: every function is pinned by the ``-m "not gpu"`` tests in
 with m_1 <= r, which the paper's theorems do not cover ("parity unpinned" for
 those intermediate values; the final estimate is pinned to OLS).
 """
-from . import philox, sketch, linalg, slse  # noqa: F401
+from . import philox, sketch, countsketch, linalg, slse  # noqa: F401

@@ -13,7 +13,10 @@
   with H-hat^{-1} v = R^{-1} R^{-T} v from S-hat X = Q R (Appendix, implementation details).
 * ``slse_fit``: Algorithm 2 step by step: one transform of [X|Y], nested prefixes of
   the sampled rows for the K sketched subproblems (a_i M-IHS steps each, 1st stage),
-  then full-data M-IHS steps (2nd stage).
+  then full-data M-IHS steps (2nd stage).  ``kind="countsketch"`` runs the same
+  iteration on the CountSketch family of ``oracle.countsketch`` (the SLSE-FRS-CS
+  experiment of Sec. 5): S_i X is the m_i-bucket sketch (no scale factor, since
+  E[S^T S] = I), S-hat X the independent r-bucket sketch.
 
 Readings taken where the paper is silent (listed in the design doc):
 * beta_0 = 0 (Thm 4.2 allows any beta_0).
@@ -30,6 +33,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
+from . import countsketch as cs
 from . import sketch as sk
 from .linalg import householder_r, solve_lower, solve_upper
 
@@ -44,22 +48,29 @@ class Schedule:
     T: int = 100
     tol: float = 0.0
     momentum_reset: bool = False
+    kind: str = "srht"   # or "countsketch"
 
     @property
     def K(self):
         return len(self.m)
 
 
-def default_schedule(N: int, d: int, T: int = 100, tol: float = 0.0, a: int = 2) -> Schedule:
+def default_schedule(N: int, d: int, T: int = 100, tol: float = 0.0, a: int = 2,
+                     kind: str = "srht") -> Schedule:
+    """Sec. 5 settings.  For the CountSketch family the sizes must be powers of two, so
+    m_1 = 8d is rounded up to the next power of two."""
     Np = sk.padded_size(N)
     r = 6 * d
     eta = d / r
     mu = (1.0 - eta) ** 2
-    m, mi = [], 8 * d
+    mi = 8 * d
+    if kind == "countsketch":
+        mi = sk.padded_size(mi)
+    m = []
     while mi <= Np // 2:
         m.append(mi)
         mi *= 2
-    return Schedule(m=m, a=[a] * len(m), r=r, mu=mu, eta=eta, T=T, tol=tol)
+    return Schedule(m=m, a=[a] * len(m), r=r, mu=mu, eta=eta, T=T, tol=tol, kind=kind)
 
 
 def ai_bound(omega: float, m_prev: float, m_i: float, d: float) -> float:
@@ -118,30 +129,40 @@ def slse_fit(X, Y, sched: Schedule, seed: int, trace: bool = False,
     X = np.asarray(X)
     N, d = X.shape
     Np = sk.padded_size(N)
-    D, P, sigma = sk.draws(Np, seed)
-    if sketch_override is None:
-        ZX = sk.hdp(X, D, P)
-        ZY = sk.hdp(Y, D, P)
+    if sched.kind == "countsketch":
+        def subproblem(m):
+            SX, SY = cs.countsketch(X, Y, m, seed)
+            return SX, SY, 1.0
+        R = householder_r(cs.countsketch_hat(X, Y, sched.r, seed)[0])
     else:
-        ZX, ZY = sketch_override
-    mK = sched.m[-1] if sched.K else 0
-    h0, h1 = sk.hessian_rows(Np, mK, sched.r)
-    SX_hat = math.sqrt(Np / sched.r) * ZX[sigma[h0:h1]]
-    R = householder_r(SX_hat)
+        D, P, sigma = sk.draws(Np, seed)
+        if sketch_override is None:
+            ZX = sk.hdp(X, D, P)
+            ZY = sk.hdp(Y, D, P)
+        else:
+            ZX, ZY = sketch_override
+        mK = sched.m[-1] if sched.K else 0
+        h0, h1 = sk.hessian_rows(Np, mK, sched.r)
+        SX_hat = math.sqrt(Np / sched.r) * ZX[sigma[h0:h1]]
+        R = householder_r(SX_hat)
+
+        def subproblem(m):
+            # S_i X = sqrt(N'/m) U with U the first m sampled rows; the gradient of the
+            # sketched problem is (N'/m) U^T (V - U beta)
+            return ZX[sigma[:m]], ZY[sigma[:m]], Np / m
 
     beta = np.zeros(d)
     beta_prev = beta.copy()
     hist = []
     t = 0
     for m, a in zip(sched.m, sched.a):
-        U = ZX[sigma[:m]]
-        V = ZY[sigma[:m]]
+        U, V, scale = subproblem(m)
         if sched.momentum_reset:
             beta_prev = beta.copy()
         for _ in range(a):
             if t >= sched.T:
                 break
-            g = (Np / m) * (U.T @ (V - U @ beta))
+            g = scale * (U.T @ (V - U @ beta))
             beta, beta_prev = mihs_step(beta, beta_prev, g, R, sched.mu, sched.eta)
             t += 1
             if trace:

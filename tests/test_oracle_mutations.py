@@ -89,3 +89,46 @@ def test_transposed_preconditioner_is_caught(monkeypatch):
     monkeypatch.setattr(slse, "hinv_apply",
                         lambda R, v: linalg.solve_lower(R.T, linalg.solve_upper(R, v)))
     _fails(tv.test_hinv_apply_inverts_sketched_hessian)
+
+
+# ---- CountSketch oracle (tests/test_oracle_countsketch.py)
+import tests.test_oracle_countsketch as tc  # noqa: E402
+from oracle import countsketch as cs  # noqa: E402
+
+
+def test_countsketch_signs_dropped_is_caught(monkeypatch):
+    good = cs.cs_hash
+    monkeypatch.setattr(cs, "cs_hash", lambda N, seed: (good(N, seed)[0], np.ones(N)))
+    _fails(tc.test_expectation_of_sts_is_identity)
+    _fails(tc.test_bucket_and_sign_uniformity)
+
+
+def test_countsketch_srht_style_scale_is_caught(monkeypatch):
+    good = cs.countsketch
+    monkeypatch.setattr(cs, "countsketch",
+                        lambda X, Y, m, seed: tuple(math.sqrt(np.asarray(X).shape[0] / m) * a for a in good(X, Y, m, seed)))
+    _fails(tc.test_dense_matrix_structure_and_product, 64, 16, 2)
+
+
+def test_countsketch_high_bits_bucket_is_caught(monkeypatch):
+    def bad(h, m):
+        l = m.bit_length() - 1
+        return (h >> np.uint64(32 - l)).astype(np.int64) if l else np.zeros(h.shape, np.int64)
+    monkeypatch.setattr(cs, "cs_buckets", bad)
+    _fails(tc.test_folding_identity, 8)
+
+
+def test_countsketch_hessian_sketch_not_independent_is_caught(monkeypatch):
+    def bad(N, seed, r):
+        h, s = cs.cs_hash(N, seed)
+        return ((h * np.uint64(r)) >> np.uint64(32)).astype(np.int64), s
+    monkeypatch.setattr(cs, "hat_hash", bad)
+    _fails(tc.test_bucket_and_sign_uniformity)
+
+
+def test_countsketch_fold_wrong_offset_is_caught(monkeypatch):
+    def bad(SX, m):
+        M = SX.shape[0]
+        return SX.reshape((m, M // m) + SX.shape[1:]).sum(axis=1)   # adds neighbours, not b + q m
+    monkeypatch.setattr(cs, "fold", bad)
+    _fails(tc.test_folding_identity, 8)
