@@ -57,7 +57,19 @@ typedef enum {
 
 typedef enum { SLSE_F64 = 0, SLSE_F32 = 1, SLSE_BF16 = 2 } slse_dtype;
 
-typedef enum { SLSE_SRHT = 0, SLSE_COUNTSKETCH = 1, SLSE_GAUSSIAN = 2 } slse_sketch_kind;
+/* Sketch families.
+ * SLSE_SRHT: subsampled randomized Hadamard transform (Sec. 3), the paper's method.
+ * SLSE_COUNTSKETCH: the sparse projection of Sec. 2 (one random sign per column, in a
+ *   uniformly random row), used in place of the SRHT in the SLSE-FRS-CS experiment of
+ *   Sec. 5.  Row k of [X|Y] goes with sign s(k) to bucket h(k) mod m; h(k) and s(k) are
+ *   word 0 and bit 0 of word 1 of Philox4x32-10 at counter (k, 3).  Sizes are powers of
+ *   two, so a smaller sketch of the family is a fold of a larger one.  No scale factor
+ *   (E[S^T S] = I).
+ * SLSE_COUNTSKETCH_HAT: the independent CountSketch used for the Hessian sketch with the
+ *   CountSketch family: m buckets (any m >= 1), bucket floor(w0 m / 2^32) and sign bit 0
+ *   of w1 at counter (k, 4).
+ * SLSE_GAUSSIAN: reserved (not built). */
+typedef enum { SLSE_SRHT = 0, SLSE_COUNTSKETCH = 1, SLSE_GAUSSIAN = 2, SLSE_COUNTSKETCH_HAT = 3 } slse_sketch_kind;
 
 /* Arithmetic of the path.
  * SLSE_PREC_FP64: every step in FP64 (X stored F64 or F32; F32 values are widened exactly).
@@ -85,7 +97,9 @@ typedef struct {
   double mu, eta;       /* M-IHS step and momentum */
   int32_t T;            /* cap on the total number of iterations (both stages) */
   double tol;           /* 2nd stage stops when ||b+ - b|| <= tol (1-rho)/rho ||b+||, rho = sqrt(d/r); <= 0: run to T */
-  int32_t kind;         /* slse_sketch_kind (only SLSE_SRHT in this build) */
+  int32_t kind;         /* SLSE_SRHT, or SLSE_COUNTSKETCH: S_i X is the 2^l-bucket CountSketch
+                           (all m_i powers of two, unscaled) and S-hat X the independent
+                           r-bucket SLSE_COUNTSKETCH_HAT sketch */
   int32_t prec;         /* slse_precision */
   int32_t momentum_reset; /* 0: momentum carries across subproblems (Algorithm 2's global t);
                              1: beta_{-1} = beta_0 at each subproblem and at the 2nd stage (proof of Thm 4.1) */
@@ -113,8 +127,8 @@ typedef struct {
   int32_t count;      /* out: iterations recorded */
 } slse_trace;
 
-/* Workspace query.  op: SLSE_OP_FIT (sched required), SLSE_OP_SKETCH (arg = m, prec in
- * sched->prec if sched != NULL else FP64), SLSE_OP_GRAD, SLSE_OP_DRAWS (arg = N), SLSE_OP_QR
+/* Workspace query.  op: SLSE_OP_FIT (sched required), SLSE_OP_SKETCH (arg = m; prec and kind
+ * from sched->prec and sched->kind if sched != NULL, else FP64 SRHT), SLSE_OP_GRAD, SLSE_OP_DRAWS (arg = N), SLSE_OP_QR
  * (arg = r).  Returns 0 for invalid arguments. */
 enum { SLSE_OP_FIT = 0, SLSE_OP_SKETCH = 1, SLSE_OP_GRAD = 2, SLSE_OP_DRAWS = 3, SLSE_OP_QR = 4 };
 size_t slse_workspace_size(const slse_problem *prob, const slse_schedule *sched, int32_t op, int64_t arg);
@@ -129,9 +143,14 @@ slse_status slse_fit(const slse_problem *prob, const slse_schedule *sched, uint6
                      double *beta_out, slse_report *report, slse_trace *trace,
                      void *workspace, size_t ws_bytes, slse_stream_t stream);
 
-/* One SRHT sketch of size m (Sec. 3): SX = sqrt(N'/m) * rows sigma[0..m) of H D P X_pad / sqrt(N'),
- * SY likewise.  prec FP64 -> SX, SY are double; MIXED_BF16 -> bf16.  SX: device m x ldsx
- * (ldsx >= d), SY: device m.  Asynchronous on `stream`. */
+/* One sketch of size m.  kind SLSE_SRHT (Sec. 3): SX = sqrt(N'/m) * rows sigma[0..m) of
+ * H D P X_pad / sqrt(N'), SY likewise.  kind SLSE_COUNTSKETCH (Sec. 2; m a power of two,
+ * else SLSE_EINVAL): row b of SX is the signed sum of the rows of X in bucket b.  kind
+ * SLSE_COUNTSKETCH_HAT: the same with the Hessian-sketch hash into m buckets.  prec FP64 ->
+ * SX, SY are double; MIXED_BF16 -> bf16 (CountSketch sums accumulated in FP32, in row
+ * order within a bucket, so the result is deterministic).  SX: device m x ldsx (ldsx >= d),
+ * SY: device m.  Asynchronous on `stream`; the workspace size comes from
+ * slse_workspace_size(SLSE_OP_SKETCH) with sched->kind and sched->prec set. */
 slse_status slse_sketch(const slse_problem *prob, int32_t kind, int32_t prec, uint64_t seed, int64_t m,
                         void *SX, int64_t ldsx, void *SY, void *workspace, size_t ws_bytes,
                         slse_stream_t stream);
@@ -181,6 +200,12 @@ slse_status slse_qr(const double *A, int64_t r, int32_t d, int64_t lda, double *
  * Returns K (the number of sizes the schedule wants; > cap means truncated). */
 int32_t slse_default_schedule(int64_t N, int32_t d, slse_schedule *out, int64_t *m_buf, int32_t *a_buf,
                               int32_t cap);
+
+/* The same defaults for a given sketch family: kind SLSE_SRHT as above; kind
+ * SLSE_COUNTSKETCH with m_1 = 8d rounded up to a power of two (the family's sizes are
+ * powers of two).  Returns -1 for other kinds. */
+int32_t slse_default_schedule_for(int64_t N, int32_t d, int32_t kind, slse_schedule *out, int64_t *m_buf,
+                                  int32_t *a_buf, int32_t cap);
 
 /* Theorem 4.3 lower bound on the inner iterations: log_3[((1+omega) r + 1)/omega] with
  * r = sqrt((m_i - d)/(m_prev - d)).  Host-only.  Returns NaN for m_prev <= d or omega <= 0. */

@@ -27,7 +27,8 @@ _lib = ctypes.CDLL(LIB_PATH)
 # ----------------------------------------------------------------------------- C types
 OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ENUMERIC, ETIMEOUT = range(7)
 F64, F32, BF16 = 0, 1, 2
-SRHT, COUNTSKETCH, GAUSSIAN = 0, 1, 2
+SRHT, COUNTSKETCH, GAUSSIAN, COUNTSKETCH_HAT = 0, 1, 2, 3
+KIND = {"srht": SRHT, "countsketch": COUNTSKETCH, "countsketch_hat": COUNTSKETCH_HAT}
 PREC = {"fp64": 0, "mixed_bf16": 1, "mixed_fp8": 2}
 OP_FIT, OP_SKETCH, OP_GRAD, OP_DRAWS, OP_QR = range(5)
 
@@ -78,6 +79,9 @@ _lib.slse_qr.argtypes = [_vp, _i64, _i32, _i64, _vp, _vp, _vp, _sz, _vp]
 _lib.slse_default_schedule.restype = _i32
 _lib.slse_default_schedule.argtypes = [_i64, _i32, ctypes.POINTER(CSchedule), ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(ctypes.c_int32), _i32]
+_lib.slse_default_schedule_for.restype = _i32
+_lib.slse_default_schedule_for.argtypes = [_i64, _i32, _i32, ctypes.POINTER(CSchedule), ctypes.POINTER(ctypes.c_int64),
+                                           ctypes.POINTER(ctypes.c_int32), _i32]
 _lib.slse_ai_bound.restype = ctypes.c_double
 _lib.slse_ai_bound.argtypes = [ctypes.c_double, _i64, _i64, _i32]
 _lib.slse_status_string.restype = ctypes.c_char_p
@@ -85,7 +89,8 @@ _lib.slse_status_string.argtypes = [_i32]
 _lib.slse_version.restype = _i32
 
 EXPORTED = ["slse_workspace_size", "slse_fit", "slse_sketch", "slse_grad", "slse_grad_noalloc", "slse_draws", "slse_qr",
-            "slse_default_schedule", "slse_ai_bound", "slse_status_string", "slse_version"]
+            "slse_default_schedule", "slse_default_schedule_for", "slse_ai_bound", "slse_status_string",
+            "slse_version"]
 
 
 class SlseError(RuntimeError):
@@ -133,16 +138,18 @@ class Schedule:
                          1 if self.momentum_reset else 0)
 
 
-def default_schedule(N: int, d: int, prec: str = "fp64", T: int = 100, tol: float = 0.0) -> Schedule:
-    """The paper's experimental schedule (Sec. 5 preamble), from the library."""
+def default_schedule(N: int, d: int, prec: str = "fp64", T: int = 100, tol: float = 0.0,
+                     kind: str = "srht") -> Schedule:
+    """The paper's experimental schedule (Sec. 5 preamble), from the library; kind "countsketch"
+    rounds m_1 = 8d up to a power of two."""
     c = CSchedule()
     mb = (ctypes.c_int64 * 64)()
     ab = (ctypes.c_int32 * 64)()
-    K = _lib.slse_default_schedule(N, d, ctypes.byref(c), mb, ab, 64)
+    K = _lib.slse_default_schedule_for(N, d, KIND[kind], ctypes.byref(c), mb, ab, 64)
     if K < 0 or K > 64:
         raise ValueError("invalid problem size")
     return Schedule(m=list(mb[:K]), a=list(ab[:K]), r=c.r, mu=c.mu, eta=c.eta, T=T, tol=tol, prec=prec,
-                    momentum_reset=bool(c.momentum_reset))
+                    momentum_reset=bool(c.momentum_reset), kind=c.kind)
 
 
 # ----------------------------------------------------------------------------- helpers
@@ -229,15 +236,16 @@ def fit(X, Y, schedule: Schedule | None = None, seed: int = 0, workspace=None, t
     return out
 
 
-def sketch(X, Y, m: int, seed: int = 0, prec: str = "fp64", workspace=None, stream=None):
-    """slse_sketch: (S X, S Y) for one SRHT sketch of size m.  FP64 -> float64, mixed -> bfloat16."""
+def sketch(X, Y, m: int, seed: int = 0, prec: str = "fp64", workspace=None, stream=None, kind: str = "srht"):
+    """slse_sketch: (S X, S Y) for one sketch of size m (kind "srht", "countsketch" or
+    "countsketch_hat").  FP64 -> float64, mixed -> bfloat16."""
     torch = _torch()
     p = problem(X, Y)
     dt = torch.float64 if prec == "fp64" else torch.bfloat16
     SX = torch.empty((m, p.d), dtype=dt, device=X.device)
     SY = torch.empty(m, dtype=dt, device=X.device)
     ws_ptr, ws_len = (workspace.data_ptr(), workspace.numel()) if workspace is not None else (None, 0)
-    st = _lib.slse_sketch(ctypes.byref(p), SRHT, PREC[prec], seed, m, SX.data_ptr(), p.d, SY.data_ptr(), ws_ptr,
+    st = _lib.slse_sketch(ctypes.byref(p), KIND[kind], PREC[prec], seed, m, SX.data_ptr(), p.d, SY.data_ptr(), ws_ptr,
                           ws_len, _stream(stream))
     _check(st, "slse_sketch")
     return SX, SY

@@ -58,7 +58,10 @@ struct Sched {
   int64_t r;
   double mu, eta, tol;
   int T, prec, momentum_reset;
+  int kind = SLSE_SRHT;
 };
+
+bool is_pow2(int64_t m) { return m >= 1 && (m & (m - 1)) == 0; }
 
 bool make_sched(const slse_problem *p, const slse_schedule *s, Sched &o) {
   const int64_t Np = padded(p->N);
@@ -72,10 +75,11 @@ bool make_sched(const slse_problem *p, const slse_schedule *s, Sched &o) {
     o.a.assign(ab, ab + K);
     o.r = d.r; o.mu = d.mu; o.eta = d.eta; o.tol = d.tol; o.T = d.T; o.prec = d.prec;
     o.momentum_reset = d.momentum_reset;
+    o.kind = SLSE_SRHT;
     return true;
   }
   if (s->K < 0 || (s->K > 0 && (!s->m || !s->a))) return false;
-  if (s->kind != SLSE_SRHT) return false;
+  if (s->kind != SLSE_SRHT && s->kind != SLSE_COUNTSKETCH) return false;
   if (s->prec != SLSE_PREC_FP64 && s->prec != SLSE_PREC_MIXED_BF16) return false;
   if (s->prec == SLSE_PREC_MIXED_BF16 && p->dtype != SLSE_F32) return false;
   if (s->r < p->d || s->r > Np || s->T < 0) return false;
@@ -86,8 +90,12 @@ bool make_sched(const slse_problem *p, const slse_schedule *s, Sched &o) {
     if (o.m[i] < 1 || o.m[i] > Np || o.a[i] < 0) return false;
     if (i > 0 && o.m[i] <= o.m[i - 1]) return false;
   }
+  if (s->kind == SLSE_COUNTSKETCH)
+    for (int i = 0; i < s->K; ++i)
+      if (!is_pow2(o.m[i])) return false;  // the nested CountSketch family has sizes 2^l
   o.r = s->r; o.mu = s->mu; o.eta = s->eta; o.tol = s->tol; o.T = s->T; o.prec = s->prec;
   o.momentum_reset = s->momentum_reset;
+  o.kind = s->kind;
   return true;
 }
 
@@ -104,6 +112,9 @@ struct Layout {
 struct FitLayout {
   int64_t Np, n_samp, h0, ldu;
   SrhtPlan sp;
+  bool cs;                  // CountSketch family instead of the SRHT
+  CsPlan csp;
+  std::vector<int64_t> lvl_off;  // CountSketch: first row in U of the sketch of each schedule size
   int nblk;
   bool host_in;
   size_t o_xin, o_yin;
@@ -119,20 +130,29 @@ FitLayout fit_layout(const slse_problem *p, const Sched &s, int nsm) {
   const int d = p->d;
   L.Np = padded(p->N);
   L.sp = srht_plan(L.Np);
+  L.cs = s.kind == SLSE_COUNTSKETCH;
   const int64_t mK = s.m.empty() ? 0 : s.m.back();
-  if (mK + s.r <= L.Np) { L.h0 = mK; L.n_samp = mK + s.r; }
+  if (L.cs) {
+    // U holds the sketch of every schedule size, in schedule order, then the r rows of S-hat
+    int64_t off = 0;
+    for (int64_t m : s.m) { L.lvl_off.push_back(off); off += m; }
+    L.h0 = off;
+    L.n_samp = off + s.r;
+    L.csp = cs_plan(p->N, d, s.prec, s.m.empty() ? 0 : s.m.front(), mK, s.r);
+  } else if (mK + s.r <= L.Np) { L.h0 = mK; L.n_samp = mK + s.r; }
   else { L.h0 = 0; L.n_samp = mK > s.r ? mK : s.r; }
   L.ldu = (d + 7) & ~int64_t(7);
   const size_t eu = elem_bytes_u(s.prec);
   L.nblk = 2 * (nsm > 0 ? nsm : 152);
   Layout w;
   L.o_state = w.take(kStateBytes);
-  L.o_psd = w.take(4 * (size_t)L.Np);
-  L.o_sigma = w.take(4 * (size_t)L.Np);
-  L.o_pos = w.take(4 * (size_t)L.Np);
-  size_t big = draws_ws_bytes(L.Np);
-  const size_t wbytes = L.sp.single ? 0 : (size_t)L.Np * L.ldu * eu;
-  const size_t wybytes = L.sp.single ? 0 : (size_t)L.Np * eu;
+  const size_t nperm = L.cs ? 0 : 4 * (size_t)L.Np;
+  L.o_psd = w.take(nperm);
+  L.o_sigma = w.take(nperm);
+  L.o_pos = w.take(nperm);
+  size_t big = L.cs ? L.csp.total : draws_ws_bytes(L.Np);
+  const size_t wbytes = (L.sp.single || L.cs) ? 0 : (size_t)L.Np * L.ldu * eu;
+  const size_t wybytes = (L.sp.single || L.cs) ? 0 : (size_t)L.Np * eu;
   if (wbytes + align256(wybytes) + 256 > big) big = align256(wbytes) + align256(wybytes);
   L.o_big = w.take(big);
   L.o_wy = L.o_big + align256(wbytes);
@@ -376,24 +396,46 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
   k_init_state<<<1, 32, 0, st>>>(dst, 0);
   CK(cudaGetLastError());
   ++kernels;
-  // a1: random draws
-  CK(launch_draws(L.Np, seed, Psd, nullptr, sigma, nullptr, big, st));
-  kernels += 9;
-  CK(launch_pos_map(sigma, L.Np, 0, L.n_samp, L.sp.single ? L.sp.logN : L.sp.log2, pos, st));
-  kernels += 1;
-  CK(cudaEventRecord(e_draws, st));
-  if (L.host_in) CK(cudaStreamWaitEvent(st, e_copied, 0));
-  // a2-a4: SRHT into the sampled rows (U = Z[sigma] with Z = H D P X / sqrt(N'); sketch scales applied later)
-  CK(launch_srht(L.sp, s.prec, p->dtype, p->X, p->ldx, p->Y, p->N, d, Psd, pos, big, WY, L.ldu, U, V, L.ldu,
-                 1.0 / std::sqrt((double)L.Np), st, L.sp.single ? nullptr : e_mid));
-  kernels += L.sp.single ? 1 : 2;
+  const size_t eu = elem_bytes_u(s.prec);
+  if (L.cs) {
+    // CountSketch family (Sec. 2; SLSE-FRS-CS of Sec. 5): its hashes are drawn inside the
+    // one sort-and-gather pass, so the draws phase is empty.
+    CK(cudaEventRecord(e_draws, st));
+    if (L.host_in) CK(cudaStreamWaitEvent(st, e_copied, 0));
+    void *lvX[25] = {}, *lvY[25] = {};
+    for (size_t i = 0; i < s.m.size(); ++i) {
+      int l = 0;
+      while ((int64_t(1) << l) < s.m[i]) ++l;
+      lvX[l] = static_cast<char *>(U) + (size_t)L.lvl_off[i] * L.ldu * eu;
+      lvY[l] = static_cast<char *>(V) + (size_t)L.lvl_off[i] * eu;
+    }
+    CK(launch_countsketch(L.csp, p->dtype, p->X, p->ldx, p->Y, seed, lvX, lvY, L.ldu,
+                          static_cast<char *>(U) + (size_t)L.h0 * L.ldu * eu, static_cast<char *>(V) + (size_t)L.h0 * eu,
+                          L.ldu, big, st));
+    kernels += 12;
+    CK(cudaEventRecord(e_mid, st));
+  } else {
+    // a1: random draws
+    CK(launch_draws(L.Np, seed, Psd, nullptr, sigma, nullptr, big, st));
+    kernels += 9;
+    CK(launch_pos_map(sigma, L.Np, 0, L.n_samp, L.sp.single ? L.sp.logN : L.sp.log2, pos, st));
+    kernels += 1;
+    CK(cudaEventRecord(e_draws, st));
+    if (L.host_in) CK(cudaStreamWaitEvent(st, e_copied, 0));
+    // a2-a4: SRHT into the sampled rows (U = Z[sigma] with Z = H D P X / sqrt(N'); sketch scales applied later)
+    CK(launch_srht(L.sp, s.prec, p->dtype, p->X, p->ldx, p->Y, p->N, d, Psd, pos, big, WY, L.ldu, U, V, L.ldu,
+                   1.0 / std::sqrt((double)L.Np), st, L.sp.single ? nullptr : e_mid));
+    kernels += L.sp.single ? 1 : 2;
+  }
   CK(cudaEventRecord(e_sketch, st));
+  // sketch scales: SRHT S_i X = sqrt(N'/m_i) U[rows], S-hat X = sqrt(N'/r) U[h0 ..]; CountSketch: 1
+  auto sq_scale = [&](int64_t m) { return L.cs ? 1.0 : (double)L.Np / (double)m; };
   // a5: R of S-hat X = sqrt(N'/r) U[h0 : h0 + r], then H-hat^{-1} = R^{-1} R^{-T}.  FP64 path:
   // Householder QR.  Mixed path: FP64 Cholesky of the exactly accumulated Gram matrix of the
   // BF16 rows (the same R), with the Householder QR as fallback on a non-positive pivot.
   bool use_qr = !mixed;
   if (mixed) {
-    CK(launch_gram_chol(U, L.ldu, L.h0, s.r, d, (double)L.Np / (double)s.r, R, Hinv, base + L.o_chol, dst, st));
+    CK(launch_gram_chol(U, L.ldu, L.h0, s.r, d, sq_scale(s.r), R, Hinv, base + L.o_chol, dst, st));
     const int nt = (d + 31) / 32;
     kernels += 2 + 3 * nt + 2;
     DevState *mb = t_mailbox.get();
@@ -408,7 +450,7 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     }
   }
   if (use_qr) {
-    CK(launch_gather_hessian_rows(s.prec, U, L.ldu, L.h0, s.r, d, std::sqrt((double)L.Np / (double)s.r), A, st));
+    CK(launch_gather_hessian_rows(s.prec, U, L.ldu, L.h0, s.r, d, std::sqrt(sq_scale(s.r)), A, st));
     CK(launch_qr(A, s.r, d, d, R, Hinv, qrws, dst, st));
     kernels += 4;
   }
@@ -425,10 +467,14 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
   for (size_t i = 0; i < s.m.size() && t < T; ++i) {
     const int64_t m = s.m[i];
     const int nb = grad_blocks(m, L.nblk);
+    // SRHT: the prefix U[0:m_i]; CountSketch: the block of U holding S_i X
+    const size_t r0w = L.cs ? (size_t)L.lvl_off[i] : 0;
+    const void *Ui = static_cast<const char *>(U) + r0w * L.ldu * eu;
+    const void *Vi = static_cast<const char *>(V) + r0w * eu;
     for (int j = 0; j < s.a[i] && t < T; ++j) {
-      CK(launch_grad(mixed ? GM_STAGE1_BF16 : GM_STAGE1_F64, mixed ? SLSE_BF16 : SLSE_F64, U, L.ldu, V, m, d,
+      CK(launch_grad(mixed ? GM_STAGE1_BF16 : GM_STAGE1_F64, mixed ? SLSE_BF16 : SLSE_F64, Ui, L.ldu, Vi, m, d,
                      ring, dst, nullptr, nullptr, nullptr, part, nb, 0, st));
-      CK(launch_reduce(part, nb, d, (double)L.Np / (double)m, g, dst, 0, st));
+      CK(launch_reduce(part, nb, d, sq_scale(m), g, dst, 0, st));
       ua.first = (j == 0 && s.momentum_reset) || t == 0;
       ua.stage2 = 0; ua.thr = 0.0; ua.mixed = 0; ua.check_done = 0;
       CK(launch_update(ua, dst, st));
@@ -490,8 +536,8 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     rep->ms_copy_in = L.host_in ? ms_between(e_start, e_copied) : 0.0;
     rep->ms_draws = ms_between(e_start, e_draws);
     rep->ms_sketch = ms_between(e_draws, e_sketch);
-    rep->ms_srht_pass1 = L.sp.single ? rep->ms_sketch : ms_between(e_draws, e_mid);
-    rep->ms_srht_pass2 = L.sp.single ? 0.0 : ms_between(e_mid, e_sketch);
+    rep->ms_srht_pass1 = (L.sp.single || L.cs) ? rep->ms_sketch : ms_between(e_draws, e_mid);
+    rep->ms_srht_pass2 = (L.sp.single || L.cs) ? 0.0 : ms_between(e_mid, e_sketch);
     rep->ms_qr = ms_between(e_sketch, e_qr);
     rep->ms_stage1 = ms_between(e_qr, e_s1);
     rep->ms_total = ms_between(e_start, e_end);
@@ -509,7 +555,8 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     rep->rebases = fin.rebases;
     const double bx = p->dtype == SLSE_F64 ? 8.0 : 4.0, bu = (double)elem_bytes_u(s.prec);
     double bytes = 0.0;
-    if (L.sp.single) bytes += (double)p->N * (d + 1) * bx + (double)L.n_samp * (d + 1) * bu;
+    if (L.cs) bytes += 2.0 * (double)p->N * (d + 1) * bx + (double)L.n_samp * (d + 1) * bu;  // nested and S-hat passes
+    else if (L.sp.single) bytes += (double)p->N * (d + 1) * bx + (double)L.n_samp * (d + 1) * bu;
     else bytes += (double)p->N * (d + 1) * bx + 2.0 * (double)L.Np * (d + 1) * bu + (double)L.n_samp * (d + 1) * bu;
     for (size_t i = 0; i < s.m.size(); ++i) bytes += (double)s.a[i] * (double)s.m[i] * (d + 1) * bu;
     // a 2nd-stage pass reads X and one N-vector (Y in FP64 / rebase passes, r0 otherwise)
@@ -542,6 +589,9 @@ size_t slse_workspace_size(const slse_problem *prob, const slse_schedule *sched,
     case SLSE_OP_SKETCH: {
       if (!valid_problem(prob)) return 0;
       const int prec = sched ? sched->prec : SLSE_PREC_FP64;
+      const int kind = sched ? sched->kind : SLSE_SRHT;
+      if (kind == SLSE_COUNTSKETCH) return is_pow2(arg) ? cs_plan(prob->N, prob->d, prec, arg, arg, 0).total : 0;
+      if (kind == SLSE_COUNTSKETCH_HAT) return arg >= 1 ? cs_plan(prob->N, prob->d, prec, 0, 0, arg).total : 0;
       return sketch_layout(prob, prec).total;
     }
     case SLSE_OP_GRAD:
@@ -580,12 +630,28 @@ slse_status slse_sketch(const slse_problem *prob, int32_t kind, int32_t prec, ui
                         int64_t ldsx, void *SY, void *workspace, size_t ws_bytes, slse_stream_t stream) {
   if (!valid_problem(prob) || !SX || !SY) return SLSE_EINVAL;
   if (is_host_pointer(prob->X) || is_host_pointer(prob->Y)) return SLSE_EINVAL;
-  if (kind != SLSE_SRHT) return SLSE_EINVAL;
+  if (kind != SLSE_SRHT && kind != SLSE_COUNTSKETCH && kind != SLSE_COUNTSKETCH_HAT) return SLSE_EINVAL;
   if (prec != SLSE_PREC_FP64 && prec != SLSE_PREC_MIXED_BF16) return SLSE_EINVAL;
   if (prec == SLSE_PREC_MIXED_BF16 && prob->dtype != SLSE_F32) return SLSE_EINVAL;
   const int64_t Np = padded(prob->N);
   if (m < 1 || m > Np || ldsx < prob->d) return SLSE_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
+  if (kind != SLSE_SRHT) {
+    if (kind == SLSE_COUNTSKETCH && !is_pow2(m)) return SLSE_EINVAL;
+    const bool hat = kind == SLSE_COUNTSKETCH_HAT;
+    const CsPlan pl = hat ? cs_plan(prob->N, prob->d, prec, 0, 0, m) : cs_plan(prob->N, prob->d, prec, m, m, 0);
+    Workspace W;
+    slse_status a = acquire(W, workspace, ws_bytes, pl.total, st);
+    if (a != SLSE_OK) return a;
+    void *lvX[25] = {}, *lvY[25] = {};
+    if (!hat) {
+      lvX[pl.L] = SX;
+      lvY[pl.L] = SY;
+    }
+    CK(launch_countsketch(pl, prob->dtype, prob->X, prob->ldx, prob->Y, seed, lvX, lvY, ldsx, hat ? SX : nullptr,
+                          hat ? SY : nullptr, ldsx, W.ptr, st));
+    return SLSE_OK;
+  }
   const SketchLayout L = sketch_layout(prob, prec);
   Workspace W;
   slse_status a = acquire(W, workspace, ws_bytes, L.total, st);
@@ -662,10 +728,18 @@ slse_status slse_qr(const double *A, int64_t r, int32_t d, int64_t lda, double *
 }
 
 int32_t slse_default_schedule(int64_t N, int32_t d, slse_schedule *out, int64_t *m_buf, int32_t *a_buf, int32_t cap) {
+  return slse_default_schedule_for(N, d, SLSE_SRHT, out, m_buf, a_buf, cap);
+}
+
+int32_t slse_default_schedule_for(int64_t N, int32_t d, int32_t kind, slse_schedule *out, int64_t *m_buf,
+                                  int32_t *a_buf, int32_t cap) {
   if (!out || N < 1 || d < 1) return -1;
+  if (kind != SLSE_SRHT && kind != SLSE_COUNTSKETCH) return -1;
   const int64_t Np = padded(N);
   int32_t K = 0;
-  for (int64_t m = 8 * (int64_t)d; m <= Np / 2; m *= 2) {
+  // CountSketch sizes are powers of two: m_1 = 8d rounded up
+  const int64_t m1 = kind == SLSE_COUNTSKETCH ? padded(8 * (int64_t)d) : 8 * (int64_t)d;
+  for (int64_t m = m1; m <= Np / 2; m *= 2) {
     if (K < cap && m_buf && a_buf) {
       m_buf[K] = m;
       a_buf[K] = 2;
@@ -681,7 +755,7 @@ int32_t slse_default_schedule(int64_t N, int32_t d, slse_schedule *out, int64_t 
   out->mu = (1.0 - out->eta) * (1.0 - out->eta);
   out->T = 100;
   out->tol = 0.0;
-  out->kind = SLSE_SRHT;
+  out->kind = kind;
   out->prec = SLSE_PREC_FP64;
   out->momentum_reset = 0;  // Algorithm 2: one global counter t, momentum carries
   return K;

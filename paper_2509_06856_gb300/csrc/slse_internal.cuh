@@ -104,6 +104,26 @@ constexpr int64_t kMaxPaddedRows = int64_t(1) << 24;  // N' limit of this build
 bool is_host_pointer(const void *ptr);
 bool valid_problem(const slse_problem *p);
 
+// countsketch.cu: the CountSketch family (nested sizes 2^l, l1 <= l <= L, and an
+// independent r-row Hessian sketch) in one sort and one pass over the rows.
+struct CsPlan {
+  int64_t N;
+  int d, prec;
+  int64_t r;        // Hessian-sketch rows (0: none)
+  int L, l1;        // log2 of the largest and smallest nested sizes (-1: none)
+  bool big;         // top-level buckets of >= 64 rows: one CTA per bucket
+  int F;            // levels folded in registers below L by the warp kernel
+  int ib, Bn, rb, Bh;
+  int64_t lds;      // leading dimension of the working-precision scratch rows
+  size_t o_sort0, o_sort1, o_rows0, o_rows1, o_st0, o_st1, o_scr0, o_scr1, total;
+};
+CsPlan cs_plan(int64_t N, int d, int prec, int64_t m_min, int64_t m_max, int64_t r);
+// lvX[l] / lvY[l] (l <= 24, nullable): the 2^l-row sketch in natural bucket order (ld ldo);
+// hatX / hatY (nullable when r = 0): the Hessian sketch (ld ldh).  ws: pl.total bytes.
+cudaError_t launch_countsketch(const CsPlan &pl, int xdtype, const void *X, int64_t ldx, const void *Y, uint64_t seed,
+                               void *const *lvX, void *const *lvY, int64_t ldo, void *hatX, void *hatY, int64_t ldh,
+                               void *ws, cudaStream_t s);
+
 // draws.cu
 size_t draws_ws_bytes(int64_t Np);
 cudaError_t launch_draws(int64_t Np, uint64_t seed, int32_t *Psd /*N', sign-folded P*/,

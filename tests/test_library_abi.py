@@ -90,3 +90,27 @@ def test_workspace_size_is_monotone_in_problem_size(lib):
         sch = slse.default_schedule(N, 64, prec="mixed_bf16").to_c()
         sizes.append(slse._lib.slse_workspace_size(ctypes.byref(p), ctypes.byref(sch), slse.OP_FIT, 0))
     assert 0 < sizes[0] < sizes[1] < sizes[2]
+
+
+def test_countsketch_host_side(lib):
+    import paper_2509_06856_gb300 as slse
+    from oracle import slse as osl
+    for N, d in [(20000, 50), (1 << 22, 512), (1 << 16, 24)]:
+        a = slse.default_schedule(N, d, kind="countsketch")
+        b = osl.default_schedule(N, d, kind="countsketch")
+        assert a.m == b.m and a.a == b.a and a.r == b.r and a.kind == slse.COUNTSKETCH
+        assert all(m & (m - 1) == 0 for m in a.m)
+    c = slse.CSchedule()
+    assert slse._lib.slse_default_schedule_for(1000, 10, slse.GAUSSIAN, ctypes.byref(c), None, None, 0) == -1
+    beta = (ctypes.c_double * 4)()
+    good = slse.CProblem(100, 4, slse.F64, 256, 4, 512)
+    sch = slse.Schedule(m=[24, 48], a=[2, 2], r=24, mu=0.7, eta=0.1, kind=slse.COUNTSKETCH).to_c()  # not 2^l
+    assert slse._lib.slse_fit(ctypes.byref(good), ctypes.byref(sch), 0, beta, None, None, None, 0, None) == slse.EINVAL
+    assert slse._lib.slse_workspace_size(ctypes.byref(good), ctypes.byref(sch), slse.OP_FIT, 0) == 0
+    ok = slse.Schedule(m=[16, 32], a=[2, 2], r=24, mu=0.7, eta=0.1, kind=slse.COUNTSKETCH).to_c()
+    assert slse._lib.slse_workspace_size(ctypes.byref(good), ctypes.byref(ok), slse.OP_FIT, 0) > 0
+    assert slse._lib.slse_workspace_size(ctypes.byref(good), ctypes.byref(ok), slse.OP_SKETCH, 48) == 0
+    assert slse._lib.slse_workspace_size(ctypes.byref(good), ctypes.byref(ok), slse.OP_SKETCH, 64) > 0
+    sch = slse.Schedule(m=[16], a=[2], r=24, mu=0.7, eta=0.1, kind=slse.GAUSSIAN).to_c()         # not built
+    assert slse._lib.slse_fit(ctypes.byref(good), ctypes.byref(sch), 0, beta, None, None, None, 0, None) == slse.EINVAL
+    assert slse._lib.slse_sketch(ctypes.byref(good), slse.COUNTSKETCH, 0, 0, 48, 1, 4, 1, None, 0, None) == slse.EINVAL
