@@ -14,11 +14,12 @@
 //      sorted list, with its rows in index order (a fixed summation order).  The
 //      Hessian sketch's list is sorted in the same launch.
 //   2. Run starts of each group of buckets (k_group_starts).
-//   3. Top levels: one warp per group of 2^F level-L buckets (k_cs_nested).  The warp
-//      streams the group's rows (lanes hold 16 columns each, one coalesced row read per
-//      step), forms the level-L bucket sums in FP32 (FP64 on the FP64 path) and folds
-//      them pairwise in registers down to level L - F, writing each level's rows; the
-//      level L - F sums also go to a scratch buffer at working precision.
+//   3. Top levels: one warp per (group of 2^F level-L buckets, 256-column chunk)
+//      (k_cs_nested).  The warp streams the group's rows through a cp.async ring in
+//      shared memory (several rows in flight per warp), forms the level-L bucket sums in
+//      FP32 (FP64 on the FP64 path) and folds them pairwise in registers down to level
+//      L - F, writing each level's rows; the level L - F sums also go to a scratch
+//      buffer at working precision when smaller sizes remain.
 //      When the level-L buckets are large (N / 2^L >= 64 rows), one CTA per bucket
 //      (k_cs_bucket) instead: its warps sum contiguous slices of the bucket and the
 //      partial rows are added in a fixed order.
@@ -55,6 +56,7 @@ struct CsArgs {
   void *scrY;
   int64_t lds;
   int vec_in, vec_out;
+  int ncw;               // column chunks of kChunkCols per row (1 or 2)
 };
 
 __device__ __forceinline__ uint32_t brev_low(uint32_t x, int L) { return L > 0 ? (__brev(x) >> (32 - L)) : 0u; }
@@ -129,21 +131,161 @@ __device__ __forceinline__ void row_meta(const CsArgs &a, int64_t k, int &member
   member = a.nested ? (int)(brev_low(w.x, a.L) & ((1u << a.F) - 1u)) : 0;
 }
 
-// One warp per group of 2^F level-L buckets; 8 warps per CTA.
-template <class Tin, class Tacc, class Tout, int VEC, int F>
-__global__ void __launch_bounds__(256) k_cs_nested(const CsArgs a) {
-  constexpr int MAXQ = 512 / (32 * VEC);
-  constexpr int NS = F > 0 ? F : 1;
-  const int lane = threadIdx.x & 31;
-  const int64_t g = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (g >= a.ngroups) return;
+// ---------------------------------------------------------------------------------
+// Row streaming.  A warp owns a column chunk of kChunkCols columns (rows of d <= 512
+// are split in two chunks handled by two warps, which read the two halves of the same
+// rows at about the same time).  On the vector path every lane copies its 16-byte pieces
+// of a row into its own slots of a per-warp shared-memory ring with cp.async, kRing - 1
+// rows ahead of the row being summed, so a warp keeps several rows in flight without
+// holding them in registers.  Row indices, signs, members and y values come 32 rows at a
+// time (one per lane) and are broadcast by shuffles.
+constexpr int kRing = 4;
+constexpr int kChunkCols = 256;
+constexpr int kWarps = 8;
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <class Tin> constexpr int vec_of() { return 16 / (int)sizeof(Tin); }
+
+// Calls on_row(member, sign, y, v) for the rows rows[lo..hi) in order; v holds this lane's
+// columns c0 + (lane + 32 q) VEC + e of the row (zero past d).
+template <class Tin, class Tacc, class OnRow>
+__device__ __forceinline__ void stream_rows(const CsArgs &a, int64_t lo, int64_t hi, int c0, int lane, uint4 *ring,
+                                            OnRow &&on_row) {
+  constexpr int VEC = vec_of<Tin>();
+  constexpr int MAXQ = kChunkCols / (32 * VEC);
+  const unsigned FULL = 0xffffffffu;
   const int d = a.d;
-  const bool vin = a.vec_in != 0, vout = a.vec_out != 0;
   const Tin *X = static_cast<const Tin *>(a.X);
   const Tin *Y = static_cast<const Tin *>(a.Y);
-  const int64_t lo = a.starts[g], hi = a.starts[g + 1];
+  int64_t kA = 0, kB = 0;
+  int mA = 0, mB = 0;
+  float sA = 0.f, sB = 0.f;
+  Tacc yA = Tacc(0), yB = Tacc(0);
+  auto meta = [&](int64_t b, int64_t &k, int &mj, float &sg, Tacc &yv) {
+    const int64_t p = b + lane;
+    k = 0; mj = 1 << 30; sg = 0.f; yv = Tacc(0);
+    if (p < hi) {
+      k = a.rows[p];
+      row_meta(a, k, mj, sg);
+      yv = (Tacc)Y[k];
+    }
+  };
+  int64_t base = lo;
+  meta(base, kA, mA, sA, yA);
+  meta(base + 32, kB, mB, sB, yB);
+  auto row_at = [&](int64_t p) -> int64_t {
+    const int off = (int)(p - base);
+    return __shfl_sync(FULL, off < 32 ? kA : kB, off & 31);
+  };
+  const bool vec = a.vec_in != 0;
+  auto issue = [&](int64_t p) {
+    const int64_t k = row_at(p);
+    const int slot = (int)(p % kRing);
+#pragma unroll
+    for (int q = 0; q < MAXQ; ++q) {
+      const int e0 = c0 + (lane + 32 * q) * VEC;
+      if (e0 < d) cp_async16(&ring[(slot * MAXQ + q) * 32 + lane], X + k * a.ldx + e0);
+    }
+    cp_async_commit();
+  };
+  if (vec)
+    for (int i = 0; i < kRing - 1; ++i) {
+      if (lo + i < hi) issue(lo + i);
+      else cp_async_commit();
+    }
+  for (int64_t p = lo; p < hi; ++p) {
+    Tacc v[MAXQ][VEC];
+    if (vec) {
+      if (p + kRing - 1 < hi) issue(p + kRing - 1);
+      else cp_async_commit();
+      cp_async_wait<kRing - 1>();
+      const int slot = (int)(p % kRing);
+#pragma unroll
+      for (int q = 0; q < MAXQ; ++q) {
+        const int e0 = c0 + (lane + 32 * q) * VEC;
+        const uint4 t = ring[(slot * MAXQ + q) * 32 + lane];
+        if constexpr (sizeof(Tin) == 4) {
+          const float f[4] = {__uint_as_float(t.x), __uint_as_float(t.y), __uint_as_float(t.z), __uint_as_float(t.w)};
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) v[q][e] = e0 < d ? (Tacc)f[e] : Tacc(0);
+        } else {
+          const double f[2] = {__hiloint2double((int)t.y, (int)t.x), __hiloint2double((int)t.w, (int)t.z)};
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) v[q][e] = e0 < d ? (Tacc)f[e] : Tacc(0);
+        }
+      }
+    } else {
+      const int64_t k = row_at(p);
+#pragma unroll
+      for (int q = 0; q < MAXQ; ++q) {
+        const int e0 = c0 + (lane + 32 * q) * VEC;
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) v[q][e] = (e0 + e < d) ? (Tacc)X[k * a.ldx + e0 + e] : Tacc(0);
+      }
+    }
+    const int off = (int)(p - base);
+    const int mj = __shfl_sync(FULL, off < 32 ? mA : mB, off & 31);
+    const float sg = __shfl_sync(FULL, off < 32 ? sA : sB, off & 31);
+    const Tacc yv = __shfl_sync(FULL, off < 32 ? yA : yB, off & 31);
+    on_row(mj, (Tacc)sg, yv, v);
+    if (off == 31) {  // slide the metadata window
+      kA = kB; mA = mB; sA = sB; yA = yB;
+      base += 32;
+      meta(base + 32, kB, mB, sB, yB);
+    }
+  }
+  if (vec) cp_async_wait<0>();
+}
 
-  Tacc acc[MAXQ][VEC], cur[MAXQ][VEC], nxt[MAXQ][VEC], stk[NS][MAXQ][VEC];
+template <class Tout, class Tacc, int VEC, int MAXQ>
+__device__ __forceinline__ void store_chunk(Tout *row, int d, int c0, int lane, bool vec, const Tacc (&v)[MAXQ][VEC]) {
+#pragma unroll
+  for (int q = 0; q < MAXQ; ++q) {
+    const int e0 = c0 + (lane + 32 * q) * VEC;
+    if (e0 >= d) continue;
+    if constexpr (sizeof(Tout) == 2 && VEC == 4) {
+      if (vec) {
+        const __nv_bfloat162 lo = __floats2bfloat162_rn((float)v[q][0], (float)v[q][1]);
+        const __nv_bfloat162 hi = __floats2bfloat162_rn((float)v[q][2], (float)v[q][3]);
+        uint2 t;
+        t.x = *reinterpret_cast<const uint32_t *>(&lo);
+        t.y = *reinterpret_cast<const uint32_t *>(&hi);
+        *reinterpret_cast<uint2 *>(row + e0) = t;
+        continue;
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < VEC; ++e)
+      if (e0 + e < d) put(row + e0 + e, v[q][e]);
+  }
+}
+
+// One warp per (group of 2^F level-L buckets, column chunk); 8 warps per CTA.
+template <class Tin, class Tacc, class Tout, int F>
+__global__ void __launch_bounds__(256, 2) k_cs_nested(const CsArgs a) {
+  constexpr int VEC = vec_of<Tin>();
+  constexpr int MAXQ = kChunkCols / (32 * VEC);
+  constexpr int NS = F > 0 ? F : 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  uint4 *ring = reinterpret_cast<uint4 *>(smem_raw) + wib * (kRing * MAXQ * 32);
+  const int64_t unit = (int64_t)blockIdx.x * kWarps + wib;
+  const int64_t g = unit / a.ncw;
+  const int chunk = (int)(unit % a.ncw);
+  if (g >= a.ngroups) return;
+  const int c0 = chunk * kChunkCols;
+  const int d = a.d;
+  const bool vout = a.vec_out != 0, ylane = chunk == 0 && lane == 0;
+
+  Tacc acc[MAXQ][VEC], stk[NS][MAXQ][VEC];
   Tacc accy = Tacc(0), stky[NS];
   zero(acc);
   int member = 0;  // next level-L bucket of the group to be emitted
@@ -154,12 +296,12 @@ __global__ void __launch_bounds__(256) k_cs_nested(const CsArgs a) {
     {
       const int64_t b = brev_low((uint32_t)((g << F) | j), a.L);
       if (a.outX[a.L]) {
-        store_row<Tout, Tacc, VEC, MAXQ>(row_ptr<Tout>(a.outX[a.L], a.ldo, b), d, lane, vout, acc);
-        if (lane == 0) put(static_cast<Tout *>(a.outY[a.L]) + b, accy);
+        store_chunk<Tout, Tacc, VEC, MAXQ>(row_ptr<Tout>(a.outX[a.L], a.ldo, b), d, c0, lane, vout, acc);
+        if (ylane) put(static_cast<Tout *>(a.outY[a.L]) + b, accy);
       }
       if (F == 0 && a.scrX) {
-        store_row<Tacc, Tacc, VEC, MAXQ>(row_ptr<Tacc>(a.scrX, a.lds, b), d, lane, true, acc);
-        if (lane == 0) static_cast<Tacc *>(a.scrY)[b] = accy;
+        store_chunk<Tacc, Tacc, VEC, MAXQ>(row_ptr<Tacc>(a.scrX, a.lds, b), d, c0, lane, true, acc);
+        if (ylane) static_cast<Tacc *>(a.scrY)[b] = accy;
       }
     }
     bool carry = true;
@@ -182,12 +324,12 @@ __global__ void __launch_bounds__(256) k_cs_nested(const CsArgs a) {
         const int l = a.L - lev;
         const int64_t b = brev_low((uint32_t)((g << (F - lev)) | (j >> lev)), l);
         if (a.outX[l]) {
-          store_row<Tout, Tacc, VEC, MAXQ>(row_ptr<Tout>(a.outX[l], a.ldo, b), d, lane, vout, acc);
-          if (lane == 0) put(static_cast<Tout *>(a.outY[l]) + b, accy);
+          store_chunk<Tout, Tacc, VEC, MAXQ>(row_ptr<Tout>(a.outX[l], a.ldo, b), d, c0, lane, vout, acc);
+          if (ylane) put(static_cast<Tout *>(a.outY[l]) + b, accy);
         }
         if (lev == F && a.scrX) {
-          store_row<Tacc, Tacc, VEC, MAXQ>(row_ptr<Tacc>(a.scrX, a.lds, b), d, lane, true, acc);
-          if (lane == 0) static_cast<Tacc *>(a.scrY)[b] = accy;
+          store_chunk<Tacc, Tacc, VEC, MAXQ>(row_ptr<Tacc>(a.scrX, a.lds, b), d, c0, lane, true, acc);
+          if (ylane) static_cast<Tacc *>(a.scrY)[b] = accy;
         }
       }
     }
@@ -195,120 +337,71 @@ __global__ void __launch_bounds__(256) k_cs_nested(const CsArgs a) {
     accy = Tacc(0);
   };
 
-  for (int64_t base = lo; base < hi; base += 32) {
-    const int cnt = (int)(hi - base < 32 ? hi - base : 32);
-    int64_t k = 0;
-    int mj = 0;
-    float sg = 0.f;
-    if (lane < cnt) {
-      k = a.rows[base + lane];
-      row_meta(a, k, mj, sg);
-    }
-    int64_t kt = __shfl_sync(0xffffffffu, k, 0);
-    load_row<Tin, Tacc, VEC, MAXQ>(X + kt * a.ldx, d, lane, vin, cur);
-    Tacc yt = (Tacc)Y[kt];
-    for (int t = 0; t < cnt; ++t) {
-      const int jt = __shfl_sync(0xffffffffu, mj, t);
-      const Tacc st = (Tacc)__shfl_sync(0xffffffffu, sg, t);
-      Tacc yn = Tacc(0);
-      if (t + 1 < cnt) {  // issue the next row's loads before using this one
-        const int64_t kn = __shfl_sync(0xffffffffu, k, t + 1);
-        load_row<Tin, Tacc, VEC, MAXQ>(X + kn * a.ldx, d, lane, vin, nxt);
-        yn = (Tacc)Y[kn];
-      }
-      while (member < jt) emit(member++);
+  stream_rows<Tin, Tacc>(a, a.starts[g], a.starts[g + 1], c0, lane, ring,
+                         [&](int mj, Tacc sg, Tacc yv, const Tacc (&v)[MAXQ][VEC]) {
+                           while (member < mj) emit(member++);
 #pragma unroll
-      for (int q = 0; q < MAXQ; ++q)
+                           for (int q = 0; q < MAXQ; ++q)
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) acc[q][e] += st * cur[q][e];
-      accy += st * yt;
-#pragma unroll
-      for (int q = 0; q < MAXQ; ++q)
-#pragma unroll
-        for (int e = 0; e < VEC; ++e) cur[q][e] = nxt[q][e];
-      yt = yn;
-    }
-  }
+                             for (int e = 0; e < VEC; ++e) acc[q][e] += sg * v[q][e];
+                           accy += sg * yv;
+                         });
   while (member < (1 << F)) emit(member++);
 }
 
-// One CTA per bucket: 16 warps sum contiguous slices of the bucket's rows (index order),
-// then the 16 partial rows are added in warp order.
-template <class Tin, class Tacc, class Tout, int VEC>
-__global__ void __launch_bounds__(512) k_cs_bucket(const CsArgs a) {
-  constexpr int MAXQ = 512 / (32 * VEC);
-  constexpr int W = 16;
+// One CTA per bucket: the 8 warps cover (column chunk, row slice) pairs; each sums its
+// slice of the bucket's rows in index order, and the slices' partial rows are added in
+// slice order.
+template <class Tin, class Tacc, class Tout>
+__global__ void __launch_bounds__(256) k_cs_bucket(const CsArgs a) {
+  constexpr int VEC = vec_of<Tin>();
+  constexpr int MAXQ = kChunkCols / (32 * VEC);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Tacc *part = reinterpret_cast<Tacc *>(smem_raw);   // [W][513]
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint4 *ring = reinterpret_cast<uint4 *>(smem_raw) + w * (kRing * MAXQ * 32);
+  Tacc *part = reinterpret_cast<Tacc *>(reinterpret_cast<uint4 *>(smem_raw) + kWarps * kRing * MAXQ * 32);  // [slices][513]
+  const int ncw = a.ncw, nsl = kWarps / a.ncw;
+  const int chunk = w % ncw, slice = w / ncw;
+  const int c0 = chunk * kChunkCols;
   const int64_t g = blockIdx.x;
   const int d = a.d;
-  const bool vin = a.vec_in != 0;
-  const Tin *X = static_cast<const Tin *>(a.X);
-  const Tin *Y = static_cast<const Tin *>(a.Y);
   const int64_t lo = a.starts[g], hi = a.starts[g + 1];
-  const int64_t chunk = (hi - lo + W - 1) / W;
-  const int64_t s0 = lo + w * chunk, s1 = s0 + chunk < hi ? s0 + chunk : hi;
+  const int64_t len = (hi - lo + nsl - 1) / nsl;
+  const int64_t s0 = lo + slice * len < hi ? lo + slice * len : hi;
+  const int64_t s1 = s0 + len < hi ? s0 + len : hi;
 
-  Tacc acc[MAXQ][VEC], cur[MAXQ][VEC], nxt[MAXQ][VEC];
+  Tacc acc[MAXQ][VEC];
   Tacc accy = Tacc(0);
   zero(acc);
-  for (int64_t base = s0; base < s1; base += 32) {
-    const int cnt = (int)(s1 - base < 32 ? s1 - base : 32);
-    int64_t k = 0;
-    int mj = 0;
-    float sg = 0.f;
-    if (lane < cnt) {
-      k = a.rows[base + lane];
-      row_meta(a, k, mj, sg);
-    }
-    int64_t kt = __shfl_sync(0xffffffffu, k, 0);
-    load_row<Tin, Tacc, VEC, MAXQ>(X + kt * a.ldx, d, lane, vin, cur);
-    Tacc yt = (Tacc)Y[kt];
-    for (int t = 0; t < cnt; ++t) {
-      const Tacc st = (Tacc)__shfl_sync(0xffffffffu, sg, t);
-      Tacc yn = Tacc(0);
-      if (t + 1 < cnt) {
-        const int64_t kn = __shfl_sync(0xffffffffu, k, t + 1);
-        load_row<Tin, Tacc, VEC, MAXQ>(X + kn * a.ldx, d, lane, vin, nxt);
-        yn = (Tacc)Y[kn];
-      }
+  stream_rows<Tin, Tacc>(a, s0, s1, c0, lane, ring, [&](int, Tacc sg, Tacc yv, const Tacc (&v)[MAXQ][VEC]) {
 #pragma unroll
-      for (int q = 0; q < MAXQ; ++q)
+    for (int q = 0; q < MAXQ; ++q)
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) acc[q][e] += st * cur[q][e];
-      accy += st * yt;
-#pragma unroll
-      for (int q = 0; q < MAXQ; ++q)
-#pragma unroll
-        for (int e = 0; e < VEC; ++e) cur[q][e] = nxt[q][e];
-      yt = yn;
-    }
-  }
-  // partial row of this warp (column e0 + e at part[w][...], the y value at part[w][512])
+      for (int e = 0; e < VEC; ++e) acc[q][e] += sg * v[q][e];
+    accy += sg * yv;
+  });
 #pragma unroll
   for (int q = 0; q < MAXQ; ++q)
 #pragma unroll
     for (int e = 0; e < VEC; ++e) {
-      const int c = (lane + 32 * q) * VEC + e;
-      if (c < d) part[w * 513 + c] = acc[q][e];
+      const int c = c0 + (lane + 32 * q) * VEC + e;
+      if (c < d) part[slice * 513 + c] = acc[q][e];
     }
-  if (lane == 0) part[w * 513 + 512] = accy;
+  if (chunk == 0 && lane == 0) part[slice * 513 + 512] = accy;
   __syncthreads();
-  // row index of this bucket in natural order
   const int64_t b = a.nested ? (int64_t)brev_low((uint32_t)g, a.L) : g;
   for (int c = threadIdx.x; c <= 512; c += blockDim.x) {
     if (c < d || c == 512) {
-      Tacc s = Tacc(0);
-      for (int u = 0; u < W; ++u) s += part[u * 513 + c];
+      Tacc sum = Tacc(0);
+      for (int u = 0; u < nsl; ++u) sum += part[u * 513 + c];
       if (c < d) {
         void *o = a.nested ? a.outX[a.L] : a.outX[0];
-        if (o) put(row_ptr<Tout>(o, a.ldo, b) + c, s);
-        if (a.scrX) row_ptr<Tacc>(a.scrX, a.lds, b)[c] = s;
+        if (o) put(row_ptr<Tout>(o, a.ldo, b) + c, sum);
+        if (a.scrX) row_ptr<Tacc>(a.scrX, a.lds, b)[c] = sum;
       } else {
         void *o = a.nested ? a.outY[a.L] : a.outY[0];
-        if (o) put(static_cast<Tout *>(o) + b, s);
-        if (a.scrY) static_cast<Tacc *>(a.scrY)[b] = s;
+        if (o) put(static_cast<Tout *>(o) + b, sum);
+        if (a.scrY) static_cast<Tacc *>(a.scrY)[b] = sum;
       }
     }
   }
@@ -373,8 +466,8 @@ CsPlan cs_plan(int64_t N, int d, int prec, int64_t m_min, int64_t m_max, int64_t
   p.l1 = m_min > 0 ? sortk::bits_for(m_min) : -1;
   p.big = p.L >= 0 && N >= (int64_t(64) << p.L);
   p.F = 0;
-  if (p.L >= 0 && !p.big) {  // FP64 accumulators leave registers for one folded level
-    const int fmax = prec == SLSE_PREC_FP64 ? 1 : 3;
+  if (p.L >= 0 && !p.big) {  // levels folded in registers: 4 (FP32 sums), 1 (FP64 sums)
+    const int fmax = prec == SLSE_PREC_FP64 ? 1 : 4;
     p.F = p.L - p.l1 < fmax ? p.L - p.l1 : fmax;
     if (p.F < 0) p.F = 0;
   }
@@ -407,6 +500,28 @@ CsPlan cs_plan(int64_t N, int d, int prec, int64_t m_min, int64_t m_max, int64_t
 }
 
 namespace {
+
+template <class Tin, class Tacc, class Tout, int F>
+cudaError_t launch_nested(const CsArgs &a, int64_t nunits, cudaStream_t s) {
+  constexpr int MAXQ = kChunkCols / (32 * vec_of<Tin>());
+  const size_t smem = (size_t)kWarps * kRing * MAXQ * 32 * sizeof(uint4);
+  auto kern = k_cs_nested<Tin, Tacc, Tout, F>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)((nunits + kWarps - 1) / kWarps), 32 * kWarps, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class Tin, class Tacc, class Tout>
+cudaError_t launch_bucket(const CsArgs &a, int64_t nbuckets, cudaStream_t s) {
+  constexpr int MAXQ = kChunkCols / (32 * vec_of<Tin>());
+  const size_t smem = (size_t)kWarps * kRing * MAXQ * 32 * sizeof(uint4) + (size_t)kWarps * 513 * sizeof(Tacc);
+  auto kern = k_cs_bucket<Tin, Tacc, Tout>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)nbuckets, 32 * kWarps, smem, s>>>(a);
+  return cudaGetLastError();
+}
 
 template <class Tin, class Tacc, class Tout, int VEC>
 cudaError_t run_cs(const CsPlan &pl, const void *X, int64_t ldx, const void *Y, uint64_t seed,
@@ -444,6 +559,7 @@ cudaError_t run_cs(const CsPlan &pl, const void *X, int64_t ldx, const void *Y, 
     return reinterpret_cast<uintptr_t>(p) % (v * eb) == 0 && ld % v == 0;
   };
   a.vec_in = (d % VEC == 0 && vec_ok(X, ldx, sizeof(Tin), VEC)) ? 1 : 0;
+  a.ncw = (d + kChunkCols - 1) / kChunkCols;
 
   if (nested) {
     // 2. group starts, 3. top levels
@@ -463,25 +579,23 @@ cudaError_t run_cs(const CsPlan &pl, const void *X, int64_t ldx, const void *Y, 
     a.scrX = folds ? base + pl.o_scr0 : nullptr;
     a.scrY = folds ? static_cast<void *>(static_cast<Tacc *>(a.scrX) + (int64_t(1) << (pl.L - pl.F)) * pl.lds) : nullptr;
     if (pl.big) {
-      const size_t smem = 16 * 513 * sizeof(Tacc);
-      auto kern = k_cs_bucket<Tin, Tacc, Tout, VEC>;
-      if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-      kern<<<(unsigned)ng, 512, smem, s>>>(a);
+      e = launch_bucket<Tin, Tacc, Tout>(a, ng, s);
     } else {
-      const unsigned grid = (unsigned)((ng + 7) / 8);
+      const int64_t nunits = ng * a.ncw;
       if constexpr (sizeof(Tacc) == 8) {
-        if (pl.F == 0) k_cs_nested<Tin, Tacc, Tout, VEC, 0><<<grid, 256, 0, s>>>(a);
-        else k_cs_nested<Tin, Tacc, Tout, VEC, 1><<<grid, 256, 0, s>>>(a);
+        if (pl.F == 0) e = launch_nested<Tin, Tacc, Tout, 0>(a, nunits, s);
+        else e = launch_nested<Tin, Tacc, Tout, 1>(a, nunits, s);
       } else {
         switch (pl.F) {
-          case 0: k_cs_nested<Tin, Tacc, Tout, VEC, 0><<<grid, 256, 0, s>>>(a); break;
-          case 1: k_cs_nested<Tin, Tacc, Tout, VEC, 1><<<grid, 256, 0, s>>>(a); break;
-          case 2: k_cs_nested<Tin, Tacc, Tout, VEC, 2><<<grid, 256, 0, s>>>(a); break;
-          default: k_cs_nested<Tin, Tacc, Tout, VEC, 3><<<grid, 256, 0, s>>>(a); break;
+          case 0: e = launch_nested<Tin, Tacc, Tout, 0>(a, nunits, s); break;
+          case 1: e = launch_nested<Tin, Tacc, Tout, 1>(a, nunits, s); break;
+          case 2: e = launch_nested<Tin, Tacc, Tout, 2>(a, nunits, s); break;
+          case 3: e = launch_nested<Tin, Tacc, Tout, 3>(a, nunits, s); break;
+          default: e = launch_nested<Tin, Tacc, Tout, 4>(a, nunits, s); break;
         }
       }
     }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (e != cudaSuccess) return e;
     // 4. lower levels by folding the scratch
     if (folds) {
       Tacc *cx = static_cast<Tacc *>(a.scrX), *cy = static_cast<Tacc *>(a.scrY);
@@ -511,11 +625,7 @@ cudaError_t run_cs(const CsPlan &pl, const void *X, int64_t ldx, const void *Y, 
     h.outX[0] = hatX; h.outY[0] = hatY; h.ldo = ldh;
     h.scrX = nullptr; h.scrY = nullptr;
     h.vec_out = 0;
-    const size_t smem = 16 * 513 * sizeof(Tacc);
-    auto kern = k_cs_bucket<Tin, Tacc, Tout, VEC>;
-    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-    kern<<<(unsigned)pl.r, 512, smem, s>>>(h);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_bucket<Tin, Tacc, Tout>(h, pl.r, s)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
