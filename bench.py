@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--log2n", type=int, default=22)
     ap.add_argument("--d", type=int, default=512)
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--cs-steps", type=int, default=2, help="CountSketch-variant fits reported beside the SRHT line")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--sample-log2n", type=int, default=15)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline timing (accuracy reference still runs)")
@@ -354,6 +355,32 @@ def run_ours(args, rank, ws, local_rank):
                     "iters": [r64["iters_stage1"], r64["iters_stage2"]]}
         torch.cuda.empty_cache()
 
+    # CountSketch variant (SLSE-FRS-CS, Sec. 5) on the same workload and schedule sizes
+    cs = None
+    if args.cs_steps > 0:
+        scs = slse.default_schedule(N, d, prec="mixed_bf16", T=100, tol=5e-9, kind="countsketch")
+        wcs = slse.alloc_workspace(slse.workspace_size(Xd, Yd, slse.OP_FIT, scs))
+        slse.fit(Xd, Yd, scs, seed=998, workspace=wcs, trace_cap=cap)
+        tcs, fin = [], []
+        for k in range(args.cs_steps):
+            r = slse.fit(Xd, Yd, scs, seed=k, workspace=wcs, trace_cap=cap)
+            if rank == 0:
+                a8, _ = first_crossing(r.beta_hist.cpu().numpy(), np.array(r.ms_hist), bh, TARGET)
+                tcs.append(a8)
+                fin.append(float(np.linalg.norm(r.beta - bh) / np.linalg.norm(bh)))
+        del wcs
+        if rank == 0:
+            rc = r.report
+            # the sketch reads X twice (nested sizes and S-hat) and writes every sketch once
+            by = 2.0 * N * (d + 1) * 4.0 + (sum(scs.m) + scs.r) * (d + 1) * 2.0
+            cs = {"time_to_1e-8_ms": statistics.mean(tcs) if all(v is not None for v in tcs) else None,
+                  "final_rel_err": max(fin),
+                  "phases_ms": {k: rc[k] for k in ("ms_sketch", "ms_qr", "ms_stage1", "ms_stage2", "ms_total")},
+                  "iters": [rc["iters_stage1"], rc["iters_stage2"]],
+                  "sketch_alg_bytes": by, "sketch_gbs": by / rc["ms_sketch"] / 1e6,
+                  "sketch_frac_of_" + peak_kind: by / rc["ms_sketch"] / 1e6 / peak}
+        torch.cuda.empty_cache()
+
     # end to end through the public API with pinned host inputs (copy inside the call)
     e2e = None
     if args.e2e_steps > 0:
@@ -392,6 +419,7 @@ def run_ours(args, rank, ws, local_rank):
         "accuracy": {"target": TARGET, "crossed_every_step": crossed, "final_rel_err_max": max(errs_final),
                      "reference": "oracle OLS, FP64 normal equations", "reference_seconds": t_ref},
         "fp64": fp64,
+        "countsketch": cs,
         "phases_ms": {k: rep[k] for k in ("ms_draws", "ms_sketch", "ms_srht_pass1", "ms_srht_pass2", "ms_qr",
                                           "ms_stage1", "ms_stage2", "ms_total")},
         "iters": [rep["iters_stage1"], rep["iters_stage2"]], "rebases": rep["rebases"],
