@@ -125,6 +125,8 @@ typedef struct {
   float *ms_hist;     /* host, cap: CUDA-event ms from the call's start to the end of iteration t+1 */
   int32_t cap;
   int32_t count;      /* out: iterations recorded */
+  double *hinv_out;   /* device d x d (ld d), nullable: receives the H-hat^{-1} = R^{-1} R^{-T} the fit
+                         used, the preconditioner slse_solve_normal takes */
 } slse_trace;
 
 /* Workspace query.  op: SLSE_OP_FIT (sched required), SLSE_OP_SKETCH (arg = m; prec and kind
@@ -206,6 +208,34 @@ int32_t slse_default_schedule(int64_t N, int32_t d, slse_schedule *out, int64_t 
  * powers of two).  Returns -1 for other kinds. */
 int32_t slse_default_schedule_for(int64_t N, int32_t d, int32_t kind, slse_schedule *out, int64_t *m_buf,
                                   int32_t *a_buf, int32_t cap);
+
+/* Differentiation through the estimate.  SLSE-FRS converges to the least-squares
+ * estimate beta-hat = (X^T X)^{-1} X^T Y (its 2nd-stage fixed point solves the normal
+ * equations, Sec. 3), so for a loss with v = dL/d(beta-hat) the input gradients are
+ * dL/dY = X w and dL/dX = r w^T - (X w) beta-hat^T with w = (X^T X)^{-1} v and
+ * r = Y - X beta-hat.  No paper counterpart; an extension for callers that train through
+ * the estimator.
+ *
+ * slse_solve_normal: w = (X^T X)^{-1} v by the 2nd-stage M-IHS iteration (Eqs. (7), (8))
+ * with the gradient v - X^T X w and the preconditioner Hinv (device d x d, e.g. from
+ * slse_fit's trace->hinv_out): w_0 = 0, w+ = w + mu Hinv (v - X^T X w) + eta (w - w_prev).
+ * sched supplies mu, eta, T (iteration cap), tol (the fit's relative-step test with
+ * rho = sqrt(d/r)), r and prec (FP64, or MIXED_BF16 for F32 X: compensated FP32 passes);
+ * its sizes m, a and kind are ignored.  X device; Y unused.  v, w_out: device d doubles.
+ * report (nullable): ms_total, iters_stage2, final_rel_step, status.  Returns after w_out
+ * is written (SLSE_ENOTCONV if tol > 0 was not met within T, w_out holds the last iterate).
+ * Workspace: slse_solve_normal_workspace bytes, or NULL for a stream-ordered allocation. */
+slse_status slse_solve_normal(const slse_problem *prob, const double *Hinv, const double *v, double *w_out,
+                              const slse_schedule *sched, slse_report *report, void *workspace, size_t ws_bytes,
+                              slse_stream_t stream);
+size_t slse_solve_normal_workspace(const slse_problem *prob, int32_t prec);
+
+/* The input gradients from w (above) in one pass over [X | Y]: dY[i] = x_i . w and
+ * dX[i, :] = (y_i - x_i . beta) w - (x_i . w) beta.  dX (ld lddx >= d) and dY have the
+ * dtype of X (F32 inputs: compensated FP32 dot products).  All pointers device.
+ * Asynchronous on `stream`. */
+slse_status slse_ols_vjp(const slse_problem *prob, const double *beta, const double *w, void *dX, int64_t lddx,
+                         void *dY, slse_stream_t stream);
 
 /* Theorem 4.3 lower bound on the inner iterations: log_3[((1+omega) r + 1)/omega] with
  * r = sqrt((m_i - d)/(m_prev - d)).  Host-only.  Returns NaN for m_prev <= d or omega <= 0. */

@@ -57,7 +57,7 @@ class CReport(ctypes.Structure):
 
 class CTrace(ctypes.Structure):
     _fields_ = [("beta_hist", ctypes.c_void_p), ("ms_hist", ctypes.POINTER(ctypes.c_float)),
-                ("cap", ctypes.c_int32), ("count", ctypes.c_int32)]
+                ("cap", ctypes.c_int32), ("count", ctypes.c_int32), ("hinv_out", ctypes.c_void_p)]
 
 
 _vp, _sz, _i32, _i64, _u64 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
@@ -82,6 +82,13 @@ _lib.slse_default_schedule.argtypes = [_i64, _i32, ctypes.POINTER(CSchedule), ct
 _lib.slse_default_schedule_for.restype = _i32
 _lib.slse_default_schedule_for.argtypes = [_i64, _i32, _i32, ctypes.POINTER(CSchedule), ctypes.POINTER(ctypes.c_int64),
                                            ctypes.POINTER(ctypes.c_int32), _i32]
+_lib.slse_solve_normal.restype = _i32
+_lib.slse_solve_normal.argtypes = [ctypes.POINTER(CProblem), _vp, _vp, _vp, ctypes.POINTER(CSchedule),
+                                   ctypes.POINTER(CReport), _vp, _sz, _vp]
+_lib.slse_solve_normal_workspace.restype = _sz
+_lib.slse_solve_normal_workspace.argtypes = [ctypes.POINTER(CProblem), _i32]
+_lib.slse_ols_vjp.restype = _i32
+_lib.slse_ols_vjp.argtypes = [ctypes.POINTER(CProblem), _vp, _vp, _vp, _i64, _vp, _vp]
 _lib.slse_ai_bound.restype = ctypes.c_double
 _lib.slse_ai_bound.argtypes = [ctypes.c_double, _i64, _i64, _i32]
 _lib.slse_status_string.restype = ctypes.c_char_p
@@ -90,7 +97,7 @@ _lib.slse_version.restype = _i32
 
 EXPORTED = ["slse_workspace_size", "slse_fit", "slse_sketch", "slse_grad", "slse_grad_noalloc", "slse_draws", "slse_qr",
             "slse_default_schedule", "slse_default_schedule_for", "slse_ai_bound", "slse_status_string",
-            "slse_version"]
+            "slse_version", "slse_solve_normal", "slse_solve_normal_workspace", "slse_ols_vjp"]
 
 
 class SlseError(RuntimeError):
@@ -205,10 +212,11 @@ class FitResult:
     report: dict
     beta_hist: object = None   # torch (count x d) on the device, when traced
     ms_hist: list = None
+    hinv: object = None        # torch (d x d) float64 on the device: the fit's H-hat^{-1}, when asked
 
 
 def fit(X, Y, schedule: Schedule | None = None, seed: int = 0, workspace=None, trace_cap: int = 0,
-        stream=None, raise_on_error: bool = True) -> FitResult:
+        stream=None, raise_on_error: bool = True, hinv: bool = False) -> FitResult:
     """slse_fit: Algorithm 2 on device tensors X, Y.  Returns beta-hat on the host."""
     torch = _torch()
     p = problem(X, Y)
@@ -218,10 +226,17 @@ def fit(X, Y, schedule: Schedule | None = None, seed: int = 0, workspace=None, t
     tr = None
     hist = None
     ms = None
-    if trace_cap > 0:
-        hist = torch.zeros((trace_cap, p.d), dtype=torch.float64, device=X.device if X.is_cuda else "cuda")
-        ms = (ctypes.c_float * trace_cap)()
-        tr = CTrace(hist.data_ptr(), ctypes.cast(ms, ctypes.POINTER(ctypes.c_float)), trace_cap, 0)
+    hv = None
+    dev = X.device if X.is_cuda else "cuda"
+    if trace_cap > 0 or hinv:
+        if hinv:
+            hv = torch.empty((p.d, p.d), dtype=torch.float64, device=dev)
+        if trace_cap > 0:
+            hist = torch.zeros((trace_cap, p.d), dtype=torch.float64, device=dev)
+            ms = (ctypes.c_float * trace_cap)()
+        tr = CTrace(hist.data_ptr() if hist is not None else None,
+                    ctypes.cast(ms, ctypes.POINTER(ctypes.c_float)) if ms is not None else None, trace_cap, 0,
+                    hv.data_ptr() if hv is not None else None)
     ws_ptr, ws_len = (workspace.data_ptr(), workspace.numel() * workspace.element_size()) if workspace is not None \
         else (None, 0)
     st = _lib.slse_fit(ctypes.byref(p), ctypes.byref(cs) if cs is not None else None, seed, beta, ctypes.byref(rep),
@@ -230,10 +245,46 @@ def fit(X, Y, schedule: Schedule | None = None, seed: int = 0, workspace=None, t
         _check(st, "slse_fit", allow=(ENOTCONV,))
     report = {f: getattr(rep, f) for f, _ in CReport._fields_}
     out = FitResult(beta=np.frombuffer(beta, dtype=np.float64).copy(), status=st, report=report)
-    if tr is not None:
+    if tr is not None and trace_cap > 0:
         out.beta_hist = hist[:tr.count]
         out.ms_hist = list(ms[:tr.count])
+    out.hinv = hv
     return out
+
+
+def solve_normal(X, Hinv, v, schedule: Schedule, workspace=None, stream=None, raise_on_error: bool = True):
+    """slse_solve_normal: w = (X^T X)^{-1} v by preconditioned M-IHS steps (device float64).
+    Returns (w, report)."""
+    torch = _torch()
+    p = CProblem(X.shape[0], X.shape[1], _dtype_code(X), X.data_ptr(), X.stride(0), X.data_ptr())
+    if X.dim() != 2 or X.stride(1) != 1:
+        raise ValueError("X must be a row-major 2-D tensor")
+    v = v.to(torch.float64).contiguous()
+    H = Hinv.to(torch.float64).contiguous()
+    w = torch.empty(p.d, dtype=torch.float64, device=X.device)
+    cs = schedule.to_c()
+    rep = CReport()
+    ws_ptr, ws_len = (workspace.data_ptr(), workspace.numel() * workspace.element_size()) if workspace is not None \
+        else (None, 0)
+    st = _lib.slse_solve_normal(ctypes.byref(p), H.data_ptr(), v.data_ptr(), w.data_ptr(), ctypes.byref(cs),
+                                ctypes.byref(rep), ws_ptr, ws_len, _stream(stream))
+    if raise_on_error:
+        _check(st, "slse_solve_normal", allow=(ENOTCONV,))
+    return w, {f: getattr(rep, f) for f, _ in CReport._fields_}
+
+
+def ols_vjp(X, Y, beta, w, stream=None):
+    """slse_ols_vjp: (dL/dX, dL/dY) = (r w^T - (X w) beta^T, X w), r = Y - X beta, in X's dtype."""
+    torch = _torch()
+    p = problem(X, Y)
+    beta = torch.as_tensor(beta, dtype=torch.float64, device=X.device).contiguous()
+    w = w.to(torch.float64).contiguous()
+    dX = torch.empty_like(X, memory_format=torch.contiguous_format)
+    dY = torch.empty_like(Y)
+    st = _lib.slse_ols_vjp(ctypes.byref(p), beta.data_ptr(), w.data_ptr(), dX.data_ptr(), dX.stride(0), dY.data_ptr(),
+                           _stream(stream))
+    _check(st, "slse_ols_vjp")
+    return dX, dY
 
 
 def sketch(X, Y, m: int, seed: int = 0, prec: str = "fp64", workspace=None, stream=None, kind: str = "srht"):

@@ -455,6 +455,8 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     kernels += 4;
   }
   CK(cudaEventRecord(e_qr, st));
+  if (tr && tr->hinv_out)
+    CK(cudaMemcpyAsync(tr->hinv_out, Hinv, (size_t)d * d * 8, cudaMemcpyDeviceToDevice, st));
   CK(cudaMemsetAsync(ring, 0, (size_t)3 * d * 8, st));
 
   UpdateArgs ua{};
