@@ -13,6 +13,7 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Prints one JSON line (rank 0).  Multi-GPU runs are independent replicas.
 """
 import argparse
+import dataclasses
 import hashlib
 import json
 import math
@@ -45,6 +46,8 @@ def parse():
     ap.add_argument("--d", type=int, default=512)
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cs-steps", type=int, default=2, help="CountSketch-variant fits reported beside the SRHT line")
+    ap.add_argument("--fp8-steps", type=int, default=2, help="fits with the FP8 form of the sketch")
+    ap.add_argument("--diff-steps", type=int, default=2, help="forward+backward passes of the differentiation block")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--sample-log2n", type=int, default=15)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline timing (accuracy reference still runs)")
@@ -211,6 +214,34 @@ def cpu_leg(X, Y, log2n, d, sample_log2n, time_it):
     return bh, t_ref, base
 
 
+def sketch_form_errors(slse, torch, seed=4):
+    """Reference leg (oracle): error of one SRHT sketch in each stored form -- FP64, BF16 and
+    FP8 (E4M3 with 32-column block scales) -- against the oracle's FP64 sketch, on a
+    2^16 x 64 sample of the workload (m = 4096): max and mean of |error| / column rms."""
+    import workloads
+    from oracle import fp8 as ofp8, sketch as osk
+    n, d, m = 1 << 16, 64, 4096
+    p = workloads.cfg3(N=n, d=d, seed=1003)
+    X, Y = p["X"], p["Y"]
+    ref = osk.sketch(X.astype(np.float64), Y.astype(np.float64), m, seed)[0]
+    rms = np.sqrt((ref ** 2).mean(0))
+    Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+    out = {}
+    for form in ("fp64", "mixed_bf16", "mixed_fp8"):
+        if form == "fp64":
+            g = slse.sketch(Xd.double(), Yd.double(), m, seed=seed, prec="fp64")[0].cpu().numpy()
+        elif form == "mixed_bf16":
+            g = slse.sketch(Xd, Yd, m, seed=seed, prec=form)[0].float().cpu().numpy().astype(np.float64)
+        else:
+            codes, k, _ = slse.sketch(Xd, Yd, m, seed=seed, prec=form)
+            q = ofp8.decode_e4m3(codes.cpu().numpy().astype(np.int64))
+            g = q * np.repeat(np.ldexp(1.0, k.cpu().numpy().astype(np.int64) - 127), 32, axis=1)[:, :d]
+        e = np.abs(g - ref) / rms
+        out[form] = {"max": float(e.max()), "mean": float(e.mean())}
+    return {"sample": f"cfg3 rows, N=2^16, d={d}, m={m}, error / column rms vs the oracle's FP64 sketch",
+            "by_form": out}
+
+
 def run_reference(args, rank, ws):
     if rank != 0:
         return
@@ -355,6 +386,29 @@ def run_ours(args, rank, ws, local_rank):
                     "iters": [r64["iters_stage1"], r64["iters_stage2"]]}
         torch.cuda.empty_cache()
 
+    # FP8 form of the sketch on the same workload (1st-stage sketches in E4M3 + block scales)
+    f8 = None
+    if args.fp8_steps > 0:
+        s8 = slse.default_schedule(N, d, prec="mixed_fp8", T=100, tol=5e-9)
+        w8 = slse.alloc_workspace(slse.workspace_size(Xd, Yd, slse.OP_FIT, s8))
+        slse.fit(Xd, Yd, s8, seed=997, workspace=w8, trace_cap=cap)
+        t8s, fin = [], []
+        for k in range(args.fp8_steps):
+            r = slse.fit(Xd, Yd, s8, seed=k, workspace=w8, trace_cap=cap)
+            if rank == 0:
+                a8, _ = first_crossing(r.beta_hist.cpu().numpy(), np.array(r.ms_hist), bh, TARGET)
+                t8s.append(a8)
+                fin.append(float(np.linalg.norm(r.beta - bh) / np.linalg.norm(bh)))
+        del w8
+        if rank == 0:
+            r8 = r.report
+            f8 = {"time_to_1e-8_ms": statistics.mean(t8s) if all(v is not None for v in t8s) else None,
+                  "final_rel_err": max(fin),
+                  "phases_ms": {k: r8[k] for k in ("ms_sketch", "ms_qr", "ms_stage1", "ms_stage2", "ms_total")},
+                  "iters": [r8["iters_stage1"], r8["iters_stage2"]],
+                  "sketch_error_by_form": sketch_form_errors(slse, torch)}
+        torch.cuda.empty_cache()
+
     # CountSketch variant (SLSE-FRS-CS, Sec. 5) on the same workload and schedule sizes
     cs = None
     if args.cs_steps > 0:
@@ -379,6 +433,42 @@ def run_ours(args, rank, ws, local_rank):
                   "iters": [rc["iters_stage1"], rc["iters_stage2"]],
                   "sketch_alg_bytes": by, "sketch_gbs": by / rc["ms_sketch"] / 1e6,
                   "sketch_frac_of_" + peak_kind: by / rc["ms_sketch"] / 1e6 / peak}
+        torch.cuda.empty_cache()
+
+    # differentiation through the estimate at the N = 2^21, d = 128 FP32 workload (forward
+    # fit, backward normal-equation solve and the one-pass input gradients)
+    diff = None
+    if args.diff_steps > 0:
+        import workloads
+        n5, d5 = 1 << 21, 128
+        p5 = workloads.cfg5(N=n5, d=d5, seed=1005)
+        X5, Y5 = torch.from_numpy(p5["X"]).cuda(), torch.from_numpy(p5["Y"]).cuda()
+        s5 = slse.default_schedule(n5, d5, prec="mixed_bf16", T=100, tol=1e-10)
+        sa = dataclasses.replace(s5, tol=1e-9)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        fw, sv, vj, its = [], [], [], []
+        for k in range(args.diff_steps + 1):
+            ev[0].record()
+            r5 = slse.fit(X5, Y5, s5, seed=k, hinv=True)
+            ev[1].record()
+            v5 = torch.from_numpy(r5.beta - p5["beta_true"]).cuda()
+            w5, rep5 = slse.solve_normal(X5, r5.hinv, v5, sa)
+            ev[2].record()
+            dX5, dY5 = slse.ols_vjp(X5, Y5, r5.beta, w5)
+            ev[3].record()
+            torch.cuda.synchronize()
+            if k > 0:
+                fw.append(ev[0].elapsed_time(ev[1]))
+                sv.append(ev[1].elapsed_time(ev[2]))
+                vj.append(ev[2].elapsed_time(ev[3]))
+                its.append(rep5["iters_stage2"])
+        vjp_bytes = 2.0 * n5 * d5 * 4 + 2.0 * n5 * 4
+        diff = {"workload": f"N=2^21, d={d5}, X fp32, L = 1/2 ||beta-hat - beta*||^2",
+                "forward_fit_ms": statistics.mean(fw), "backward_solve_ms": statistics.mean(sv),
+                "backward_solve_iters": statistics.mean(its), "vjp_ms": statistics.mean(vj),
+                "vjp_gbs": vjp_bytes / statistics.mean(vj) / 1e6,
+                "vjp_frac_of_" + peak_kind: vjp_bytes / statistics.mean(vj) / 1e6 / peak}
+        del X5, Y5, dX5, dY5
         torch.cuda.empty_cache()
 
     # end to end through the public API with pinned host inputs (copy inside the call)
@@ -420,6 +510,8 @@ def run_ours(args, rank, ws, local_rank):
                      "reference": "oracle OLS, FP64 normal equations", "reference_seconds": t_ref},
         "fp64": fp64,
         "countsketch": cs,
+        "fp8": f8,
+        "differentiation": diff,
         "phases_ms": {k: rep[k] for k in ("ms_draws", "ms_sketch", "ms_srht_pass1", "ms_srht_pass2", "ms_qr",
                                           "ms_stage1", "ms_stage2", "ms_total")},
         "iters": [rep["iters_stage1"], rep["iters_stage2"]], "rebases": rep["rebases"],

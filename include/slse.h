@@ -77,6 +77,11 @@ typedef enum { SLSE_SRHT = 0, SLSE_COUNTSKETCH = 1, SLSE_GAUSSIAN = 2, SLSE_COUN
  *   the BF16 sketch with FP32 accumulation; 2nd-stage residual-gradient in FP32 with
  *   error-free (TwoProd/TwoSum) residuals against an FP64 base point and two-sum
  *   compensated accumulation; QR, preconditioner and update in FP64.  Requires X F32. */
+/* SLSE_PREC_MIXED_FP8: as MIXED_BF16, but the sampled sketch rows U are stored as E4M3 values
+ *   with one power-of-two scale 2^k per 32-column block of a row (k + 127 in a byte; k is
+ *   the smallest integer with max|block| <= 448 2^k), so the 1st-stage subproblems read one
+ *   byte per element; the pass-1 intermediate and the sketch of Y stay BF16.  No paper
+ *   counterpart (the paper's sketches are double precision).  Requires X F32, kind SRHT. */
 typedef enum { SLSE_PREC_FP64 = 0, SLSE_PREC_MIXED_BF16 = 1, SLSE_PREC_MIXED_FP8 = 2 } slse_precision;
 
 typedef struct {
@@ -151,7 +156,9 @@ slse_status slse_fit(const slse_problem *prob, const slse_schedule *sched, uint6
  * SLSE_COUNTSKETCH_HAT: the same with the Hessian-sketch hash into m buckets.  prec FP64 ->
  * SX, SY are double; MIXED_BF16 -> bf16 (CountSketch sums accumulated in FP32, in row
  * order within a bucket, so the result is deterministic).  SX: device m x ldsx (ldsx >= d),
- * SY: device m.  Asynchronous on `stream`; the workspace size comes from
+ * SY: device m.  prec MIXED_FP8 (kind SRHT): SX holds m x ldsx E4M3 bytes (ldsx a multiple of
+ * 4, SX 4-byte aligned) followed by m x ceil(d/32) block-exponent bytes; SY is bf16.
+ * Asynchronous on `stream`; the workspace size comes from
  * slse_workspace_size(SLSE_OP_SKETCH) with sched->kind and sched->prec set. */
 slse_status slse_sketch(const slse_problem *prob, int32_t kind, int32_t prec, uint64_t seed, int64_t m,
                         void *SX, int64_t ldsx, void *SY, void *workspace, size_t ws_bytes,

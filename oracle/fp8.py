@@ -95,3 +95,19 @@ def dequantize_rows(Q, K) -> np.ndarray:
     for b in range(K.shape[1]):
         out[:, b * BLOCK:(b + 1) * BLOCK] = Q[:, b * BLOCK:(b + 1) * BLOCK] * np.ldexp(1.0, K[:, b])[:, None]
     return out
+
+
+def decode_e4m3(codes) -> np.ndarray:
+    """Values of E4M3 codes (uint8), from the bit-field definition (NaN codes -> nan)."""
+    table = np.empty(256)
+    for code in range(256):
+        s = -1.0 if code & 0x80 else 1.0
+        e = (code >> 3) & 0xF
+        m = code & 0x7
+        if e == 0xF and m == 0x7:
+            table[code] = np.nan
+        elif e == 0:
+            table[code] = s * m / 8.0 * 2.0 ** -6
+        else:
+            table[code] = s * (1.0 + m / 8.0) * 2.0 ** (e - 7)
+    return table[np.asarray(codes, np.int64)]

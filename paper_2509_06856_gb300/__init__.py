@@ -289,13 +289,24 @@ def ols_vjp(X, Y, beta, w, stream=None):
 
 def sketch(X, Y, m: int, seed: int = 0, prec: str = "fp64", workspace=None, stream=None, kind: str = "srht"):
     """slse_sketch: (S X, S Y) for one sketch of size m (kind "srht", "countsketch" or
-    "countsketch_hat").  FP64 -> float64, mixed -> bfloat16."""
+    "countsketch_hat").  FP64 -> float64, mixed_bf16 -> bfloat16; mixed_fp8 -> (E4M3 codes
+    (uint8, m x d), block exponents + 127 (uint8, m x ceil(d/32)), S Y in bfloat16)."""
     torch = _torch()
     p = problem(X, Y)
+    ws_ptr, ws_len = (workspace.data_ptr(), workspace.numel()) if workspace is not None else (None, 0)
+    if prec == "mixed_fp8":
+        # E4M3 bytes (m x ldq) followed by the block-exponent bytes (m x ceil(d/32))
+        ldq = (p.d + 15) // 16 * 16
+        nsb = (p.d + 31) // 32
+        buf = torch.empty(m * ldq + m * nsb, dtype=torch.uint8, device=X.device)
+        SY = torch.empty(m, dtype=torch.bfloat16, device=X.device)
+        st = _lib.slse_sketch(ctypes.byref(p), KIND[kind], PREC[prec], seed, m, buf.data_ptr(), ldq, SY.data_ptr(),
+                              ws_ptr, ws_len, _stream(stream))
+        _check(st, "slse_sketch")
+        return buf[:m * ldq].view(m, ldq)[:, :p.d], buf[m * ldq:].view(m, nsb), SY
     dt = torch.float64 if prec == "fp64" else torch.bfloat16
     SX = torch.empty((m, p.d), dtype=dt, device=X.device)
     SY = torch.empty(m, dtype=dt, device=X.device)
-    ws_ptr, ws_len = (workspace.data_ptr(), workspace.numel()) if workspace is not None else (None, 0)
     st = _lib.slse_sketch(ctypes.byref(p), KIND[kind], PREC[prec], seed, m, SX.data_ptr(), p.d, SY.data_ptr(), ws_ptr,
                           ws_len, _stream(stream))
     _check(st, "slse_sketch")

@@ -18,7 +18,7 @@ LIB = os.path.join(PKG, "libslse.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include")]
-SOURCES = ["api.cu", "draws.cu", "srht.cu", "grad.cu", "linalg.cu", "noalloc.cu", "countsketch.cu", "adjoint.cu"]
+SOURCES = ["api.cu", "draws.cu", "srht.cu", "grad.cu", "linalg.cu", "noalloc.cu", "countsketch.cu", "adjoint.cu", "fp8.cu"]
 
 
 def nvcc() -> str:

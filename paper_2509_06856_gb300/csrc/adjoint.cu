@@ -9,6 +9,7 @@
 // (8)), so it converges at the fit's rate: w+ = w + mu H^{-1}(v - X^T X w) + eta (w - w_prev).
 // Each iteration is one pass over X (the residual-gradient kernels with Y = 0).
 #include <cmath>
+#include <type_traits>
 
 #include "slse_internal.cuh"
 
@@ -34,85 +35,83 @@ __global__ void k_add_rhs(double *g, const double *v, int d, const DevState *st)
   if (i < d) g[i] = v[i] + g[i];
 }
 
-// One warp per row: a = x.w, p = x.beta (FP32 inputs: compensated products and sums,
-// so both dot products carry about twice the working precision), then
-// dY = a and dX = (y - p) w - a beta.
-template <class T>
+// One warp per row: a = x.w, p = x.beta (FP32 inputs: compensated products and sums with
+// w and beta split into float head + tail, so both dot products carry about twice the
+// working precision), then dY = a and dX = (y - p) w - a beta.  Lane l holds columns
+// l + 32 q, q < MQ (MQ = ceil(d / 32) rounded up to 4, 8 or 16).
+template <class T, int MQ>
 __global__ void __launch_bounds__(256) k_vjp_rows(const T *X, int64_t ldx, const T *Y, int64_t N, int d,
                                                   const double *beta, const double *w, T *dX, int64_t lddx, T *dY) {
-  constexpr int MQ = 16;  // d <= 512 = 32 lanes x 16
+  using Tw = std::conditional_t<sizeof(T) == 8, double, float>;
   const int lane = threadIdx.x & 31;
-  double bq[MQ], wq[MQ];
+  Tw bh[MQ], bl[MQ], wh[MQ], wl[MQ];
 #pragma unroll
   for (int q = 0; q < MQ; ++q) {
     const int c = lane + 32 * q;
-    bq[q] = c < d ? beta[c] : 0.0;
-    wq[q] = c < d ? w[c] : 0.0;
+    const double bv = c < d ? beta[c] : 0.0, wv = c < d ? w[c] : 0.0;
+    bh[q] = (Tw)bv; bl[q] = (Tw)(bv - (double)bh[q]);
+    wh[q] = (Tw)wv; wl[q] = (Tw)(wv - (double)wh[q]);
   }
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < N; i += nw) {
     const T *x = X + i * ldx;
-    double a, p;
+    T xv[MQ];
+#pragma unroll
+    for (int q = 0; q < MQ; ++q) {
+      const int c = lane + 32 * q;
+      xv[q] = c < d ? x[c] : T(0);
+    }
+    Tw rf, af;
     if constexpr (sizeof(T) == 8) {
-      a = 0.0; p = 0.0;
+      double a = 0.0, p = 0.0;
 #pragma unroll
       for (int q = 0; q < MQ; ++q) {
-        const int c = lane + 32 * q;
-        if (c < d) {
-          const double xv = x[c];
-          a = fma(xv, wq[q], a);
-          p = fma(xv, bq[q], p);
-        }
+        a = fma(xv[q], wh[q], a);
+        p = fma(xv[q], bh[q], p);
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_xor_sync(0xffffffffu, a, o);
         p += __shfl_xor_sync(0xffffffffu, p, o);
       }
+      af = a;
+      rf = Y[i] - p;
     } else {
+      // head/tail float pairs throughout (no FP64 arithmetic, which is slow on this part)
       float as = 0.f, ae = 0.f, ps = 0.f, pe = 0.f;
 #pragma unroll
       for (int q = 0; q < MQ; ++q) {
-        const int c = lane + 32 * q;
-        if (c < d) {
-          const float xv = (float)x[c];
-          const float wh = (float)wq[q], wl = (float)(wq[q] - (double)wh);
-          const float bh = (float)bq[q], bl = (float)(bq[q] - (double)bh);
-          float pr, er, s, e2;
-          two_prod(xv, wh, pr, er);
-          two_sum(as, pr, s, e2);
-          as = s;
-          ae += e2 + er + xv * wl;
-          two_prod(xv, bh, pr, er);
-          two_sum(ps, pr, s, e2);
-          ps = s;
-          pe += e2 + er + xv * bl;
-        }
+        float pr, er, s, e2;
+        two_prod(xv[q], wh[q], pr, er);
+        two_sum(as, pr, s, e2);
+        as = s;
+        ae += e2 + er + xv[q] * wl[q];
+        two_prod(xv[q], bh[q], pr, er);
+        two_sum(ps, pr, s, e2);
+        ps = s;
+        pe += e2 + er + xv[q] * bl[q];
       }
-      a = (double)as + (double)ae;
-      p = (double)ps + (double)pe;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        p += __shfl_xor_sync(0xffffffffu, p, o);
+        const float as2 = __shfl_xor_sync(0xffffffffu, as, o), ae2 = __shfl_xor_sync(0xffffffffu, ae, o);
+        const float ps2 = __shfl_xor_sync(0xffffffffu, ps, o), pe2 = __shfl_xor_sync(0xffffffffu, pe, o);
+        float t, e;
+        two_sum(as, as2, t, e);
+        as = t; ae = (ae + ae2) + e;
+        two_sum(ps, ps2, t, e);
+        ps = t; pe = (pe + pe2) + e;
       }
+      float rh, re;
+      two_sum((float)Y[i], -ps, rh, re);
+      rf = rh + (re - pe);
+      af = as + ae;
     }
-    const double r = (double)Y[i] - p;
-    if (lane == 0) dY[i] = (T)a;
+    if (lane == 0) dY[i] = (T)af;
     T *o = dX + i * lddx;
-    if constexpr (sizeof(T) == 8) {
 #pragma unroll
-      for (int q = 0; q < MQ; ++q) {
-        const int c = lane + 32 * q;
-        if (c < d) o[c] = fma(r, wq[q], -a * bq[q]);
-      }
-    } else {
-      const float rf = (float)r, af = (float)a;
-#pragma unroll
-      for (int q = 0; q < MQ; ++q) {
-        const int c = lane + 32 * q;
-        if (c < d) o[c] = fmaf(rf, (float)wq[q], -af * (float)bq[q]);
-      }
+    for (int q = 0; q < MQ; ++q) {
+      const int c = lane + 32 * q;
+      if (c < d) o[c] = (T)fma(rf, wh[q], -af * bh[q]);
     }
   }
 }
@@ -319,14 +318,23 @@ extern "C" slse_status slse_ols_vjp(const slse_problem *prob, const double *beta
   if (nsm <= 0) return SLSE_ECUDA;
   cudaStream_t s = (cudaStream_t)stream;
   const unsigned grid = (unsigned)(8 * nsm);
-  if (prob->dtype == SLSE_F64)
-    k_vjp_rows<double><<<grid, 256, 0, s>>>(static_cast<const double *>(prob->X), prob->ldx,
-                                             static_cast<const double *>(prob->Y), prob->N, prob->d, beta, w,
-                                             static_cast<double *>(dX), lddx, static_cast<double *>(dY));
-  else
-    k_vjp_rows<float><<<grid, 256, 0, s>>>(static_cast<const float *>(prob->X), prob->ldx,
-                                            static_cast<const float *>(prob->Y), prob->N, prob->d, beta, w,
-                                            static_cast<float *>(dX), lddx, static_cast<float *>(dY));
+  auto run = [&](auto tag, auto mq) {
+    using T = decltype(tag);
+    constexpr int MQ = decltype(mq)::value;
+    k_vjp_rows<T, MQ><<<grid, 256, 0, s>>>(static_cast<const T *>(prob->X), prob->ldx,
+                                           static_cast<const T *>(prob->Y), prob->N, prob->d, beta, w,
+                                           static_cast<T *>(dX), lddx, static_cast<T *>(dY));
+  };
+  const int d = prob->d;
+  if (prob->dtype == SLSE_F64) {
+    if (d <= 128) run(double{}, std::integral_constant<int, 4>{});
+    else if (d <= 256) run(double{}, std::integral_constant<int, 8>{});
+    else run(double{}, std::integral_constant<int, 16>{});
+  } else {
+    if (d <= 128) run(float{}, std::integral_constant<int, 4>{});
+    else if (d <= 256) run(float{}, std::integral_constant<int, 8>{});
+    else run(float{}, std::integral_constant<int, 16>{});
+  }
   if (cudaGetLastError() != cudaSuccess) return SLSE_ECUDA;
   return SLSE_OK;
 }

@@ -80,8 +80,9 @@ bool make_sched(const slse_problem *p, const slse_schedule *s, Sched &o) {
   }
   if (s->K < 0 || (s->K > 0 && (!s->m || !s->a))) return false;
   if (s->kind != SLSE_SRHT && s->kind != SLSE_COUNTSKETCH) return false;
-  if (s->prec != SLSE_PREC_FP64 && s->prec != SLSE_PREC_MIXED_BF16) return false;
-  if (s->prec == SLSE_PREC_MIXED_BF16 && p->dtype != SLSE_F32) return false;
+  if (s->prec != SLSE_PREC_FP64 && s->prec != SLSE_PREC_MIXED_BF16 && s->prec != SLSE_PREC_MIXED_FP8) return false;
+  if (s->prec != SLSE_PREC_FP64 && p->dtype != SLSE_F32) return false;
+  if (s->prec == SLSE_PREC_MIXED_FP8 && s->kind != SLSE_SRHT) return false;  // FP8 form: SRHT only
   if (s->r < p->d || s->r > Np || s->T < 0) return false;
   if (!std::isfinite(s->mu) || !std::isfinite(s->eta) || !std::isfinite(s->tol)) return false;
   o.m.assign(s->m, s->m + s->K);
@@ -111,6 +112,7 @@ struct Layout {
 
 struct FitLayout {
   int64_t Np, n_samp, h0, ldu;
+  int64_t ld16, nsb;        // FP8 form: BF16 leading dimension, scale bytes per row
   SrhtPlan sp;
   bool cs;                  // CountSketch family instead of the SRHT
   CsPlan csp;
@@ -119,11 +121,14 @@ struct FitLayout {
   bool host_in;
   size_t o_xin, o_yin;
   size_t o_state, o_psd, o_sigma, o_pos, o_big, o_wy, o_u, o_v, o_A, o_R, o_Hinv, o_qr, o_chol, o_part, o_g,
-      o_ring, o_b0, o_d32, o_out, o_r0;
+      o_ring, o_b0, o_d32, o_out, o_r0, o_us, o_hat16;
   size_t total;
 };
 
-size_t elem_bytes_u(int prec) { return prec == SLSE_PREC_FP64 ? 8 : 2; }
+// bytes per element of the sketch rows U, of the pass-1 intermediate W and of V
+size_t elem_bytes_u(int prec) { return prec == SLSE_PREC_FP64 ? 8 : (prec == SLSE_PREC_MIXED_FP8 ? 1 : 2); }
+size_t elem_bytes_w(int prec) { return prec == SLSE_PREC_FP64 ? 8 : 2; }
+int64_t mx_blocks(int d) { return (d + 31) / 32; }
 
 FitLayout fit_layout(const slse_problem *p, const Sched &s, int nsm) {
   FitLayout L{};
@@ -141,8 +146,11 @@ FitLayout fit_layout(const slse_problem *p, const Sched &s, int nsm) {
     L.csp = cs_plan(p->N, d, s.prec, s.m.empty() ? 0 : s.m.front(), mK, s.r);
   } else if (mK + s.r <= L.Np) { L.h0 = mK; L.n_samp = mK + s.r; }
   else { L.h0 = 0; L.n_samp = mK > s.r ? mK : s.r; }
-  L.ldu = (d + 7) & ~int64_t(7);
-  const size_t eu = elem_bytes_u(s.prec);
+  const bool fp8 = s.prec == SLSE_PREC_MIXED_FP8;
+  L.ld16 = (d + 7) & ~int64_t(7);
+  L.ldu = fp8 ? ((d + 15) & ~int64_t(15)) : L.ld16;
+  L.nsb = mx_blocks(d);
+  const size_t eu = elem_bytes_u(s.prec), ew = elem_bytes_w(s.prec), ev = fp8 ? 2 : eu;
   L.nblk = 2 * (nsm > 0 ? nsm : 152);
   Layout w;
   L.o_state = w.take(kStateBytes);
@@ -151,25 +159,29 @@ FitLayout fit_layout(const slse_problem *p, const Sched &s, int nsm) {
   L.o_sigma = w.take(nperm);
   L.o_pos = w.take(nperm);
   size_t big = L.cs ? L.csp.total : draws_ws_bytes(L.Np);
-  const size_t wbytes = (L.sp.single || L.cs) ? 0 : (size_t)L.Np * L.ldu * eu;
-  const size_t wybytes = (L.sp.single || L.cs) ? 0 : (size_t)L.Np * eu;
+  const size_t wbytes = (L.sp.single || L.cs) ? 0 : (size_t)L.Np * L.ld16 * ew;
+  const size_t wybytes = (L.sp.single || L.cs) ? 0 : (size_t)L.Np * ew;
   if (wbytes + align256(wybytes) + 256 > big) big = align256(wbytes) + align256(wybytes);
+  // FP8 form at single-pass sizes: the BF16 rows are formed in this region, then quantised
+  if (fp8 && L.sp.single && (size_t)L.n_samp * L.ld16 * 2 > big) big = (size_t)L.n_samp * L.ld16 * 2;
   L.o_big = w.take(big);
   L.o_wy = L.o_big + align256(wbytes);
   L.o_u = w.take((size_t)L.n_samp * L.ldu * eu);
-  L.o_v = w.take((size_t)L.n_samp * eu);
+  L.o_v = w.take((size_t)L.n_samp * ev);
+  L.o_us = w.take(fp8 ? (size_t)L.n_samp * L.nsb : 0);
+  L.o_hat16 = w.take(fp8 ? (size_t)s.r * L.ld16 * 2 : 0);
   L.o_A = w.take((size_t)s.r * d * 8);
   L.o_R = w.take((size_t)d * d * 8);
   L.o_Hinv = w.take((size_t)d * d * 8);
   L.o_qr = w.take(qr_ws_bytes(s.r, d, nsm > 0 ? nsm : 152));
-  L.o_chol = w.take(s.prec == SLSE_PREC_MIXED_BF16 ? chol_ws_bytes(s.r, d) : 0);
+  L.o_chol = w.take(s.prec != SLSE_PREC_FP64 ? chol_ws_bytes(s.r, d) : 0);
   L.o_part = w.take((size_t)L.nblk * d * 8);
   L.o_g = w.take((size_t)d * 8);
   L.o_ring = w.take((size_t)3 * d * 8);
   L.o_b0 = w.take((size_t)d * 8);
   L.o_d32 = w.take((size_t)d * 4);
   L.o_out = w.take((size_t)d * 8);
-  L.o_r0 = w.take(s.prec == SLSE_PREC_MIXED_BF16 ? (size_t)p->N * 4 : 0);
+  L.o_r0 = w.take(s.prec != SLSE_PREC_FP64 ? (size_t)p->N * 4 : 0);
   L.host_in = is_host_pointer(p->X);
   if (L.host_in) {
     const size_t bx = p->dtype == SLSE_F64 ? 8 : 4;
@@ -186,12 +198,12 @@ struct SketchLayout {
   size_t o_psd, o_sigma, o_pos, o_big, o_wy, total;
 };
 
-SketchLayout sketch_layout(const slse_problem *p, int prec) {
+SketchLayout sketch_layout(const slse_problem *p, int prec, int64_t m) {
   SketchLayout L{};
   L.Np = padded(p->N);
   L.sp = srht_plan(L.Np);
   L.ldw = (p->d + 7) & ~int64_t(7);
-  const size_t eu = elem_bytes_u(prec);
+  const size_t eu = elem_bytes_w(prec);
   Layout w;
   L.o_psd = w.take(4 * (size_t)L.Np);
   L.o_sigma = w.take(4 * (size_t)L.Np);
@@ -200,6 +212,8 @@ SketchLayout sketch_layout(const slse_problem *p, int prec) {
   const size_t wbytes = L.sp.single ? 0 : (size_t)L.Np * L.ldw * eu;
   const size_t wybytes = L.sp.single ? 0 : (size_t)L.Np * eu;
   if (align256(wbytes) + align256(wybytes) > big) big = align256(wbytes) + align256(wybytes);
+  // FP8 form at single-pass sizes: BF16 rows first, then quantised
+  if (prec == SLSE_PREC_MIXED_FP8 && L.sp.single && (size_t)m * L.ldw * 2 > big) big = (size_t)m * L.ldw * 2;
   L.o_big = w.take(big);
   L.o_wy = L.o_big + align256(wbytes);
   L.total = w.total;
@@ -348,9 +362,11 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
   double *b0 = reinterpret_cast<double *>(base + L.o_b0);
   float *d32 = reinterpret_cast<float *>(base + L.o_d32);
   double *outb = reinterpret_cast<double *>(base + L.o_out);
-  float *r0 = s.prec == SLSE_PREC_MIXED_BF16 ? reinterpret_cast<float *>(base + L.o_r0) : nullptr;
+  float *r0 = s.prec != SLSE_PREC_FP64 ? reinterpret_cast<float *>(base + L.o_r0) : nullptr;
   const int d = p->d;
-  const bool mixed = s.prec == SLSE_PREC_MIXED_BF16;
+  const bool mixed = s.prec != SLSE_PREC_FP64;     // BF16 or FP8 sketch, FP32 2nd-stage passes
+  const bool fp8 = s.prec == SLSE_PREC_MIXED_FP8;
+  uint8_t *Us = fp8 ? reinterpret_cast<uint8_t *>(base + L.o_us) : nullptr;
   const int T = s.T;
   int kernels = 0;
 
@@ -385,8 +401,11 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     void *yd = base + L.o_yin;
     CK(cudaStreamCreateWithFlags(&side.h, cudaStreamNonBlocking));
     CK(cudaStreamWaitEvent(side.h, e_start, 0));
-    CK(cudaMemcpy2DAsync(xd, (size_t)d * bx, pin->X, (size_t)pin->ldx * bx, (size_t)d * bx, (size_t)p->N,
-                         cudaMemcpyHostToDevice, side.h));
+    if (pin->ldx == d)  // contiguous rows: one linear copy (a pitched copy splits it per row)
+      CK(cudaMemcpyAsync(xd, pin->X, (size_t)p->N * d * bx, cudaMemcpyHostToDevice, side.h));
+    else
+      CK(cudaMemcpy2DAsync(xd, (size_t)d * bx, pin->X, (size_t)pin->ldx * bx, (size_t)d * bx, (size_t)p->N,
+                           cudaMemcpyHostToDevice, side.h));
     CK(cudaMemcpyAsync(yd, pin->Y, (size_t)p->N * bx, cudaMemcpyHostToDevice, side.h));
     CK(cudaEventRecord(e_copied, side.h));
     prob.X = xd;
@@ -423,9 +442,22 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     CK(cudaEventRecord(e_draws, st));
     if (L.host_in) CK(cudaStreamWaitEvent(st, e_copied, 0));
     // a2-a4: SRHT into the sampled rows (U = Z[sigma] with Z = H D P X / sqrt(N'); sketch scales applied later)
-    CK(launch_srht(L.sp, s.prec, p->dtype, p->X, p->ldx, p->Y, p->N, d, Psd, pos, big, WY, L.ldu, U, V, L.ldu,
-                   1.0 / std::sqrt((double)L.Np), st, L.sp.single ? nullptr : e_mid));
-    kernels += L.sp.single ? 1 : 2;
+    __nv_bfloat16 *h16 = fp8 ? reinterpret_cast<__nv_bfloat16 *>(base + L.o_hat16) : nullptr;
+    if (fp8 && L.sp.single) {  // one-pass sizes: BF16 rows, then the FP8 form (S-hat rows stay BF16)
+      CK(launch_srht(L.sp, SLSE_PREC_MIXED_BF16, p->dtype, p->X, p->ldx, p->Y, p->N, d, Psd, pos, nullptr, nullptr,
+                     L.ld16, big, V, L.ld16, 1.0 / std::sqrt((double)L.Np), st, nullptr));
+      CK(launch_quantize_mx(static_cast<const __nv_bfloat16 *>(big), L.ld16, L.n_samp, d, static_cast<uint8_t *>(U),
+                            L.ldu, Us, L.nsb, st));
+      CK(cudaMemcpyAsync(h16, static_cast<const __nv_bfloat16 *>(big) + (size_t)L.h0 * L.ld16,
+                         (size_t)s.r * L.ld16 * 2, cudaMemcpyDeviceToDevice, st));
+      kernels += 2;
+    } else {
+      // FP8 form: the Hessian-sketch rows (sampling positions >= h0) are written in BF16 to h16
+      CK(launch_srht(L.sp, s.prec, p->dtype, p->X, p->ldx, p->Y, p->N, d, Psd, pos, big, WY, L.ld16, U, V, L.ldu,
+                     1.0 / std::sqrt((double)L.Np), st, L.sp.single ? nullptr : e_mid, Us, L.nsb, h16,
+                     L.h0 > 0 ? L.h0 : INT64_MAX, L.ld16));
+      kernels += L.sp.single ? 1 : 2;
+    }
   }
   CK(cudaEventRecord(e_sketch, st));
   // sketch scales: SRHT S_i X = sqrt(N'/m_i) U[rows], S-hat X = sqrt(N'/r) U[h0 ..]; CountSketch: 1
@@ -434,8 +466,19 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
   // Householder QR.  Mixed path: FP64 Cholesky of the exactly accumulated Gram matrix of the
   // BF16 rows (the same R), with the Householder QR as fallback on a non-positive pivot.
   bool use_qr = !mixed;
+  // the Hessian-sketch rows as BF16 (the FP8 form is widened exactly)
+  const void *Uh = U;
+  int64_t ldh = L.ldu, h0 = L.h0;
+  if (fp8) {
+    __nv_bfloat16 *h16 = reinterpret_cast<__nv_bfloat16 *>(base + L.o_hat16);
+    if (L.h0 == 0 && !L.sp.single) {  // S-hat shares the prefix rows (m_K + r > N'): widen them
+      CK(launch_mx_to_bf16(static_cast<const uint8_t *>(U), L.ldu, Us, L.nsb, s.r, d, h16, L.ld16, st));
+      ++kernels;
+    }
+    Uh = h16; ldh = L.ld16; h0 = 0;
+  }
   if (mixed) {
-    CK(launch_gram_chol(U, L.ldu, L.h0, s.r, d, sq_scale(s.r), R, Hinv, base + L.o_chol, dst, st));
+    CK(launch_gram_chol(Uh, ldh, h0, s.r, d, sq_scale(s.r), R, Hinv, base + L.o_chol, dst, st));
     const int nt = (d + 31) / 32;
     kernels += 2 + 3 * nt + 2;
     DevState *mb = t_mailbox.get();
@@ -450,7 +493,8 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     }
   }
   if (use_qr) {
-    CK(launch_gather_hessian_rows(s.prec, U, L.ldu, L.h0, s.r, d, std::sqrt(sq_scale(s.r)), A, st));
+    CK(launch_gather_hessian_rows(fp8 ? SLSE_PREC_MIXED_BF16 : s.prec, Uh, ldh, h0, s.r, d, std::sqrt(sq_scale(s.r)),
+                                  A, st));
     CK(launch_qr(A, s.r, d, d, R, Hinv, qrws, dst, st));
     kernels += 4;
   }
@@ -472,10 +516,14 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     // SRHT: the prefix U[0:m_i]; CountSketch: the block of U holding S_i X
     const size_t r0w = L.cs ? (size_t)L.lvl_off[i] : 0;
     const void *Ui = static_cast<const char *>(U) + r0w * L.ldu * eu;
-    const void *Vi = static_cast<const char *>(V) + r0w * eu;
+    const void *Vi = static_cast<const char *>(V) + r0w * (fp8 ? 2 : eu);
     for (int j = 0; j < s.a[i] && t < T; ++j) {
-      CK(launch_grad(mixed ? GM_STAGE1_BF16 : GM_STAGE1_F64, mixed ? SLSE_BF16 : SLSE_F64, Ui, L.ldu, Vi, m, d,
-                     ring, dst, nullptr, nullptr, nullptr, part, nb, 0, st));
+      if (fp8)
+        CK(launch_grad_mx(static_cast<const uint8_t *>(Ui), L.ldu, Us + r0w * L.nsb, L.nsb,
+                          static_cast<const __nv_bfloat16 *>(Vi), m, d, ring, dst, part, nb, st));
+      else
+        CK(launch_grad(mixed ? GM_STAGE1_BF16 : GM_STAGE1_F64, mixed ? SLSE_BF16 : SLSE_F64, Ui, L.ldu, Vi, m, d,
+                       ring, dst, nullptr, nullptr, nullptr, part, nb, 0, st));
       CK(launch_reduce(part, nb, d, sq_scale(m), g, dst, 0, st));
       ua.first = (j == 0 && s.momentum_reset) || t == 0;
       ua.stage2 = 0; ua.thr = 0.0; ua.mixed = 0; ua.check_done = 0;
@@ -594,7 +642,7 @@ size_t slse_workspace_size(const slse_problem *prob, const slse_schedule *sched,
       const int kind = sched ? sched->kind : SLSE_SRHT;
       if (kind == SLSE_COUNTSKETCH) return is_pow2(arg) ? cs_plan(prob->N, prob->d, prec, arg, arg, 0).total : 0;
       if (kind == SLSE_COUNTSKETCH_HAT) return arg >= 1 ? cs_plan(prob->N, prob->d, prec, 0, 0, arg).total : 0;
-      return sketch_layout(prob, prec).total;
+      return sketch_layout(prob, prec, arg).total;
     }
     case SLSE_OP_GRAD:
       if (!valid_problem(prob)) return 0;
@@ -633,8 +681,10 @@ slse_status slse_sketch(const slse_problem *prob, int32_t kind, int32_t prec, ui
   if (!valid_problem(prob) || !SX || !SY) return SLSE_EINVAL;
   if (is_host_pointer(prob->X) || is_host_pointer(prob->Y)) return SLSE_EINVAL;
   if (kind != SLSE_SRHT && kind != SLSE_COUNTSKETCH && kind != SLSE_COUNTSKETCH_HAT) return SLSE_EINVAL;
-  if (prec != SLSE_PREC_FP64 && prec != SLSE_PREC_MIXED_BF16) return SLSE_EINVAL;
-  if (prec == SLSE_PREC_MIXED_BF16 && prob->dtype != SLSE_F32) return SLSE_EINVAL;
+  if (prec != SLSE_PREC_FP64 && prec != SLSE_PREC_MIXED_BF16 && prec != SLSE_PREC_MIXED_FP8) return SLSE_EINVAL;
+  if (prec != SLSE_PREC_FP64 && prob->dtype != SLSE_F32) return SLSE_EINVAL;
+  if (prec == SLSE_PREC_MIXED_FP8 && (kind != SLSE_SRHT || ldsx % 4 != 0 || reinterpret_cast<uintptr_t>(SX) % 4 != 0))
+    return SLSE_EINVAL;
   const int64_t Np = padded(prob->N);
   if (m < 1 || m > Np || ldsx < prob->d) return SLSE_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
@@ -654,7 +704,7 @@ slse_status slse_sketch(const slse_problem *prob, int32_t kind, int32_t prec, ui
                           hat ? SY : nullptr, ldsx, W.ptr, st));
     return SLSE_OK;
   }
-  const SketchLayout L = sketch_layout(prob, prec);
+  const SketchLayout L = sketch_layout(prob, prec, m);
   Workspace W;
   slse_status a = acquire(W, workspace, ws_bytes, L.total, st);
   if (a != SLSE_OK) return a;
@@ -664,6 +714,21 @@ slse_status slse_sketch(const slse_problem *prob, int32_t kind, int32_t prec, ui
   int32_t *pos = reinterpret_cast<int32_t *>(base + L.o_pos);
   CK(launch_draws(Np, seed, Psd, nullptr, sigma, nullptr, base + L.o_big, st));
   CK(launch_pos_map(sigma, Np, 0, m, L.sp.single ? L.sp.logN : L.sp.log2, pos, st));
+  if (prec == SLSE_PREC_MIXED_FP8) {
+    // SX: m x ldsx E4M3 bytes followed by the m x ceil(d/32) block-exponent bytes
+    uint8_t *scales = static_cast<uint8_t *>(SX) + (size_t)m * ldsx;
+    const int64_t nsb = mx_blocks(prob->d);
+    if (L.sp.single) {
+      CK(launch_srht(L.sp, SLSE_PREC_MIXED_BF16, prob->dtype, prob->X, prob->ldx, prob->Y, prob->N, prob->d, Psd, pos,
+                     nullptr, nullptr, L.ldw, base + L.o_big, SY, L.ldw, 1.0 / std::sqrt((double)m), st, nullptr));
+      CK(launch_quantize_mx(reinterpret_cast<const __nv_bfloat16 *>(base + L.o_big), L.ldw, m, prob->d,
+                            static_cast<uint8_t *>(SX), ldsx, scales, nsb, st));
+    } else {
+      CK(launch_srht(L.sp, prec, prob->dtype, prob->X, prob->ldx, prob->Y, prob->N, prob->d, Psd, pos, base + L.o_big,
+                     base + L.o_wy, L.ldw, SX, SY, ldsx, 1.0 / std::sqrt((double)m), st, nullptr, scales, nsb));
+    }
+    return SLSE_OK;
+  }
   CK(launch_srht(L.sp, prec, prob->dtype, prob->X, prob->ldx, prob->Y, prob->N, prob->d, Psd, pos, base + L.o_big,
                  base + L.o_wy, L.ldw, SX, SY, ldsx, 1.0 / std::sqrt((double)m), st, nullptr));
   return SLSE_OK;

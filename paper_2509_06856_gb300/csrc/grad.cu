@@ -567,14 +567,24 @@ cudaError_t launch_grad(int mode, int xdtype, const void *X, int64_t ldx, const 
     case GM_STAGE1_BF16:
       // the sketch buffer's padding columns are never written: the vector path requires
       // d % 8 == 0 so that no padding word is read
-      if (d % 8 == 0 && ldx % 8 == 0 && aligned(X, ldx, 2, 8)) return launch1(k_grad_bf16v<2, 4>, nblk, a, s);
+      // lanes cover 8 columns per word: one word per lane up to d = 256 (more rows in flight)
+      if (d % 8 == 0 && ldx % 8 == 0 && aligned(X, ldx, 2, 8))
+        return d <= 256 ? launch1(k_grad_bf16v<1, 6>, nblk, a, s) : launch1(k_grad_bf16v<2, 4>, nblk, a, s);
       return launch1(k_grad_bf16s<16>, nblk, a, s);
     case GM_MIXED: {
       if (xdtype != SLSE_F32) return cudaErrorInvalidValue;
       const bool vec = d % 4 == 0 && aligned(X, ldx, 4, 4);
-      cudaError_t e = vec ? launch1(k_grad_mixed<4, 4, 1, 2>, nblk, a, s) : launch1(k_grad_mixed<1, 16, 1, 1>, nblk, a, s);
+      // rows in flight per warp grow as d shrinks (the same 32 x-values per lane)
+      cudaError_t e;
+      if (!vec) e = launch1(k_grad_mixed<1, 16, 1, 1>, nblk, a, s);
+      else if (d <= 128) e = launch1(k_grad_mixed<4, 1, 1, 8>, nblk, a, s);
+      else if (d <= 256) e = launch1(k_grad_mixed<4, 2, 1, 4>, nblk, a, s);
+      else e = launch1(k_grad_mixed<4, 4, 1, 2>, nblk, a, s);
       if (e != cudaSuccess) return e;
-      return vec ? launch1(k_grad_mixed<4, 4, 0, 2>, nblk, a, s) : launch1(k_grad_mixed<1, 16, 0, 1>, nblk, a, s);
+      if (!vec) return launch1(k_grad_mixed<1, 16, 0, 1>, nblk, a, s);
+      if (d <= 128) return launch1(k_grad_mixed<4, 1, 0, 8>, nblk, a, s);
+      if (d <= 256) return launch1(k_grad_mixed<4, 2, 0, 4>, nblk, a, s);
+      return launch1(k_grad_mixed<4, 4, 0, 2>, nblk, a, s);
     }
     default:
       return cudaErrorInvalidValue;

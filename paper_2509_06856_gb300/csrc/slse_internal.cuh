@@ -124,6 +124,16 @@ cudaError_t launch_countsketch(const CsPlan &pl, int xdtype, const void *X, int6
                                void *const *lvX, void *const *lvY, int64_t ldo, void *hatX, void *hatY, int64_t ldh,
                                void *ws, cudaStream_t s);
 
+// fp8.cu: the FP8 form of the sketch (E4M3 values, one power-of-two scale per 32-column
+// block of a row, byte = exponent + 127; Y values in BF16).
+cudaError_t launch_grad_mx(const uint8_t *U, int64_t ldq, const uint8_t *S, int64_t nsb, const __nv_bfloat16 *V,
+                           int64_t nrows, int d, const double *beta_ring, const DevState *st, double *part, int nblk,
+                           cudaStream_t s);
+cudaError_t launch_mx_to_bf16(const uint8_t *U, int64_t ldq, const uint8_t *S, int64_t nsb, int64_t rows, int d,
+                              __nv_bfloat16 *out, int64_t ldo, cudaStream_t s);
+cudaError_t launch_quantize_mx(const __nv_bfloat16 *A, int64_t lda, int64_t rows, int d, uint8_t *U, int64_t ldq,
+                               uint8_t *S, int64_t nsb, cudaStream_t s);
+
 // draws.cu
 size_t draws_ws_bytes(int64_t Np);
 cudaError_t launch_draws(int64_t Np, uint64_t seed, int32_t *Psd /*N', sign-folded P*/,
@@ -146,7 +156,10 @@ SrhtPlan srht_plan(int64_t Np);
 cudaError_t launch_srht(const SrhtPlan &pl, int prec, int xdtype, const void *X, int64_t ldx,
                         const void *Y, int64_t N, int d, const int32_t *Psd, const int32_t *pos,
                         void *W, void *WY, int64_t ldw, void *U, void *V, int64_t ldu, double scale,
-                        cudaStream_t s, cudaEvent_t ev_mid /* nullable: recorded between the passes */);
+                        cudaStream_t s, cudaEvent_t ev_mid /* nullable: recorded between the passes */,
+                        uint8_t *Uscale = nullptr /* MIXED_FP8: block exponents of U */, int64_t ld_scale = 0,
+                        __nv_bfloat16 *hat = nullptr /* MIXED_FP8: rows >= hat_row0 in BF16 here */,
+                        int64_t hat_row0 = 0, int64_t hat_ld = 0);
 
 // grad.cu
 enum GradMode { GM_F64 = 0, GM_MIXED = 1, GM_STAGE1_BF16 = 2, GM_STAGE1_F64 = 3 };

@@ -23,6 +23,9 @@
 // every warp access is coalesced.  The work is adds/subtracts only: HBM-bound in
 // FP32, FP64-ALU-bound in FP64 on this part.
 #include <cooperative_groups.h>
+#include <cuda_fp8.h>
+
+#include <type_traits>
 
 #include "slse_internal.cuh"
 
@@ -30,6 +33,10 @@ namespace cg = cooperative_groups;
 
 namespace slse {
 namespace {
+
+// Output tag for the FP8 form of the sketch: E4M3 values with one power-of-two scale per
+// 32-column block of a row (scale byte = exponent + 127); the rows' Y values stay BF16.
+struct mx8 {};
 
 struct GroupArgs {
   const void *in;       // X (pass 1 / single) or W (pass 2)
@@ -47,8 +54,29 @@ struct GroupArgs {
   int nslab;
   int logq;
   int vec_in, vec_out;  // 1: rows allow VEC-wide vector access
+  uint8_t *out_scale;   // FP8 form: block exponents, ld_scale bytes per row
+  int64_t ld_scale;
+  __nv_bfloat16 *hat_out;  // FP8 form: output rows >= hat_row0 go here in BF16 (nullable)
+  int64_t hat_row0, hat_ld;
   double scale;
 };
+
+// Smallest k with amax <= 448 2^k (448 = 1.75 2^8, the largest E4M3 value), clamped to
+// the E8M0 range; -127 for amax = 0.  Exact, from the float's bit fields.
+__device__ __forceinline__ int mx_exponent(float amax) {
+  const uint32_t b = __float_as_uint(amax);
+  const int E = (int)((b >> 23) & 0xFFu);
+  if (!(amax > 0.f) || E == 0) return -127;
+  const int k = (b & 0x7FFFFFu) <= 0x600000u ? (E - 127) - 8 : (E - 127) - 7;
+  return k < -127 ? -127 : (k > 127 ? 127 : k);
+}
+
+// Four values scaled by 2^-k and rounded to E4M3 (nearest, ties to even), packed in order.
+__device__ __forceinline__ uint32_t mx_pack4(float x0, float x1, float x2, float x3, float inv) {
+  const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(x0 * inv, x1 * inv), __NV_SATFINITE, __NV_E4M3);
+  const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(x2 * inv, x3 * inv), __NV_SATFINITE, __NV_E4M3);
+  return (lo & 0xFFFFu) | (hi << 16);
+}
 
 template <class T> __device__ __forceinline__ float to_f(T v);
 template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
@@ -318,16 +346,52 @@ __global__ void __launch_bounds__(NT, MINB) k_group(const GroupArgs a) {
     for (int q = 0; q < Q; ++q) {
       const int64_t kappa = (int64_t)q * M + l;
       const int64_t dst = a.pos ? (int64_t)s_dst[q * MQ + lq] : kappa * a.ostride + g * a.ogstride;
-      if (dst < 0) continue;
-      Ts o[VO];
+      if constexpr (std::is_same_v<Tout, mx8>) {
+        // the 8 consecutive lanes with the same lq hold this row's 32-column block
+        static_assert(VO == 4 && C == 32 && sizeof(Ts) == 4, "an FP8 block is one 32-column FP32 slab");
+        float am = 0.f;
 #pragma unroll
-      for (int e = 0; e < VO; ++e) o[e] = v[e][q];
-      if (fast_out) {
-        store_vec<Tout, Ts, VO>(out + dst * a.ldout + col, o);
+        for (int e = 0; e < VO; ++e) am = fmaxf(am, fabsf(v[e][q]));
+        am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, 1));
+        am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, 2));
+        am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, 4));
+        const int k = mx_exponent(am);
+        const float inv = ldexpf(1.f, -k);
+        if (dst >= 0 && a.hat_out && dst >= a.hat_row0) {
+          // the Hessian-sketch rows keep the BF16 form (they set the preconditioner)
+          float o[VO] = {v[0][q], v[1][q], v[2][q], v[3][q]};
+          __nv_bfloat16 *hrow = a.hat_out + (dst - a.hat_row0) * a.hat_ld;
+          if (col + VO <= d) {
+            store_vec<__nv_bfloat16, float, VO>(hrow + col, o);
+          } else {
+#pragma unroll
+            for (int e = 0; e < VO; ++e)
+              if (col + e < d) hrow[col + e] = __float2bfloat16_rn(o[e]);
+          }
+        } else if (dst >= 0) {
+          uint8_t *orow = reinterpret_cast<uint8_t *>(a.out) + dst * a.ldout;
+          if (col + VO <= d) {
+            *reinterpret_cast<uint32_t *>(orow + col) = mx_pack4(v[0][q], v[1][q], v[2][q], v[3][q], inv);
+          } else {
+            const uint32_t w = mx_pack4(v[0][q], v[1][q], v[2][q], v[3][q], inv);
+#pragma unroll
+            for (int e = 0; e < VO; ++e)
+              if (col + e < d) orow[col + e] = (uint8_t)(w >> (8 * e));
+          }
+          if (cq == 0) a.out_scale[dst * a.ld_scale + slab] = (uint8_t)(k + 127);
+        }
       } else {
+        if (dst < 0) continue;
+        Ts o[VO];
 #pragma unroll
-        for (int e = 0; e < VO; ++e)
-          if (col + e < d) store_cvt(out + dst * a.ldout + col + e, o[e]);
+        for (int e = 0; e < VO; ++e) o[e] = v[e][q];
+        if (fast_out) {
+          store_vec<Tout, Ts, VO>(out + dst * a.ldout + col, o);
+        } else {
+#pragma unroll
+          for (int e = 0; e < VO; ++e)
+            if (col + e < d) store_cvt(out + dst * a.ldout + col + e, o[e]);
+        }
       }
     }
   }
@@ -479,7 +543,8 @@ cudaError_t launch_pass_t(const GroupArgs &a, int L, int64_t ngroups, cudaStream
   }
   if (e != cudaSuccess) return e;
   const size_t ysm = (size_t)(1 << L) * sizeof(Ts);
-  auto ykern = k_ycol<Tin, Ts, Tout>;
+  using TY = std::conditional_t<std::is_same_v<Tout, mx8>, __nv_bfloat16, Tout>;  // FP8 form: Y in BF16
+  auto ykern = k_ycol<Tin, Ts, TY>;
   if ((e = cudaFuncSetAttribute(ykern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ysm)) != cudaSuccess) return e;
   ykern<<<(unsigned)ngroups, 512, ysm, s>>>(a, L);
   return cudaGetLastError();
@@ -501,7 +566,9 @@ template <class Tin, class Ts, class Tout, int C, int VA, int VB, int VO>
 cudaError_t run_plan(const SrhtPlan &pl, const void *X, int64_t ldx, const void *Y, int64_t N, int d,
                      const int32_t *Psd, const int32_t *pos, void *W, void *WY, int64_t ldw, void *U,
                      void *V, int64_t ldu, double scale, cudaStream_t s,
-                     cudaError_t (*pass2)(const GroupArgs &, int, int64_t, cudaStream_t), cudaEvent_t ev_mid) {
+                     cudaError_t (*pass2)(const GroupArgs &, int, int64_t, cudaStream_t), cudaEvent_t ev_mid,
+                     uint8_t *Uscale = nullptr, int64_t ld_scale = 0, __nv_bfloat16 *hat = nullptr,
+                     int64_t hat_row0 = 0, int64_t hat_ld = 0) {
   GroupArgs a = {};
   a.d = d;
   a.nslab = (d + 1 + C - 1) / C;
@@ -541,6 +608,8 @@ cudaError_t run_plan(const SrhtPlan &pl, const void *X, int64_t ldx, const void 
   b.vec_out = vec_ok(U, ldu, sizeof(Tout), VO) ? 1 : 0;
   b.istride = n2; b.igstride = 1;
   b.out = U; b.ldout = ldu; b.out_y = V; b.pos = pos;
+  b.out_scale = Uscale; b.ld_scale = ld_scale;
+  b.hat_out = hat; b.hat_row0 = hat_row0; b.hat_ld = hat_ld;
   b.ostride = 1; b.ogstride = n1;  // pos is stored pass-2-major: entry (k2, k1) at k2 n1 + k1
   b.scale = scale;
   return pass2(b, pl.log1, n2, s);
@@ -562,7 +631,8 @@ SrhtPlan srht_plan(int64_t Np) {
 cudaError_t launch_srht(const SrhtPlan &pl, int prec, int xdtype, const void *X, int64_t ldx, const void *Y,
                         int64_t N, int d, const int32_t *Psd, const int32_t *pos, void *W, void *WY,
                         int64_t ldw, void *U, void *V, int64_t ldu, double scale, cudaStream_t s,
-                        cudaEvent_t ev_mid) {
+                        cudaEvent_t ev_mid, uint8_t *Uscale, int64_t ld_scale, __nv_bfloat16 *hat,
+                        int64_t hat_row0, int64_t hat_ld) {
   using bf16 = __nv_bfloat16;
   if (prec == SLSE_PREC_FP64) {
     auto p2 = &launch_pass_t<double, double, double, 1, 1, 2>;
@@ -573,6 +643,14 @@ cudaError_t launch_srht(const SrhtPlan &pl, int prec, int xdtype, const void *X,
   if (prec == SLSE_PREC_MIXED_BF16 && xdtype == SLSE_F32) {
     auto p2 = &launch_pass_t<bf16, float, bf16, 2, 2, 4>;
     return run_plan<float, float, bf16, 32, 2, 2, 4>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale, s, p2, ev_mid);
+  }
+  if (prec == SLSE_PREC_MIXED_FP8 && xdtype == SLSE_F32) {
+    // pass 1 as in the BF16 form; pass 2 writes E4M3 rows with 32-column block scales
+    // (single-pass sizes are handled by the caller through the BF16 form)
+    if (pl.single || !Uscale) return cudaErrorInvalidValue;
+    auto p2 = &launch_pass_t<bf16, float, mx8, 2, 2, 4>;
+    return run_plan<float, float, bf16, 32, 2, 2, 4>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale, s, p2,
+                                                     ev_mid, Uscale, ld_scale, hat, hat_row0, hat_ld);
   }
   return cudaErrorInvalidValue;
 }
