@@ -54,14 +54,20 @@ def parse():
     return ap.parse_args()
 
 
-def dist_init():
+def dist_init(backend: str = "nccl"):
+    """Replica setup from the torchrun environment (RANK, LOCAL_RANK, WORLD_SIZE, MASTER_*).
+    The replicas exchange only timing scalars; the library itself runs on one GPU per rank."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws <= 1:
         return 0, 1, 0
     import torch.distributed as dist
-    backend = "nccl"
     dist.init_process_group(backend=backend)
     return dist.get_rank(), ws, int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _scalar_device():
+    import torch.distributed as dist
+    return "cuda" if dist.get_backend() == "nccl" else "cpu"
 
 
 def barrier(ws):
@@ -75,7 +81,7 @@ def reduce_max(v, ws):
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([float(v)], dtype=torch.float64, device="cuda")
+    t = torch.tensor([float(v)], dtype=torch.float64, device=_scalar_device())
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -85,9 +91,16 @@ def reduce_sum(v, ws):
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([float(v)], dtype=torch.float64, device="cuda")
+    t = torch.tensor([float(v)], dtype=torch.float64, device=_scalar_device())
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def replica_summary(ms_local: float, units_local: float, ws: int) -> dict:
+    """Whole-job numbers from per-rank results: the slowest rank's time (after the barrier
+    that brackets the timed region) and the units all ranks processed."""
+    barrier(ws)
+    return {"ms": reduce_max(ms_local, ws), "units": reduce_sum(units_local, ws), "ranks": ws}
 
 
 # ----------------------------------------------------------------------------- clocks
