@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cs-steps", type=int, default=2, help="CountSketch-variant fits reported beside the SRHT line")
     ap.add_argument("--fp8-steps", type=int, default=2, help="fits with the FP8 form of the sketch")
+    ap.add_argument("--tuning-steps", type=int, default=2, help="fits with the SLSE-FRS-tuning schedule")
     ap.add_argument("--diff-steps", type=int, default=2, help="forward+backward passes of the differentiation block")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--sample-log2n", type=int, default=15)
@@ -422,6 +423,26 @@ def run_ours(args, rank, ws, local_rank):
                   "sketch_error_by_form": sketch_form_errors(slse, torch)}
         torch.cuda.empty_cache()
 
+    # the SLSE-FRS-tuning schedule (Sec. 5) on the same workload
+    tun = None
+    if args.tuning_steps > 0:
+        stn = slse.tuning_schedule(N, d, prec="mixed_bf16", T=100, tol=5e-9)
+        wtn = slse.alloc_workspace(slse.workspace_size(Xd, Yd, slse.OP_FIT, stn))
+        slse.fit(Xd, Yd, stn, seed=996, workspace=wtn, trace_cap=cap)
+        ttn = []
+        for k in range(args.tuning_steps):
+            r = slse.fit(Xd, Yd, stn, seed=k, workspace=wtn, trace_cap=cap)
+            if rank == 0:
+                a8, _ = first_crossing(r.beta_hist.cpu().numpy(), np.array(r.ms_hist), bh, TARGET)
+                ttn.append(a8)
+        del wtn
+        if rank == 0:
+            rt = r.report
+            tun = {"schedule": f"m={stn.m}, a_i=3", "time_to_1e-8_ms": statistics.mean(ttn) if all(v is not None for v in ttn) else None,
+                   "phases_ms": {k: rt[k] for k in ("ms_sketch", "ms_qr", "ms_stage1", "ms_stage2", "ms_total")},
+                   "iters": [rt["iters_stage1"], rt["iters_stage2"]]}
+        torch.cuda.empty_cache()
+
     # CountSketch variant (SLSE-FRS-CS, Sec. 5) on the same workload and schedule sizes
     cs = None
     if args.cs_steps > 0:
@@ -523,6 +544,7 @@ def run_ours(args, rank, ws, local_rank):
                      "reference": "oracle OLS, FP64 normal equations", "reference_seconds": t_ref},
         "fp64": fp64,
         "countsketch": cs,
+        "tuning": tun,
         "fp8": f8,
         "differentiation": diff,
         "phases_ms": {k: rep[k] for k in ("ms_draws", "ms_sketch", "ms_srht_pass1", "ms_srht_pass2", "ms_qr",

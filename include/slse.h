@@ -244,6 +244,13 @@ size_t slse_solve_normal_workspace(const slse_problem *prob, int32_t prec);
 slse_status slse_ols_vjp(const slse_problem *prob, const double *beta, const double *w, void *dX, int64_t lddx,
                          void *dY, slse_stream_t stream);
 
+/* The SLSE-FRS-tuning schedule (Sec. 5, sketch size tuning): a few small sketched problems
+ * and one large one with a_i = 3; the paper's sizes at d = 2^6 (2^10 .. 2^16 and 2^19) are
+ * 16d 2^j (j = 0..6) and 8192d, here dropped above N'/2 (rounded up to powers of two for
+ * SLSE_COUNTSKETCH).  Other fields as slse_default_schedule_for.  Returns K, or -1. */
+int32_t slse_tuning_schedule(int64_t N, int32_t d, int32_t kind, slse_schedule *out, int64_t *m_buf, int32_t *a_buf,
+                             int32_t cap);
+
 /* Theorem 4.3 lower bound on the inner iterations: log_3[((1+omega) r + 1)/omega] with
  * r = sqrt((m_i - d)/(m_prev - d)).  Host-only.  Returns NaN for m_prev <= d or omega <= 0. */
 double slse_ai_bound(double omega, int64_t m_prev, int64_t m_i, int32_t d);

@@ -73,6 +73,20 @@ def default_schedule(N: int, d: int, T: int = 100, tol: float = 0.0, a: int = 2,
     return Schedule(m=m, a=[a] * len(m), r=r, mu=mu, eta=eta, T=T, tol=tol, kind=kind)
 
 
+def tuning_schedule(N: int, d: int, T: int = 100, tol: float = 0.0, kind: str = "srht") -> Schedule:
+    """The SLSE-FRS-tuning schedule (Sec. 5, sketch size tuning): a few small sketched
+    problems and one large one, a_i = 3.  The paper's sizes for d = 2^6 are 2^10 .. 2^16
+    and 2^19, i.e. 16d 2^j (j = 0..6) and 8192d; sizes above N'/2 are dropped.  r, eta and mu
+    as in the default schedule."""
+    base = default_schedule(N, d, T=T, tol=tol, kind=kind)
+    Np = sk.padded_size(N)
+    m = [16 * d * 2 ** j for j in range(7)] + [8192 * d]
+    if kind == "countsketch":
+        m = [sk.padded_size(v) for v in m]
+    m = sorted(set(v for v in m if v <= Np // 2))
+    return Schedule(m=m, a=[3] * len(m), r=base.r, mu=base.mu, eta=base.eta, T=T, tol=tol, kind=kind)
+
+
 def ai_bound(omega: float, m_prev: float, m_i: float, d: float) -> float:
     """Theorem 4.3 lower bound on a_i (i >= 2)."""
     rr = math.sqrt((m_i - d) / (m_prev - d))

@@ -89,6 +89,9 @@ _lib.slse_solve_normal_workspace.restype = _sz
 _lib.slse_solve_normal_workspace.argtypes = [ctypes.POINTER(CProblem), _i32]
 _lib.slse_ols_vjp.restype = _i32
 _lib.slse_ols_vjp.argtypes = [ctypes.POINTER(CProblem), _vp, _vp, _vp, _i64, _vp, _vp]
+_lib.slse_tuning_schedule.restype = _i32
+_lib.slse_tuning_schedule.argtypes = [_i64, _i32, _i32, ctypes.POINTER(CSchedule), ctypes.POINTER(ctypes.c_int64),
+                                      ctypes.POINTER(ctypes.c_int32), _i32]
 _lib.slse_ai_bound.restype = ctypes.c_double
 _lib.slse_ai_bound.argtypes = [ctypes.c_double, _i64, _i64, _i32]
 _lib.slse_status_string.restype = ctypes.c_char_p
@@ -97,7 +100,8 @@ _lib.slse_version.restype = _i32
 
 EXPORTED = ["slse_workspace_size", "slse_fit", "slse_sketch", "slse_grad", "slse_grad_noalloc", "slse_draws", "slse_qr",
             "slse_default_schedule", "slse_default_schedule_for", "slse_ai_bound", "slse_status_string",
-            "slse_version", "slse_solve_normal", "slse_solve_normal_workspace", "slse_ols_vjp"]
+            "slse_version", "slse_solve_normal", "slse_solve_normal_workspace", "slse_ols_vjp",
+            "slse_tuning_schedule"]
 
 
 class SlseError(RuntimeError):
@@ -153,6 +157,19 @@ def default_schedule(N: int, d: int, prec: str = "fp64", T: int = 100, tol: floa
     mb = (ctypes.c_int64 * 64)()
     ab = (ctypes.c_int32 * 64)()
     K = _lib.slse_default_schedule_for(N, d, KIND[kind], ctypes.byref(c), mb, ab, 64)
+    if K < 0 or K > 64:
+        raise ValueError("invalid problem size")
+    return Schedule(m=list(mb[:K]), a=list(ab[:K]), r=c.r, mu=c.mu, eta=c.eta, T=T, tol=tol, prec=prec,
+                    momentum_reset=bool(c.momentum_reset), kind=c.kind)
+
+
+def tuning_schedule(N: int, d: int, prec: str = "fp64", T: int = 100, tol: float = 0.0,
+                    kind: str = "srht") -> Schedule:
+    """The SLSE-FRS-tuning schedule (Sec. 5, sketch size tuning), from the library."""
+    c = CSchedule()
+    mb = (ctypes.c_int64 * 64)()
+    ab = (ctypes.c_int32 * 64)()
+    K = _lib.slse_tuning_schedule(N, d, KIND[kind], ctypes.byref(c), mb, ab, 64)
     if K < 0 or K > 64:
         raise ValueError("invalid problem size")
     return Schedule(m=list(mb[:K]), a=list(ab[:K]), r=c.r, mu=c.mu, eta=c.eta, T=T, tol=tol, prec=prec,

@@ -828,6 +828,29 @@ int32_t slse_default_schedule_for(int64_t N, int32_t d, int32_t kind, slse_sched
   return K;
 }
 
+int32_t slse_tuning_schedule(int64_t N, int32_t d, int32_t kind, slse_schedule *out, int64_t *m_buf, int32_t *a_buf,
+                             int32_t cap) {
+  if (slse_default_schedule_for(N, d, kind, out, nullptr, nullptr, 0) < 0) return -1;
+  const int64_t Np = padded(N);
+  std::vector<int64_t> m;
+  for (int j = 0; j <= 6; ++j) m.push_back(16 * (int64_t)d << j);
+  m.push_back(8192 * (int64_t)d);
+  std::vector<int64_t> keep;
+  for (int64_t v : m) {
+    if (kind == SLSE_COUNTSKETCH) v = padded(v);
+    if (v <= Np / 2 && (keep.empty() || v > keep.back())) keep.push_back(v);
+  }
+  const int32_t K = (int32_t)keep.size();
+  for (int32_t i = 0; i < K && i < cap && m_buf && a_buf; ++i) {
+    m_buf[i] = keep[i];
+    a_buf[i] = 3;
+  }
+  out->K = K < cap ? K : cap;
+  out->m = m_buf;
+  out->a = a_buf;
+  return K;
+}
+
 double slse_ai_bound(double omega, int64_t m_prev, int64_t m_i, int32_t d) {
   if (!(omega > 0.0) || m_prev <= d || m_i <= d) return NAN;
   const double r = std::sqrt((double)(m_i - d) / (double)(m_prev - d));

@@ -114,3 +114,15 @@ def test_countsketch_host_side(lib):
     sch = slse.Schedule(m=[16], a=[2], r=24, mu=0.7, eta=0.1, kind=slse.GAUSSIAN).to_c()         # not built
     assert slse._lib.slse_fit(ctypes.byref(good), ctypes.byref(sch), 0, beta, None, None, None, 0, None) == slse.EINVAL
     assert slse._lib.slse_sketch(ctypes.byref(good), slse.COUNTSKETCH, 0, 0, 48, 1, 4, 1, None, 0, None) == slse.EINVAL
+
+
+def test_tuning_schedule_matches_oracle(lib):
+    import paper_2509_06856_gb300 as slse
+    from oracle import slse as osl
+    # the paper's tuning sizes at d = 2^6, N = 2^22: 2^10 .. 2^16 and 2^19, a_i = 3
+    a = slse.tuning_schedule(1 << 22, 64)
+    assert a.m == [1 << k for k in range(10, 17)] + [1 << 19] and a.a == [3] * 8
+    for N, d, kind in [(1 << 22, 64, "srht"), (1 << 22, 512, "srht"), (20000, 50, "srht"), (20000, 50, "countsketch")]:
+        x = slse.tuning_schedule(N, d, kind=kind)
+        y = osl.tuning_schedule(N, d, kind=kind)
+        assert x.m == y.m and x.a == y.a and x.r == y.r
