@@ -266,103 +266,127 @@ __global__ void k_gram_reduce(const double *part, int ksplit, int d, double scal
 }
 
 // Diagonal block [k0, k0+nb) of the right-looking blocked Cholesky (lower, in place), and
-// the inverse of that block for the panel solve.  One warp: lane i keeps row i of the block
-// in registers; pivots use rsqrt, column entries travel by shuffle.  FP64 latency is long on
-// this part, so the dependent chain per column is kept to a few operations.  Rows past d
-// are identity rows.
-__global__ void __launch_bounds__(32) k_potrf(double *A, int d, int k0, double *Linv, DevState *st) {
+// the inverse of that block for the panel solve.  Four warps (one per SM sub-partition:
+// a warp's FP64 instruction occupies its sub-partition's FP64 pipe for many cycles on this
+// part, so the work is spread over all four).  Lane i holds row i; warp w holds columns
+// l = w + 4t (t < 8) in registers.  Step j: the owner of column j takes the pivot (rsqrt),
+// scales the column and publishes it in shared memory; after one barrier every warp
+// updates its columns l > j.  The inverse is formed by a column sweep with the same split.
+// Rows past d are identity rows; a non-positive pivot raises ST_NUMERIC.
+__global__ void __launch_bounds__(128) k_potrf(double *A, int d, int k0, double *Linv, DevState *st) {
+  __shared__ double s_col[kTile][kTile + 1];  // s_col[j][i] = L[i][j]
   __shared__ double s_rinv[kTile];
-  const int lane = threadIdx.x;
+  __shared__ int s_bad;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int nb = min(kTile, d - k0);
-  double a[kTile];
+  constexpr int TC = kTile / 4;  // columns per warp
+  double a[TC];
 #pragma unroll
-  for (int l = 0; l < kTile; ++l)
-    a[l] = (lane < nb && l <= lane && l < nb) ? A[(size_t)(k0 + lane) * d + k0 + l] : (l == lane ? 1.0 : 0.0);
-#pragma unroll
+  for (int t = 0; t < TC; ++t) {
+    const int l = w + 4 * t;
+    a[t] = (lane < nb && l < nb && l <= lane) ? A[(size_t)(k0 + lane) * d + k0 + l] : (l == lane ? 1.0 : 0.0);
+  }
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+#pragma unroll 1
   for (int j = 0; j < kTile; ++j) {
-    const double piv = __shfl_sync(0xffffffffu, a[j], j);
-    if (!(piv > 0.0)) {
-      if (lane == 0) atomicOr(&st->status, ST_NUMERIC);
+    if (w == (j & 3)) {
+      const int tj = j >> 2;
+      double aj = 0.0;
+#pragma unroll
+      for (int t = 0; t < TC; ++t)
+        if (t == tj) aj = a[t];
+      const double piv = __shfl_sync(0xffffffffu, aj, j);
+      const bool ok = piv > 0.0;
+      const double rs = ok ? rsqrt(piv) : 0.0;
+      const double lj = lane == j ? piv * rs : (lane > j ? aj * rs : 0.0);
+#pragma unroll
+      for (int t = 0; t < TC; ++t)
+        if (t == tj) a[t] = lj;
+      s_col[j][lane] = lj;
+      if (lane == 0) {
+        s_rinv[j] = rs;
+        if (!ok) s_bad = 1;
+      }
+    }
+    __syncthreads();
+    if (s_bad) {
+      if (threadIdx.x == 0) atomicOr(&st->status, ST_NUMERIC);
       return;
     }
-    const double rs = rsqrt(piv);
-    if (lane == 0) s_rinv[j] = rs;  // 1 / L[j][j]
-    if (lane == j) a[j] = piv * rs;
-    else if (lane > j) a[j] *= rs;
+    const double lij = s_col[j][lane];
 #pragma unroll
-    for (int l = j + 1; l < kTile; ++l) {
-      const double llj = __shfl_sync(0xffffffffu, a[j], l);  // L[l][j]
-      if (lane >= l) a[l] = fma(-a[j], llj, a[l]);
+    for (int t = 0; t < TC; ++t) {
+      const int l = w + 4 * t;
+      if (l > j) a[t] = fma(-lij, s_col[j][l], a[t]);
     }
   }
-  __syncwarp();
-  // column `lane` of L^{-1} by column sweep: x_i = x_i / L[i][i]; x_l -= L[l][i] x_i (l > i)
-  double x[kTile];
+  // L back to A (lower triangle of the block)
+  if (lane < nb) {
 #pragma unroll
-  for (int l = 0; l < kTile; ++l) x[l] = (l == lane) ? 1.0 : 0.0;
+    for (int t = 0; t < TC; ++t) {
+      const int l = w + 4 * t;
+      if (l < nb) A[(size_t)(k0 + lane) * d + k0 + l] = l <= lane ? a[t] : 0.0;
+    }
+  }
+  // L^{-1}: column c = w + 4t of the inverse in x[t] (lane = row); sweep i = 0..31:
+  // x_i <- x_i / L_ii, then x_r <- x_r - L_ri x_i for r > i
+  double x[TC];
 #pragma unroll
+  for (int t = 0; t < TC; ++t) x[t] = (lane == w + 4 * t) ? 1.0 : 0.0;
+#pragma unroll 1
   for (int i = 0; i < kTile; ++i) {
-    const double xi = x[i] * s_rinv[i];
-    x[i] = xi;
+    const double rinv = s_rinv[i], lri = s_col[i][lane];
 #pragma unroll
-    for (int l = i + 1; l < kTile; ++l) {
-      const double lli = __shfl_sync(0xffffffffu, a[i], l);  // L[l][i]
-      x[l] = fma(-lli, xi, x[l]);
+    for (int t = 0; t < TC; ++t) {
+      const double xi = __shfl_sync(0xffffffffu, x[t], i) * rinv;
+      x[t] = lane == i ? xi : (lane > i ? fma(-lri, xi, x[t]) : x[t]);
     }
   }
   if (lane < nb) {
 #pragma unroll
-    for (int l = 0; l < kTile; ++l)
-      if (l < nb) A[(size_t)(k0 + lane) * d + k0 + l] = l <= lane ? a[l] : 0.0;
+    for (int t = 0; t < TC; ++t) {
+      const int c = w + 4 * t;
+      if (c < nb) Linv[lane * kTile + c] = lane >= c ? x[t] : 0.0;
+    }
   }
-#pragma unroll
-  for (int l = 0; l < kTile; ++l)
-    if (l < nb && lane < nb) Linv[l * kTile + lane] = l >= lane ? x[l] : 0.0;
 }
 
-// Panel below the diagonal block: A[i0:i0+32, k0:k0+nb] <- A * Linv^T.
+// Panel below the diagonal block: A[i0:i0+8, k0:k0+nb] <- A * Linv^T, 8 rows per CTA (one
+// output per thread) so that the FP64 work spreads over many SMs.
 __global__ void __launch_bounds__(256) k_trsm(double *A, int d, int k0, const double *Linv) {
-  __shared__ double P[kTile][kTile + 1], T[kTile][kTile + 1];
+  __shared__ double P[8][kTile + 1], T[kTile][kTile + 1];
   const int nb = min(kTile, d - k0);
-  const int i0 = k0 + kTile * (1 + blockIdx.x);
+  const int i0 = k0 + kTile + 8 * blockIdx.x;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int rr = ty; rr < kTile; rr += 8) {
-    P[rr][tx] = (i0 + rr < d && tx < nb) ? A[(size_t)(i0 + rr) * d + k0 + tx] : 0.0;
-    T[rr][tx] = (rr < nb && tx < nb) ? Linv[rr * kTile + tx] : 0.0;
-  }
+  P[ty][tx] = (i0 + ty < d && tx < nb) ? A[(size_t)(i0 + ty) * d + k0 + tx] : 0.0;
+  for (int rr = ty; rr < kTile; rr += 8) T[rr][tx] = (rr < nb && tx < nb) ? Linv[rr * kTile + tx] : 0.0;
   __syncthreads();
+  double s = 0.0;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int rr = ty + 8 * q;
-    double s = 0.0;
-    for (int l = 0; l < kTile; ++l) s = fma(P[rr][l], T[tx][l], s);  // (P Linv^T)[rr][tx]
-    if (i0 + rr < d && tx < nb) A[(size_t)(i0 + rr) * d + k0 + tx] = s;
-  }
+  for (int l = 0; l < kTile; ++l) s = fma(P[ty][l], T[tx][l], s);  // (P Linv^T)[ty][tx]
+  if (i0 + ty < d && tx < nb) A[(size_t)(i0 + ty) * d + k0 + tx] = s;
 }
 
-// Trailing update of the lower triangle: A[bi, bj] -= L[bi, k] L[bj, k]^T for bj <= bi.
+// Trailing update of the lower triangle: A[rows, cols] -= L[rows, k] L[cols, k]^T for the
+// 8-row slice blockIdx.y of the trailing part against the 32-column block blockIdx.x
+// (lower triangle only), one output per thread.
 __global__ void __launch_bounds__(256) k_syrk(double *A, int d, int k0) {
-  __shared__ double Li[kTile][kTile + 1], Lj[kTile][kTile + 1];
+  __shared__ double Li[8][kTile + 1], Lj[kTile][kTile + 1];
   const int nb = min(kTile, d - k0);
   const int base = k0 + kTile;
-  const int bi = blockIdx.y, bj = blockIdx.x;
-  if (bj > bi) return;
-  const int i0 = base + kTile * bi, j0 = base + kTile * bj;
+  const int i0 = base + 8 * blockIdx.y, j0 = base + kTile * blockIdx.x;
+  if (j0 > i0 + 7) return;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int rr = ty; rr < kTile; rr += 8) {
-    Li[rr][tx] = (i0 + rr < d && tx < nb) ? A[(size_t)(i0 + rr) * d + k0 + tx] : 0.0;
-    Lj[rr][tx] = (j0 + rr < d && tx < nb) ? A[(size_t)(j0 + rr) * d + k0 + tx] : 0.0;
-  }
+  Li[ty][tx] = (i0 + ty < d && tx < nb) ? A[(size_t)(i0 + ty) * d + k0 + tx] : 0.0;
+  for (int rr = ty; rr < kTile; rr += 8) Lj[rr][tx] = (j0 + rr < d && tx < nb) ? A[(size_t)(j0 + rr) * d + k0 + tx] : 0.0;
   __syncthreads();
+  const int gi = i0 + ty, gj = j0 + tx;
+  if (gi < d && gj < d && gj <= gi) {
+    double s = 0.0;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int rr = ty + 8 * q;
-    const int gi = i0 + rr, gj = j0 + tx;
-    if (gi < d && gj < d && gj <= gi) {
-      double s = 0.0;
-      for (int l = 0; l < kTile; ++l) s = fma(Li[rr][l], Lj[tx][l], s);
-      A[(size_t)gi * d + gj] -= s;
-    }
+    for (int l = 0; l < kTile; ++l) s = fma(Li[ty][l], Lj[tx][l], s);
+    A[(size_t)gi * d + gj] -= s;
   }
 }
 
@@ -486,11 +510,13 @@ cudaError_t launch_gram_chol(const void *U, int64_t ldu, int64_t row0, int64_t r
   k_gram_reduce<<<(unsigned)((dd + 255) / 256), 256, 0, s>>>(part, ksplit, d, scale2, G);
   for (int kb = 0; kb < nt; ++kb) {
     const int k0 = kb * kTile;
-    k_potrf<<<1, 32, 0, s>>>(G, d, k0, Linv, st);
+    k_potrf<<<1, 128, 0, s>>>(G, d, k0, Linv, st);
     const int below = nt - kb - 1;
     if (below > 0) {
-      k_trsm<<<below, 256, 0, s>>>(G, d, k0, Linv);
-      k_syrk<<<dim3(below, below), 256, 0, s>>>(G, d, k0);
+      const int rows = d - k0 - kTile;  // rows below the diagonal block
+      const int slices = (rows + 7) / 8;
+      k_trsm<<<slices, 256, 0, s>>>(G, d, k0, Linv);
+      k_syrk<<<dim3(below, slices), 256, 0, s>>>(G, d, k0);
     }
   }
   k_chol_to_r<<<(unsigned)((dd + 255) / 256), 256, 0, s>>>(G, d, R, Rt);
