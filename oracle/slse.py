@@ -16,7 +16,9 @@
   then full-data M-IHS steps (2nd stage).  ``kind="countsketch"`` runs the same
   iteration on the CountSketch family of ``oracle.countsketch`` (the SLSE-FRS-CS
   experiment of Sec. 5): S_i X is the m_i-bucket sketch (no scale factor, since
-  E[S^T S] = I), S-hat X the independent r-bucket sketch.
+  E[S^T S] = I), S-hat X the independent r-bucket sketch.  ``kind="gaussian"`` keeps
+  the SRHT subproblems and takes S-hat X from the r x N Gaussian sketch of
+  ``oracle.gaussian`` (Sec. 2) instead of the sampled SRHT rows.
 
 Readings taken where the paper is silent (listed in the design doc):
 * beta_0 = 0 (Thm 4.2 allows any beta_0).
@@ -34,6 +36,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import countsketch as cs
+from . import gaussian as gs
 from . import sketch as sk
 from .linalg import householder_r, solve_lower, solve_upper
 
@@ -48,7 +51,7 @@ class Schedule:
     T: int = 100
     tol: float = 0.0
     momentum_reset: bool = False
-    kind: str = "srht"   # or "countsketch"
+    kind: str = "srht"   # or "countsketch", or "gaussian" (SRHT subproblems, Gaussian S-hat)
 
     @property
     def K(self):
@@ -156,9 +159,12 @@ def slse_fit(X, Y, sched: Schedule, seed: int, trace: bool = False,
         else:
             ZX, ZY = sketch_override
         mK = sched.m[-1] if sched.K else 0
-        h0, h1 = sk.hessian_rows(Np, mK, sched.r)
-        SX_hat = math.sqrt(Np / sched.r) * ZX[sigma[h0:h1]]
-        R = householder_r(SX_hat)
+        if sched.kind == "gaussian":
+            R = householder_r(gs.gaussian_sketch(X, Y, sched.r, seed)[0])
+        else:
+            h0, h1 = sk.hessian_rows(Np, mK, sched.r)
+            SX_hat = math.sqrt(Np / sched.r) * ZX[sigma[h0:h1]]
+            R = householder_r(SX_hat)
 
         def subproblem(m):
             # S_i X = sqrt(N'/m) U with U the first m sampled rows; the gradient of the

@@ -6,7 +6,9 @@ import math
 import numpy as np
 import pytest
 
+from oracle import gaussian as gs
 from oracle import linalg, sketch as sk, slse
+import tests.test_oracle_gaussian as tg
 import tests.test_oracle_random as tr
 import tests.test_oracle_sketch as ts
 import tests.test_oracle_solve as tv
@@ -132,3 +134,33 @@ def test_countsketch_fold_wrong_offset_is_caught(monkeypatch):
         return SX.reshape((m, M // m) + SX.shape[1:]).sum(axis=1)   # adds neighbours, not b + q m
     monkeypatch.setattr(cs, "fold", bad)
     _fails(tc.test_folding_identity, 8)
+
+
+def test_gaussian_log_base_is_caught(monkeypatch):
+    def bad(w):
+        w = np.asarray(w, np.uint64)
+        u1 = ((w & np.uint64(0xFFFF)).astype(np.float64) + 0.5) / 65536.0
+        u2 = ((w >> np.uint64(16)).astype(np.float64) + 0.5) / 65536.0
+        rad = np.sqrt(-2.0 * np.log10(u1))          # log10 in place of ln
+        return rad * np.cos(2 * math.pi * u2), rad * np.sin(2 * math.pi * u2)
+    monkeypatch.setattr(gs, "normals_from_words", bad)
+    _fails(tg.test_box_muller_closed_form_values)
+    _fails(tg.test_normal_law_moments_and_ks)
+
+
+def test_gaussian_swapped_cosine_and_sine_is_caught(monkeypatch):
+    good = gs.normals_from_words
+    monkeypatch.setattr(gs, "normals_from_words", lambda w: good(w)[::-1])
+    _fails(tg.test_box_muller_closed_form_values)
+
+
+def test_gaussian_row_counter_ignored_is_caught(monkeypatch):
+    good = gs.gaussian_rows
+    monkeypatch.setattr(gs, "gaussian_rows", lambda seed, i0, i1, N: np.repeat(good(seed, 0, 1, N), i1 - i0, 0))
+    _fails(tg.test_rows_and_columns_are_independent)
+    _fails(tg.test_prediction_efficiency_exact_gaussian_value)
+
+
+def test_gaussian_missing_scale_is_caught(monkeypatch):
+    monkeypatch.setattr(gs, "gaussian_matrix_dense", lambda N, m, seed: gs.gaussian_rows(seed, 0, m, N))
+    _fails(tg.test_expectation_of_sts_is_identity)
