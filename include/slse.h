@@ -68,7 +68,14 @@ typedef enum { SLSE_F64 = 0, SLSE_F32 = 1, SLSE_BF16 = 2 } slse_dtype;
  * SLSE_COUNTSKETCH_HAT: the independent CountSketch used for the Hessian sketch with the
  *   CountSketch family: m buckets (any m >= 1), bucket floor(w0 m / 2^32) and sign bit 0
  *   of w1 at counter (k, 4).
- * SLSE_GAUSSIAN: reserved (not built). */
+ * SLSE_GAUSSIAN: the Gaussian sketch of Sec. 2, S = G / sqrt(m) with i.i.d. standard normal
+ *   G[i, k]: Philox4x32-10 at counter (q mod 2^32, q div 2^32, 5, i), q = k div 8, gives the
+ *   entries G[i, 8q .. 8q+7]; output word j yields G[i, 8q+2j] = sqrt(-2 ln u1) cos(2 pi u2) and
+ *   G[i, 8q+2j+1] = sqrt(-2 ln u1) sin(2 pi u2) (Box-Muller) with u1 = (w mod 2^16 + 1/2) 2^-16,
+ *   u2 = (w div 2^16 + 1/2) 2^-16.  Used for the Hessian sketch only (a schedule of this kind
+ *   keeps the SRHT subproblems).  MIXED_BF16: entries drawn in FP32 with the hardware log2,
+ *   sine, cosine and reciprocal square root (absolute error below 1e-4, then BF16 rounding),
+ *   products on the tensor cores with FP32 accumulation; FP64: entries and products in FP64. */
 typedef enum { SLSE_SRHT = 0, SLSE_COUNTSKETCH = 1, SLSE_GAUSSIAN = 2, SLSE_COUNTSKETCH_HAT = 3 } slse_sketch_kind;
 
 /* Arithmetic of the path.
@@ -104,7 +111,9 @@ typedef struct {
   double tol;           /* 2nd stage stops when ||b+ - b|| <= tol (1-rho)/rho ||b+||, rho = sqrt(d/r); <= 0: run to T */
   int32_t kind;         /* SLSE_SRHT, or SLSE_COUNTSKETCH: S_i X is the 2^l-bucket CountSketch
                            (all m_i powers of two, unscaled) and S-hat X the independent
-                           r-bucket SLSE_COUNTSKETCH_HAT sketch */
+                           r-bucket SLSE_COUNTSKETCH_HAT sketch, or SLSE_GAUSSIAN: SRHT
+                           subproblems and S-hat X = G X / sqrt(r) from the r x N Gaussian
+                           sketch (prec FP64 or MIXED_BF16) */
   int32_t prec;         /* slse_precision */
   int32_t momentum_reset; /* 0: momentum carries across subproblems (Algorithm 2's global t);
                              1: beta_{-1} = beta_0 at each subproblem and at the 2nd stage (proof of Thm 4.1) */
@@ -153,7 +162,10 @@ slse_status slse_fit(const slse_problem *prob, const slse_schedule *sched, uint6
 /* One sketch of size m.  kind SLSE_SRHT (Sec. 3): SX = sqrt(N'/m) * rows sigma[0..m) of
  * H D P X_pad / sqrt(N'), SY likewise.  kind SLSE_COUNTSKETCH (Sec. 2; m a power of two,
  * else SLSE_EINVAL): row b of SX is the signed sum of the rows of X in bucket b.  kind
- * SLSE_COUNTSKETCH_HAT: the same with the Hessian-sketch hash into m buckets.  prec FP64 ->
+ * SLSE_COUNTSKETCH_HAT: the same with the Hessian-sketch hash into m buckets.  kind SLSE_GAUSSIAN
+ * (prec FP64, or MIXED_BF16 with X F32): SX = G X / sqrt(m), SY = G Y / sqrt(m), G m x N as
+ * described at slse_sketch_kind (any 1 <= m < 2^31); SY may be NULL (not formed); a bounded
+ * device wait that gave up leaves NaN in SX and SY.  prec FP64 ->
  * SX, SY are double; MIXED_BF16 -> bf16 (CountSketch sums accumulated in FP32, in row
  * order within a bucket, so the result is deterministic).  SX: device m x ldsx (ldsx >= d),
  * SY: device m.  prec MIXED_FP8 (kind SRHT): SX holds m x ldsx E4M3 bytes (ldsx a multiple of

@@ -28,7 +28,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ENUMERIC, ETIMEOUT = range(7)
 F64, F32, BF16 = 0, 1, 2
 SRHT, COUNTSKETCH, GAUSSIAN, COUNTSKETCH_HAT = 0, 1, 2, 3
-KIND = {"srht": SRHT, "countsketch": COUNTSKETCH, "countsketch_hat": COUNTSKETCH_HAT}
+KIND = {"srht": SRHT, "countsketch": COUNTSKETCH, "countsketch_hat": COUNTSKETCH_HAT, "gaussian": GAUSSIAN}
 PREC = {"fp64": 0, "mixed_bf16": 1, "mixed_fp8": 2}
 OP_FIT, OP_SKETCH, OP_GRAD, OP_DRAWS, OP_QR = range(5)
 
@@ -304,10 +304,12 @@ def ols_vjp(X, Y, beta, w, stream=None):
     return dX, dY
 
 
-def sketch(X, Y, m: int, seed: int = 0, prec: str = "fp64", workspace=None, stream=None, kind: str = "srht"):
-    """slse_sketch: (S X, S Y) for one sketch of size m (kind "srht", "countsketch" or
-    "countsketch_hat").  FP64 -> float64, mixed_bf16 -> bfloat16; mixed_fp8 -> (E4M3 codes
-    (uint8, m x d), block exponents + 127 (uint8, m x ceil(d/32)), S Y in bfloat16)."""
+def sketch(X, Y, m: int, seed: int = 0, prec: str = "fp64", workspace=None, stream=None, kind: str = "srht",
+           want_y: bool = True):
+    """slse_sketch: (S X, S Y) for one sketch of size m (kind "srht", "countsketch",
+    "countsketch_hat" or "gaussian").  FP64 -> float64, mixed_bf16 -> bfloat16; mixed_fp8 ->
+    (E4M3 codes (uint8, m x d), block exponents + 127 (uint8, m x ceil(d/32)), S Y in bfloat16).
+    want_y=False (kind "gaussian" only) skips S Y and returns None for it."""
     torch = _torch()
     p = problem(X, Y)
     ws_ptr, ws_len = (workspace.data_ptr(), workspace.numel()) if workspace is not None else (None, 0)
@@ -323,9 +325,9 @@ def sketch(X, Y, m: int, seed: int = 0, prec: str = "fp64", workspace=None, stre
         return buf[:m * ldq].view(m, ldq)[:, :p.d], buf[m * ldq:].view(m, nsb), SY
     dt = torch.float64 if prec == "fp64" else torch.bfloat16
     SX = torch.empty((m, p.d), dtype=dt, device=X.device)
-    SY = torch.empty(m, dtype=dt, device=X.device)
-    st = _lib.slse_sketch(ctypes.byref(p), KIND[kind], PREC[prec], seed, m, SX.data_ptr(), p.d, SY.data_ptr(), ws_ptr,
-                          ws_len, _stream(stream))
+    SY = torch.empty(m, dtype=dt, device=X.device) if want_y else None
+    st = _lib.slse_sketch(ctypes.byref(p), KIND[kind], PREC[prec], seed, m, SX.data_ptr(), p.d,
+                          SY.data_ptr() if want_y else None, ws_ptr, ws_len, _stream(stream))
     _check(st, "slse_sketch")
     return SX, SY
 

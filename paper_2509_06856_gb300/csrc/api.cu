@@ -79,7 +79,7 @@ bool make_sched(const slse_problem *p, const slse_schedule *s, Sched &o) {
     return true;
   }
   if (s->K < 0 || (s->K > 0 && (!s->m || !s->a))) return false;
-  if (s->kind != SLSE_SRHT && s->kind != SLSE_COUNTSKETCH) return false;
+  if (s->kind != SLSE_SRHT && s->kind != SLSE_COUNTSKETCH && s->kind != SLSE_GAUSSIAN) return false;
   if (s->prec != SLSE_PREC_FP64 && s->prec != SLSE_PREC_MIXED_BF16 && s->prec != SLSE_PREC_MIXED_FP8) return false;
   if (s->prec != SLSE_PREC_FP64 && p->dtype != SLSE_F32) return false;
   if (s->prec == SLSE_PREC_MIXED_FP8 && s->kind != SLSE_SRHT) return false;  // FP8 form: SRHT only
@@ -116,6 +116,8 @@ struct FitLayout {
   SrhtPlan sp;
   bool cs;                  // CountSketch family instead of the SRHT
   CsPlan csp;
+  bool gauss;               // SRHT subproblems, Gaussian Hessian sketch
+  GaussPlan gp;
   std::vector<int64_t> lvl_off;  // CountSketch: first row in U of the sketch of each schedule size
   int nblk;
   bool host_in;
@@ -144,7 +146,8 @@ FitLayout fit_layout(const slse_problem *p, const Sched &s, int nsm) {
     L.h0 = off;
     L.n_samp = off + s.r;
     L.csp = cs_plan(p->N, d, s.prec, s.m.empty() ? 0 : s.m.front(), mK, s.r);
-  } else if (mK + s.r <= L.Np) { L.h0 = mK; L.n_samp = mK + s.r; }
+  } else if (s.kind == SLSE_GAUSSIAN) { L.h0 = mK; L.n_samp = mK; }  // S-hat is not sampled
+  else if (mK + s.r <= L.Np) { L.h0 = mK; L.n_samp = mK + s.r; }
   else { L.h0 = 0; L.n_samp = mK > s.r ? mK : s.r; }
   const bool fp8 = s.prec == SLSE_PREC_MIXED_FP8;
   L.ld16 = (d + 7) & ~int64_t(7);
@@ -164,12 +167,18 @@ FitLayout fit_layout(const slse_problem *p, const Sched &s, int nsm) {
   if (wbytes + align256(wybytes) + 256 > big) big = align256(wbytes) + align256(wybytes);
   // FP8 form at single-pass sizes: the BF16 rows are formed in this region, then quantised
   if (fp8 && L.sp.single && (size_t)L.n_samp * L.ld16 * 2 > big) big = (size_t)L.n_samp * L.ld16 * 2;
+  // Gaussian Hessian sketch: its packed X and partial sums reuse this region after the SRHT
+  L.gauss = s.kind == SLSE_GAUSSIAN;
+  if (L.gauss) {
+    L.gp = gauss_plan(p->N, d, s.prec, s.r, false, nsm);
+    if (L.gp.total > big) big = L.gp.total;
+  }
   L.o_big = w.take(big);
   L.o_wy = L.o_big + align256(wbytes);
   L.o_u = w.take((size_t)L.n_samp * L.ldu * eu);
   L.o_v = w.take((size_t)L.n_samp * ev);
   L.o_us = w.take(fp8 ? (size_t)L.n_samp * L.nsb : 0);
-  L.o_hat16 = w.take(fp8 ? (size_t)s.r * L.ld16 * 2 : 0);
+  L.o_hat16 = w.take((fp8 || (L.gauss && s.prec != SLSE_PREC_FP64)) ? (size_t)s.r * L.ld16 * 2 : 0);
   L.o_A = w.take((size_t)s.r * d * 8);
   L.o_R = w.take((size_t)d * d * 8);
   L.o_Hinv = w.take((size_t)d * d * 8);
@@ -458,6 +467,16 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
                      L.h0 > 0 ? L.h0 : INT64_MAX, L.ld16));
       kernels += L.sp.single ? 1 : 2;
     }
+    if (L.gauss) {
+      // S-hat X = G X / sqrt(r) (Gaussian sketch, Sec. 2) in place of sampled SRHT rows:
+      // BF16 rows for the Gram-Cholesky route, FP64 rows straight into the QR input
+      void *hout = mixed ? static_cast<void *>(base + L.o_hat16) : static_cast<void *>(A);
+      const int64_t ldo = mixed ? L.ld16 : d;
+      if (mixed) CK(cudaMemsetAsync(hout, 0, (size_t)s.r * L.ld16 * 2, st));
+      CK(launch_gaussian(L.gp, p->dtype, p->X, p->ldx, p->Y, seed, hout, ldo, nullptr, 1.0 / std::sqrt((double)s.r),
+                         &dst->status, big, st));
+      kernels += mixed ? 3 * L.gp.groups : 2;
+    }
   }
   CK(cudaEventRecord(e_sketch, st));
   // sketch scales: SRHT S_i X = sqrt(N'/m_i) U[rows], S-hat X = sqrt(N'/r) U[h0 ..]; CountSketch: 1
@@ -469,6 +488,11 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
   // the Hessian-sketch rows as BF16 (the FP8 form is widened exactly)
   const void *Uh = U;
   int64_t ldh = L.ldu, h0 = L.h0;
+  double hat_scale2 = sq_scale(s.r);
+  if (L.gauss) {
+    hat_scale2 = 1.0;  // rows already scaled by 1/sqrt(r)
+    if (mixed) { Uh = base + L.o_hat16; ldh = L.ld16; h0 = 0; }
+  }
   if (fp8) {
     __nv_bfloat16 *h16 = reinterpret_cast<__nv_bfloat16 *>(base + L.o_hat16);
     if (L.h0 == 0 && !L.sp.single) {  // S-hat shares the prefix rows (m_K + r > N'): widen them
@@ -478,7 +502,7 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     Uh = h16; ldh = L.ld16; h0 = 0;
   }
   if (mixed) {
-    CK(launch_gram_chol(Uh, ldh, h0, s.r, d, sq_scale(s.r), R, Hinv, base + L.o_chol, dst, st));
+    CK(launch_gram_chol(Uh, ldh, h0, s.r, d, hat_scale2, R, Hinv, base + L.o_chol, dst, st));
     const int nt = (d + 31) / 32;
     kernels += 2 + 3 * nt + 2;
     DevState *mb = t_mailbox.get();
@@ -493,10 +517,13 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     }
   }
   if (use_qr) {
-    CK(launch_gather_hessian_rows(fp8 ? SLSE_PREC_MIXED_BF16 : s.prec, Uh, ldh, h0, s.r, d, std::sqrt(sq_scale(s.r)),
-                                  A, st));
+    if (!(L.gauss && !mixed)) {  // the FP64 Gaussian rows are already in A
+      CK(launch_gather_hessian_rows((fp8 || L.gauss) ? SLSE_PREC_MIXED_BF16 : s.prec, Uh, ldh, h0, s.r, d,
+                                    std::sqrt(hat_scale2), A, st));
+      ++kernels;
+    }
     CK(launch_qr(A, s.r, d, d, R, Hinv, qrws, dst, st));
-    kernels += 4;
+    kernels += 3;
   }
   CK(cudaEventRecord(e_qr, st));
   if (tr && tr->hinv_out)
@@ -608,6 +635,8 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     if (L.cs) bytes += 2.0 * (double)p->N * (d + 1) * bx + (double)L.n_samp * (d + 1) * bu;  // nested and S-hat passes
     else if (L.sp.single) bytes += (double)p->N * (d + 1) * bx + (double)L.n_samp * (d + 1) * bu;
     else bytes += (double)p->N * (d + 1) * bx + 2.0 * (double)L.Np * (d + 1) * bu + (double)L.n_samp * (d + 1) * bu;
+    // Gaussian Hessian sketch: one read of X (and, mixed, the packed BF16 copy written and read)
+    if (L.gauss) bytes += (double)p->N * d * bx + (mixed ? 2.0 * (double)p->N * L.gp.ncp * 2.0 : 0.0);
     for (size_t i = 0; i < s.m.size(); ++i) bytes += (double)s.a[i] * (double)s.m[i] * (d + 1) * bu;
     // a 2nd-stage pass reads X and one N-vector (Y in FP64 / rebase passes, r0 otherwise)
     rep->bytes_grad2 = (double)p->N * d * bx + (double)p->N * (mixed ? 4.0 : bx);
@@ -642,6 +671,7 @@ size_t slse_workspace_size(const slse_problem *prob, const slse_schedule *sched,
       const int kind = sched ? sched->kind : SLSE_SRHT;
       if (kind == SLSE_COUNTSKETCH) return is_pow2(arg) ? cs_plan(prob->N, prob->d, prec, arg, arg, 0).total : 0;
       if (kind == SLSE_COUNTSKETCH_HAT) return arg >= 1 ? cs_plan(prob->N, prob->d, prec, 0, 0, arg).total : 0;
+      if (kind == SLSE_GAUSSIAN) return arg >= 1 ? gauss_plan(prob->N, prob->d, prec, arg, true, nsm).total : 0;
       return sketch_layout(prob, prec, arg).total;
     }
     case SLSE_OP_GRAD:
@@ -678,16 +708,32 @@ slse_status slse_fit(const slse_problem *prob, const slse_schedule *sched, uint6
 
 slse_status slse_sketch(const slse_problem *prob, int32_t kind, int32_t prec, uint64_t seed, int64_t m, void *SX,
                         int64_t ldsx, void *SY, void *workspace, size_t ws_bytes, slse_stream_t stream) {
-  if (!valid_problem(prob) || !SX || !SY) return SLSE_EINVAL;
+  if (!valid_problem(prob) || !SX || (!SY && kind != SLSE_GAUSSIAN)) return SLSE_EINVAL;
   if (is_host_pointer(prob->X) || is_host_pointer(prob->Y)) return SLSE_EINVAL;
-  if (kind != SLSE_SRHT && kind != SLSE_COUNTSKETCH && kind != SLSE_COUNTSKETCH_HAT) return SLSE_EINVAL;
+  if (kind != SLSE_SRHT && kind != SLSE_COUNTSKETCH && kind != SLSE_COUNTSKETCH_HAT && kind != SLSE_GAUSSIAN)
+    return SLSE_EINVAL;
   if (prec != SLSE_PREC_FP64 && prec != SLSE_PREC_MIXED_BF16 && prec != SLSE_PREC_MIXED_FP8) return SLSE_EINVAL;
   if (prec != SLSE_PREC_FP64 && prob->dtype != SLSE_F32) return SLSE_EINVAL;
   if (prec == SLSE_PREC_MIXED_FP8 && (kind != SLSE_SRHT || ldsx % 4 != 0 || reinterpret_cast<uintptr_t>(SX) % 4 != 0))
     return SLSE_EINVAL;
   const int64_t Np = padded(prob->N);
-  if (m < 1 || m > Np || ldsx < prob->d) return SLSE_EINVAL;
+  // sampled sketches keep at most N' rows; a Gaussian sketch may have any number (row index 32-bit)
+  if (m < 1 || ldsx < prob->d || m > (kind == SLSE_GAUSSIAN ? int64_t(INT32_MAX) : Np)) return SLSE_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
+  if (kind == SLSE_GAUSSIAN) {
+    if (prec == SLSE_PREC_MIXED_FP8) return SLSE_EINVAL;
+    const int nsm = num_sms();
+    if (nsm <= 0) return SLSE_ECUDA;
+    const GaussPlan gp = gauss_plan(prob->N, prob->d, prec, m, SY != nullptr, nsm);
+    Workspace W;
+    slse_status a = acquire(W, workspace, ws_bytes, gp.total, st);
+    if (a != SLSE_OK) return a;
+    unsigned *status = reinterpret_cast<unsigned *>(static_cast<char *>(W.ptr) + gp.o_status);
+    CK(cudaMemsetAsync(status, 0, sizeof(unsigned), st));
+    CK(launch_gaussian(gp, prob->dtype, prob->X, prob->ldx, prob->Y, seed, SX, ldsx, SY, 1.0 / std::sqrt((double)m),
+                       status, W.ptr, st));
+    return SLSE_OK;
+  }
   if (kind != SLSE_SRHT) {
     if (kind == SLSE_COUNTSKETCH && !is_pow2(m)) return SLSE_EINVAL;
     const bool hat = kind == SLSE_COUNTSKETCH_HAT;
@@ -801,7 +847,7 @@ int32_t slse_default_schedule(int64_t N, int32_t d, slse_schedule *out, int64_t 
 int32_t slse_default_schedule_for(int64_t N, int32_t d, int32_t kind, slse_schedule *out, int64_t *m_buf,
                                   int32_t *a_buf, int32_t cap) {
   if (!out || N < 1 || d < 1) return -1;
-  if (kind != SLSE_SRHT && kind != SLSE_COUNTSKETCH) return -1;
+  if (kind != SLSE_SRHT && kind != SLSE_COUNTSKETCH && kind != SLSE_GAUSSIAN) return -1;
   const int64_t Np = padded(N);
   int32_t K = 0;
   // CountSketch sizes are powers of two: m_1 = 8d rounded up

@@ -1,0 +1,559 @@
+// Gaussian sketch (Sec. 2: S in R^{m x N} with i.i.d. N(0, 1/m) entries), used as the
+// Hessian sketch S-hat X = G X / sqrt(m).  Forming it is a dense (m x N)(N x d) product, so
+// the mixed-precision path runs it on the tensor cores.
+//
+// Entries: G[i, k] from Philox4x32-10 at counter (q mod 2^32, q div 2^32, 5, i), q = k div 8,
+// key = seed; output word j feeds Box-Muller with u1 = (w mod 2^16 + 1/2) 2^-16 and
+// u2 = (w div 2^16 + 1/2) 2^-16: G[i, 8q + 2j] = sqrt(-2 ln u1) cos(2 pi u2),
+// G[i, 8q + 2j + 1] = sqrt(-2 ln u1) sin(2 pi u2).
+//
+// MIXED_BF16 (X F32): X is packed once into BF16 chunks of 64 rows laid out as the K-major
+// operand of tcgen05.mma (8 x 16-byte core matrices); k_gauss_tc gives each CTA 128 rows of
+// G and a range of chunks.  Eight producer warps draw the G tile in FP32 (hardware log2,
+// sin, cos, rsqrt), round it to BF16 and store it in the same layout; one thread copies the
+// X chunk with cp.async.bulk; one thread issues the 128 x ncp x 64 MMAs into an FP32
+// accumulator in tensor memory; four warps read it back (tcgen05.ld) into per-split
+// partial sums, which k_gauss_reduce adds in a fixed order.
+// FP64: the same entries in double precision (log, sincospi) and an FP64 CUDA-core product.
+#include "slse_internal.cuh"
+
+namespace slse {
+namespace {
+
+constexpr int kStreamG = 5;
+
+// ------------------------------------------------------------------ normals
+__device__ __forceinline__ uint32_t box_muller_bf16x2(uint32_t w) {
+  // (lo + 1/2) 2^-16 exactly: 1 + lo 2^-16 minus (1 - 2^-17) (both in [1/2, 2]: exact)
+  const float u1 = __uint_as_float(0x3F800000u | ((w & 0xFFFFu) << 7)) - 0.99999237060546875f;
+  const float u2 = __uint_as_float(0x3F800000u | ((w >> 16) << 7)) - 0.99999237060546875f;
+  const float t = fmaxf(-1.3862943611198906f * __log2f(u1), 0x1p-30f);  // -2 ln u1
+  const float rad = t * rsqrtf(t);
+  float sn, cs;
+  // 2 pi u2 - pi lies in (-pi, pi), where the hardware sine and cosine are accurate;
+  // cos(2 pi u2) = -cos(theta), sin(2 pi u2) = -sin(theta)
+  __sincosf(fmaf(u2, 6.2831853071795865f, -3.1415926535897932f), &sn, &cs);
+  const __nv_bfloat162 h = __floats2bfloat162_rn(-rad * cs, -rad * sn);
+  return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+__device__ __forceinline__ void box_muller_f64(uint32_t w, double &a, double &b) {
+  const double u1 = ((double)(w & 0xFFFFu) + 0.5) * 0x1p-16;
+  const double u2 = ((double)(w >> 16) + 0.5) * 0x1p-16;
+  const double rad = sqrt(-2.0 * log(u1));
+  double sn, cs;
+  sincospi(2.0 * u2, &sn, &cs);
+  a = rad * cs;
+  b = rad * sn;
+}
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                   smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Waits for the phase of parity `parity` to complete.  Gives up (returns false) when the CTA's
+// abort flag is set, or after 2 s, which raises the flag and ST_TIMEOUT.
+__device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_f, unsigned *status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63u) == 0) {
+      if (*abort_f) return false;
+      if (global_ns() - t0 > 2000000000ull) {
+        *abort_f = 1;
+        atomicOr(status, ST_TIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// global -> shared bulk copy completing on an mbarrier (16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// Shared-memory matrix descriptor of tcgen05 for a K-major operand without swizzling:
+// start address, leading byte offset (between core matrices adjacent in K), stride byte
+// offset (between 8-row groups), descriptor version 1 (bit 46).
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+         (1ull << 46);
+}
+// Instruction descriptor of tcgen05.mma kind::f16: D F32 (bit 4), A and B BF16 (bits 7, 10),
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+// 32 lanes x 32 consecutive 32-bit columns: thread l of the warp gets row (lane base + l)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ------------------------------------------------------------------ tensor-core path
+constexpr int kBM = 128;               // rows of G per CTA (MMA M)
+constexpr int kBK = 64;                // rows of X per chunk (4 MMAs of K = 16)
+constexpr int kTileA = kBM * kBK * 2;  // 16 KiB
+constexpr int kProdWarps = 8;
+constexpr int kLoadWarp = 8, kMmaWarp = 9;
+constexpr int kTcThreads = 320;
+constexpr int kMaxStages = 8;
+
+struct TcArgs {
+  const uint8_t *xt;   // nchunk packed X chunks of ncp * 128 bytes
+  float *part;         // [splits][mpad][ncp]
+  unsigned *status;
+  int64_t nchunk, cps; // chunks, chunks per split
+  int64_t m;           // rows of G
+  int ncp;             // packed columns: a multiple of 16, <= 512
+  int tmem_cols;       // power of two >= max(ncp, 32)
+  int stages;
+  uint32_t seed_lo, seed_hi;
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_gauss_tc(const TcArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int S = a.stages;
+  const uint32_t bB = (uint32_t)a.ncp * 128u;
+  uint8_t *sA = sm;
+  uint8_t *sB = sm + (size_t)S * kTileA;
+  uint64_t *full_g = reinterpret_cast<uint64_t *>(sB + (size_t)S * bB);
+  uint64_t *full_x = full_g + S;
+  uint64_t *empty = full_x + S;
+  uint64_t *accum = empty + S;
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(accum + 1);
+  volatile int *abort_f = reinterpret_cast<volatile int *>(tslot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full_g[s], kProdWarps * 32);
+      mbar_init(&full_x[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    *abort_f = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == kLoadWarp) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(a.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const int64_t c0 = (int64_t)blockIdx.y * a.cps;
+  const int64_t c1 = c0 + a.cps < a.nchunk ? c0 + a.cps : a.nchunk;
+  const int nk = (int)(c1 - c0);
+  const int64_t m0 = (int64_t)blockIdx.x * kBM;
+
+  if (warp < kProdWarps) {
+    // producers: row = thread mod 128, octets 4h .. 4h + 3 of each chunk (h = thread div 128)
+    const int row = threadIdx.x & (kBM - 1);
+    const int h = threadIdx.x >> 7;
+    const int64_t gi = m0 + row;
+    const bool live = gi < a.m;
+    uint8_t *dst0 = sA + (row >> 3) * 1024 + (row & 7) * 16 + h * 4 * 128;
+    for (int k = 0; k < nk; ++k) {
+      const int s = k % S;
+      const uint32_t ph = (uint32_t)(k / S) & 1u;
+      if (!mbar_wait(&empty[s], ph ^ 1u, abort_f, a.status)) break;
+      uint8_t *dst = dst0 + (size_t)s * kTileA;
+      const uint64_t q0 = (uint64_t)(c0 + k) * 8u + (uint64_t)h * 4u;
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (live) {
+          const uint64_t q = q0 + o;
+          const U4 w = philox4x32_10((uint32_t)q, (uint32_t)(q >> 32), kStreamG, (uint32_t)gi, a.seed_lo, a.seed_hi);
+          v = make_uint4(box_muller_bf16x2(w.x), box_muller_bf16x2(w.y), box_muller_bf16x2(w.z),
+                         box_muller_bf16x2(w.w));
+        }
+        *reinterpret_cast<uint4 *>(dst + o * 128) = v;
+      }
+      fence_proxy_async_smem();
+      mbar_arrive(&full_g[s]);
+    }
+    if (warp < 4) {
+      // epilogue: TMEM lanes 32 warp .. 32 warp + 31 hold rows m0 + 32 warp + lane
+      const bool ok = mbar_wait(accum, 0u, abort_f, a.status);
+      tc_fence_after();
+      if (__all_sync(0xFFFFFFFFu, ok && !*abort_f)) {
+        float *dst = a.part + (((int64_t)blockIdx.y * gridDim.x * kBM) + m0 + 32 * warp + lane) * a.ncp;
+        for (int c = 0; c < a.ncp; c += 32) {
+          uint32_t v[32];
+          tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, v);
+          const int nv = a.ncp - c < 32 ? a.ncp - c : 32;  // ncp is a multiple of 16
+#pragma unroll
+          for (int j = 0; j < 32; j += 4)
+            if (j < nv) *reinterpret_cast<uint4 *>(dst + c + j) = make_uint4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        }
+      }
+      tc_fence_before();
+    }
+  } else if (warp == kLoadWarp) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int k = 0; k < nk; ++k) {
+        const int s = k % S;
+        const uint32_t ph = (uint32_t)(k / S) & 1u;
+        if (!mbar_wait(&empty[s], ph ^ 1u, abort_f, a.status)) break;
+        mbar_arrive_expect_tx(&full_x[s], bB);
+        bulk_g2s(sB + (size_t)s * bB, a.xt + (size_t)(c0 + k) * bB, bB, &full_x[s]);
+        issued = k + 1;
+      }
+      // copies in flight land before the CTA exits: the last use of each stage completes
+      // (on the normal path the MMA thread has already seen every one of them)
+      const int first = issued > S ? issued - S : 0;
+      for (int k = first; k < issued; ++k) {
+        volatile int never = 0;
+        mbar_wait(&full_x[k % S], (uint32_t)(k / S) & 1u, &never, a.status);
+      }
+    }
+  } else if (warp == kMmaWarp) {
+    if (lane == 0) {
+      const int n0 = a.ncp < 256 ? a.ncp : 256;
+      const uint32_t id0 = umma_idesc_bf16(kBM, n0);
+      const uint32_t id1 = a.ncp > 256 ? umma_idesc_bf16(kBM, a.ncp - 256) : 0u;
+      for (int k = 0; k < nk; ++k) {
+        const int s = k % S;
+        const uint32_t ph = (uint32_t)(k / S) & 1u;
+        if (!mbar_wait(&full_x[s], ph, abort_f, a.status)) break;
+        if (!mbar_wait(&full_g[s], ph, abort_f, a.status)) break;
+        tc_fence_after();
+        const uint32_t ab = smem_u32(sA + (size_t)s * kTileA);
+        const uint32_t bb = smem_u32(sB + (size_t)s * bB);
+#pragma unroll
+        for (int ks = 0; ks < kBK / 16; ++ks) {
+          // K step ks covers core-matrix columns 2 ks, 2 ks + 1 (128 bytes apart)
+          const uint64_t ad = umma_desc(ab + ks * 256, 128, 1024);
+          const uint32_t acc = (k > 0 || ks > 0) ? 1u : 0u;
+          umma_bf16(tmem, ad, umma_desc(bb + ks * 256, 128, 1024), id0, acc);
+          if (a.ncp > 256) umma_bf16(tmem + 256, ad, umma_desc(bb + 32 * 1024 + ks * 256, 128, 1024), id1, acc);
+        }
+        umma_commit(&empty[s]);
+      }
+      umma_commit(accum);  // arrives once every MMA issued above has completed
+    }
+  }
+  __syncthreads();
+  if (warp == kLoadWarp) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+  }
+}
+
+// X (F32, rows k of chunk c) -> BF16 chunk in the K-major core-matrix layout of the MMA's B
+// operand: element (n, k) at byte (n div 8) 1024 + (k div 8) 128 + (n mod 8) 16 + (k mod 8) 2.
+// Packed column j is X column c0 + j for j < nx, Y for j == ycol, zero otherwise; rows >= N
+// are zero.
+__global__ void __launch_bounds__(256) k_pack_xt(const float *__restrict__ X, int64_t ldx, const float *__restrict__ Y,
+                                                 int64_t N, int c0, int nx, int ycol, int ncp,
+                                                 uint8_t *__restrict__ xt) {
+  __shared__ float s[kBK][65];
+  const int64_t k0 = (int64_t)blockIdx.x * kBK;
+  uint8_t *blk = xt + (size_t)blockIdx.x * ncp * 128;
+  for (int sc = 0; sc < ncp; sc += 64) {
+    const int w = ncp - sc < 64 ? ncp - sc : 64;
+    for (int idx = threadIdx.x; idx < kBK * 64; idx += 256) {
+      const int r = idx >> 6, j = idx & 63;
+      const int64_t k = k0 + r;
+      const int col = sc + j;
+      float v = 0.f;
+      if (k < N && j < w) {
+        if (col < nx) v = X[k * ldx + c0 + col];
+        else if (col == ycol) v = Y[k];
+      }
+      s[r][j] = v;
+    }
+    __syncthreads();
+    const int units = (w / 8) * 64;
+    for (int u = threadIdx.x; u < units; u += 256) {
+      const int ng = u >> 6, k8 = (u >> 3) & 7, n7 = u & 7;
+      const int j = ng * 8 + n7;
+      uint32_t p[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(s[k8 * 8 + 2 * e][j], s[k8 * 8 + 2 * e + 1][j]);
+        p[e] = *reinterpret_cast<const uint32_t *>(&h);
+      }
+      *reinterpret_cast<uint4 *>(blk + (size_t)(sc / 8 + ng) * 1024 + k8 * 128 + n7 * 16) =
+          make_uint4(p[0], p[1], p[2], p[3]);
+    }
+    __syncthreads();
+  }
+}
+
+// out[i, j] = scale * sum over splits of part[split][i][j] (fixed order); NaN after a timeout
+template <typename TP, typename TO>
+__global__ void k_gauss_reduce(const TP *__restrict__ part, int splits, int64_t mpad, int ncp, int64_t m, int nx,
+                               int ycol, double scale, const unsigned *status, TO *SX, int64_t ldsx, TO *SY) {
+  const bool bad = (*(volatile const unsigned *)status & ST_TIMEOUT) != 0;
+  const int64_t total = m * ncp;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / ncp;
+    const int j = (int)(idx - i * ncp);
+    if (j >= nx && j != ycol) continue;
+    double v = 0.0;
+    for (int s = 0; s < splits; ++s) v += (double)part[((int64_t)s * mpad + i) * ncp + j];
+    v *= scale;
+    if (bad) v = __longlong_as_double(0x7FF8000000000000ll);
+    if (j < nx) SX[i * ldsx + j] = (TO)v;
+    else if (SY) SY[i] = (TO)v;
+  }
+}
+
+// ------------------------------------------------------------------ FP64 path
+constexpr int kF64M = 64, kF64N = 128, kF64K = 32;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gauss_f64(const T *__restrict__ X, int64_t ldx, const T *__restrict__ Y,
+                                                   int64_t N, int nx, int ycol, int64_t m, int64_t nchunk,
+                                                   int64_t cps, uint32_t slo, uint32_t shi, double *part,
+                                                   int64_t mpad, int ncpad) {
+  extern __shared__ double sh[];
+  double *sG = sh;                       // [64][33]
+  double *sX = sh + kF64M * (kF64K + 1); // [32][129]
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  const int64_t m0 = (int64_t)blockIdx.x * kF64M;
+  const int n0 = blockIdx.y * kF64N;
+  const int64_t ca = (int64_t)blockIdx.z * cps;
+  const int64_t cb = ca + cps < nchunk ? ca + cps : nchunk;
+  double acc[4][8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0;
+  for (int64_t c = ca; c < cb; ++c) {
+    const int64_t k0 = c * kF64K;
+    {  // G tile: row t / 4, octet t mod 4 (8 entries per Philox call)
+      const int r = t >> 2, o = t & 3;
+      const int64_t gi = m0 + r;
+      double g[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      if (gi < m) {
+        const uint64_t q = (uint64_t)(k0 >> 3) + o;
+        const U4 w = philox4x32_10((uint32_t)q, (uint32_t)(q >> 32), kStreamG, (uint32_t)gi, slo, shi);
+        box_muller_f64(w.x, g[0], g[1]);
+        box_muller_f64(w.y, g[2], g[3]);
+        box_muller_f64(w.z, g[4], g[5]);
+        box_muller_f64(w.w, g[6], g[7]);
+      }
+#pragma unroll
+      for (int e = 0; e < 8; ++e) sG[r * (kF64K + 1) + o * 8 + e] = g[e];
+    }
+    for (int idx = t; idx < kF64K * kF64N; idx += 256) {
+      const int r = idx / kF64N, j = idx - r * kF64N;
+      const int64_t k = k0 + r;
+      const int col = n0 + j;
+      double v = 0.0;
+      if (k < N) {
+        if (col < nx) v = (double)X[k * ldx + col];
+        else if (col == ycol) v = (double)Y[k];
+      }
+      sX[r * (kF64N + 1) + j] = v;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < kF64K; ++kk) {
+      double av[4], bv[8];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = sG[(ty * 4 + i) * (kF64K + 1) + kk];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) bv[j] = sX[kk * (kF64N + 1) + tx * 8 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      part[((int64_t)blockIdx.z * mpad + m0 + ty * 4 + i) * ncpad + n0 + tx * 8 + j] = acc[i][j];
+}
+
+int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+// ------------------------------------------------------------------ host side
+GaussPlan gauss_plan(int64_t N, int d, int prec, int64_t m, bool with_y, int nsm) {
+  GaussPlan p{};
+  p.N = N; p.d = d; p.prec = prec; p.m = m; p.with_y = with_y;
+  p.nsm = nsm > 0 ? nsm : 152;
+  const int ncols = d + (with_y ? 1 : 0);
+  if (prec == SLSE_PREC_FP64) {
+    p.groups = 1;
+    p.ncp = (int)cdiv(ncols, kF64N) * kF64N;
+    p.nchunk = cdiv(N, kF64K);
+    const int64_t mt = cdiv(m, kF64M), nt = p.ncp / kF64N;
+    int64_t splits = (4 * (int64_t)p.nsm) / (mt * nt);
+    if (splits < 1) splits = 1;
+    if (splits > p.nchunk) splits = p.nchunk;
+    p.cps = cdiv(p.nchunk, splits);
+    p.splits = (int)cdiv(p.nchunk, p.cps);
+    p.mpad = mt * kF64M;
+    p.o_part = 0;
+    p.total = al256((size_t)p.splits * p.mpad * p.ncp * 8) + 256;
+    p.o_status = p.total - 256;
+    return p;
+  }
+  p.groups = (ncols + 511) / 512;
+  const int wmax = ncols < 512 ? ncols : 512;
+  p.ncp = (wmax + 15) & ~15;
+  int tc = 32;
+  while (tc < p.ncp) tc <<= 1;
+  p.tmem_cols = tc;
+  const size_t bB = (size_t)p.ncp * 128;
+  int S = (int)((232448 - 2048) / (kTileA + bB));
+  if (S > kMaxStages) S = kMaxStages;
+  p.stages = S;
+  size_t smem = (size_t)S * (kTileA + bB) + (3 * S + 1) * 8 + 8 + 1024;
+  // at most 512 / tmem_cols CTAs may share an SM (their TMEM allocations must all fit)
+  const size_t floor_smem = 233472 / (512 / tc + 1) - 1024 + 1;
+  if (smem < floor_smem) smem = floor_smem;
+  p.smem = smem;
+  const int per_sm = (int)(233472 / (smem + 1024)) < 512 / tc ? (int)(233472 / (smem + 1024)) : 512 / tc;
+  p.nchunk = cdiv(N, kBK);
+  const int64_t mt = cdiv(m, kBM);
+  int64_t splits = ((int64_t)p.nsm * (per_sm > 0 ? per_sm : 1)) / mt;
+  if (splits < 1) splits = 1;
+  if (splits > p.nchunk) splits = p.nchunk;
+  p.cps = cdiv(p.nchunk, splits);
+  p.splits = (int)cdiv(p.nchunk, p.cps);
+  p.mpad = mt * kBM;
+  p.o_xt = 0;
+  p.o_part = al256((size_t)p.nchunk * bB);
+  p.total = p.o_part + al256((size_t)p.splits * p.mpad * p.ncp * 4) + 256;
+  p.o_status = p.total - 256;
+  return p;
+}
+
+cudaError_t launch_gaussian(const GaussPlan &p, int xdtype, const void *X, int64_t ldx, const void *Y, uint64_t seed,
+                            void *SX, int64_t ldsx, void *SY, double scale, unsigned *status, void *ws,
+                            cudaStream_t s) {
+  uint8_t *base = static_cast<uint8_t *>(ws);
+  const uint32_t slo = (uint32_t)seed, shi = (uint32_t)(seed >> 32);
+  cudaError_t e;
+  if (p.prec == SLSE_PREC_FP64) {
+    double *part = reinterpret_cast<double *>(base + p.o_part);
+    const size_t smem = (size_t)(kF64M * (kF64K + 1) + kF64K * (kF64N + 1)) * 8;
+    const dim3 grid((unsigned)(p.mpad / kF64M), (unsigned)(p.ncp / kF64N), (unsigned)p.splits);
+    const int ycol = p.with_y ? p.d : -1;
+    if (xdtype == SLSE_F64) {
+      if ((e = cudaFuncSetAttribute(k_gauss_f64<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+        return e;
+      k_gauss_f64<double><<<grid, 256, smem, s>>>(static_cast<const double *>(X), ldx, static_cast<const double *>(Y),
+                                                   p.N, p.d, ycol, p.m, p.nchunk, p.cps, slo, shi, part, p.mpad,
+                                                   p.ncp);
+    } else {
+      if ((e = cudaFuncSetAttribute(k_gauss_f64<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+        return e;
+      k_gauss_f64<float><<<grid, 256, smem, s>>>(static_cast<const float *>(X), ldx, static_cast<const float *>(Y),
+                                                 p.N, p.d, ycol, p.m, p.nchunk, p.cps, slo, shi, part, p.mpad, p.ncp);
+    }
+    if ((e = cudaGetLastError())) return e;
+    const int64_t tot = p.m * p.ncp;
+    const int rb = (int)(cdiv(tot, 256) < 8 * p.nsm ? cdiv(tot, 256) : 8 * p.nsm);
+    k_gauss_reduce<double, double><<<rb, 256, 0, s>>>(part, p.splits, p.mpad, p.ncp, p.m, p.d, ycol, scale, status,
+                                                      static_cast<double *>(SX), ldsx, static_cast<double *>(SY));
+    return cudaGetLastError();
+  }
+  if (xdtype != SLSE_F32) return cudaErrorInvalidValue;
+  uint8_t *xt = base + p.o_xt;
+  float *part = reinterpret_cast<float *>(base + p.o_part);
+  if ((e = cudaFuncSetAttribute(k_gauss_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem))) return e;
+  const int ncols = p.d + (p.with_y ? 1 : 0);
+  for (int g = 0; g < p.groups; ++g) {
+    const int c0 = 512 * g;
+    const int w = ncols - c0 < 512 ? ncols - c0 : 512;
+    const int nx = p.d - c0 < w ? (p.d - c0 > 0 ? p.d - c0 : 0) : w;
+    const int ycol = p.with_y && p.d >= c0 && p.d < c0 + w ? p.d - c0 : -1;
+    const int ncp = (w + 15) & ~15;
+    k_pack_xt<<<(unsigned)p.nchunk, 256, 0, s>>>(static_cast<const float *>(X), ldx, static_cast<const float *>(Y),
+                                                 p.N, c0, nx, ycol, ncp, xt);
+    if ((e = cudaGetLastError())) return e;
+    TcArgs a{};
+    a.xt = xt; a.part = part; a.status = status; a.nchunk = p.nchunk; a.cps = p.cps; a.m = p.m; a.ncp = ncp;
+    int tc = 32;
+    while (tc < ncp) tc <<= 1;
+    a.tmem_cols = tc <= p.tmem_cols ? tc : p.tmem_cols;
+    a.stages = p.stages;
+    a.seed_lo = slo; a.seed_hi = shi;
+    k_gauss_tc<<<dim3((unsigned)(p.mpad / kBM), (unsigned)p.splits), kTcThreads, p.smem, s>>>(a);
+    if ((e = cudaGetLastError())) return e;
+    const int64_t tot = p.m * ncp;
+    const int rb = (int)(cdiv(tot, 256) < 8 * p.nsm ? cdiv(tot, 256) : 8 * p.nsm);
+    k_gauss_reduce<float, __nv_bfloat16><<<rb, 256, 0, s>>>(
+        part, p.splits, p.mpad, ncp, p.m, nx, ycol, scale, status, static_cast<__nv_bfloat16 *>(SX) + c0, ldsx,
+        static_cast<__nv_bfloat16 *>(SY));
+    if ((e = cudaGetLastError())) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace slse

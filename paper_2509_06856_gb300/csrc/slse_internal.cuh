@@ -134,6 +134,28 @@ cudaError_t launch_mx_to_bf16(const uint8_t *U, int64_t ldq, const uint8_t *S, i
 cudaError_t launch_quantize_mx(const __nv_bfloat16 *A, int64_t lda, int64_t rows, int d, uint8_t *U, int64_t ldq,
                                uint8_t *S, int64_t nsb, cudaStream_t s);
 
+// gaussian.cu: the Gaussian sketch G [X | Y] / sqrt(m) (G m x N, entries from Philox stream 5
+// and Box-Muller).  FP64: FP64 entries and products (X F64 or F32).  MIXED_BF16 (X F32): BF16
+// entries and X on the tensor cores with FP32 accumulation, output BF16.
+struct GaussPlan {
+  int64_t N, m;
+  int d, prec, nsm;
+  bool with_y;
+  int groups;          // column groups of <= 512 packed columns (tensor-core path)
+  int ncp;             // packed columns of the widest group
+  int tmem_cols, stages;
+  size_t smem;
+  int64_t nchunk, cps, mpad;
+  int splits;
+  size_t o_xt, o_part, o_status, total;  // workspace layout (o_status: one word the caller clears)
+};
+GaussPlan gauss_plan(int64_t N, int d, int prec, int64_t m, bool with_y, int nsm);
+// SX (m x ldsx) and SY (m, nullable when the plan has no Y column) of the output precision;
+// status: ST_TIMEOUT is raised there when a bounded wait gave up (the output is then NaN).
+cudaError_t launch_gaussian(const GaussPlan &p, int xdtype, const void *X, int64_t ldx, const void *Y, uint64_t seed,
+                            void *SX, int64_t ldsx, void *SY, double scale, unsigned *status, void *ws,
+                            cudaStream_t s);
+
 // draws.cu
 size_t draws_ws_bytes(int64_t Np);
 cudaError_t launch_draws(int64_t Np, uint64_t seed, int32_t *Psd /*N', sign-folded P*/,

@@ -101,7 +101,10 @@ def test_countsketch_host_side(lib):
         assert a.m == b.m and a.a == b.a and a.r == b.r and a.kind == slse.COUNTSKETCH
         assert all(m & (m - 1) == 0 for m in a.m)
     c = slse.CSchedule()
-    assert slse._lib.slse_default_schedule_for(1000, 10, slse.GAUSSIAN, ctypes.byref(c), None, None, 0) == -1
+    # the Gaussian Hessian sketch keeps the SRHT subproblems: same sizes as the SRHT schedule
+    g, s_ = slse.default_schedule(20000, 50, kind="gaussian"), slse.default_schedule(20000, 50)
+    assert g.m == s_.m and g.a == s_.a and g.r == s_.r and g.kind == slse.GAUSSIAN
+    assert slse._lib.slse_default_schedule_for(1000, 10, 7, ctypes.byref(c), None, None, 0) == -1
     beta = (ctypes.c_double * 4)()
     good = slse.CProblem(100, 4, slse.F64, 256, 4, 512)
     sch = slse.Schedule(m=[24, 48], a=[2, 2], r=24, mu=0.7, eta=0.1, kind=slse.COUNTSKETCH).to_c()  # not 2^l
@@ -111,8 +114,18 @@ def test_countsketch_host_side(lib):
     assert slse._lib.slse_workspace_size(ctypes.byref(good), ctypes.byref(ok), slse.OP_FIT, 0) > 0
     assert slse._lib.slse_workspace_size(ctypes.byref(good), ctypes.byref(ok), slse.OP_SKETCH, 48) == 0
     assert slse._lib.slse_workspace_size(ctypes.byref(good), ctypes.byref(ok), slse.OP_SKETCH, 64) > 0
-    sch = slse.Schedule(m=[16], a=[2], r=24, mu=0.7, eta=0.1, kind=slse.GAUSSIAN).to_c()         # not built
-    assert slse._lib.slse_fit(ctypes.byref(good), ctypes.byref(sch), 0, beta, None, None, None, 0, None) == slse.EINVAL
+    sch = slse.Schedule(m=[16], a=[2], r=24, mu=0.7, eta=0.1, kind=slse.GAUSSIAN, prec="mixed_fp8").to_c()
+    good32 = slse.CProblem(100, 4, slse.F32, 256, 4, 512)
+    assert slse._lib.slse_workspace_size(ctypes.byref(good32), ctypes.byref(sch), slse.OP_FIT, 0) == 0
+    assert slse._lib.slse_fit(ctypes.byref(good32), ctypes.byref(sch), 0, beta, None, None, None, 0, None) == \
+        slse.EINVAL
+    gs_ = slse.Schedule(m=[16], a=[2], r=24, mu=0.7, eta=0.1, kind=slse.GAUSSIAN).to_c()
+    assert slse._lib.slse_workspace_size(ctypes.byref(good), ctypes.byref(gs_), slse.OP_FIT, 0) > 0
+    assert slse._lib.slse_workspace_size(ctypes.byref(good), ctypes.byref(gs_), slse.OP_SKETCH, 30) > 0
+    # S Y may be omitted only for the Gaussian kind; the FP8 form is SRHT only
+    assert slse._lib.slse_sketch(ctypes.byref(good), slse.SRHT, 0, 0, 16, 1024, 4, None, None, 0, None) == slse.EINVAL
+    assert slse._lib.slse_sketch(ctypes.byref(good), slse.GAUSSIAN, 2, 0, 16, 1024, 4, None, None, 0, None) == \
+        slse.EINVAL
     assert slse._lib.slse_sketch(ctypes.byref(good), slse.COUNTSKETCH, 0, 0, 48, 1, 4, 1, None, 0, None) == slse.EINVAL
 
 
