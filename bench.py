@@ -34,6 +34,7 @@ TARGET = 1e-8
 def workload_name(log2n: int, d: int) -> str:
     return f"AR(1) rho=0.5 Gaussian rows, N=2^{log2n}, d={d}, X fp32, sigma=0.1, beta~N(0,I)"
 FALLBACK_HBM = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
 
 
 def parse():
@@ -48,6 +49,7 @@ def parse():
     ap.add_argument("--cs-steps", type=int, default=2, help="CountSketch-variant fits reported beside the SRHT line")
     ap.add_argument("--fp8-steps", type=int, default=2, help="fits with the FP8 form of the sketch")
     ap.add_argument("--tuning-steps", type=int, default=2, help="fits with the SLSE-FRS-tuning schedule")
+    ap.add_argument("--gauss-steps", type=int, default=2, help="fits with the Gaussian Hessian sketch")
     ap.add_argument("--diff-steps", type=int, default=2, help="forward+backward passes of the differentiation block")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--sample-log2n", type=int, default=15)
@@ -168,6 +170,18 @@ def measured_hbm_peak():
     except (OSError, ValueError):
         pass
     return FALLBACK_HBM, "fallback"
+
+
+def measured_bf16_peak():
+    """Dense BF16 tensor peak (TFLOP/s) for a kernel timed on its own: the burst figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            v = json.load(f).get("bf16_tflops")
+        if v:
+            return float(v), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_BF16_TFLOPS, "fallback"
 
 
 def profile_traffic(kernel_key, source_files):
@@ -469,6 +483,51 @@ def run_ours(args, rank, ws, local_rank):
                   "sketch_frac_of_" + peak_kind: by / rc["ms_sketch"] / 1e6 / peak}
         torch.cuda.empty_cache()
 
+    # Gaussian Hessian sketch (Sec. 2) on the same workload: SRHT subproblems, S-hat X = G X / sqrt(r)
+    # formed on the tensor cores; the sketch call alone is timed against the dense BF16 peak
+    gau = None
+    if args.gauss_steps > 0:
+        sg = slse.default_schedule(N, d, prec="mixed_bf16", T=100, tol=5e-9, kind="gaussian")
+        wg = slse.alloc_workspace(slse.workspace_size(Xd, Yd, slse.OP_FIT, sg))
+        slse.fit(Xd, Yd, sg, seed=995, workspace=wg, trace_cap=cap)
+        tg, fin = [], []
+        for k in range(args.gauss_steps):
+            r = slse.fit(Xd, Yd, sg, seed=k, workspace=wg, trace_cap=cap)
+            if rank == 0:
+                a8, _ = first_crossing(r.beta_hist.cpu().numpy(), np.array(r.ms_hist), bh, TARGET)
+                tg.append(a8)
+                fin.append(float(np.linalg.norm(r.beta - bh) / np.linalg.norm(bh)))
+        del wg
+        torch.cuda.empty_cache()
+        wsk = slse.alloc_workspace(slse.workspace_size(Xd, Yd, slse.OP_SKETCH, sg, sg.r))
+        for w in range(3):
+            slse.sketch(Xd, Yd, sg.r, seed=w, prec="mixed_bf16", kind="gaussian", workspace=wsk, want_y=False)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ng = 5
+        torch.cuda.synchronize()
+        e0.record()
+        for k in range(ng):
+            slse.sketch(Xd, Yd, sg.r, seed=k, prec="mixed_bf16", kind="gaussian", workspace=wsk, want_y=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_sk = e0.elapsed_time(e1) / ng
+        del wsk
+        torch.cuda.empty_cache()
+        if rank == 0:
+            rg = r.report
+            tpk, tkind = measured_bf16_peak()
+            flops = 2.0 * sg.r * N * d
+            gau = {"time_to_1e-8_ms": statistics.mean(tg) if all(v is not None for v in tg) else None,
+                   "final_rel_err": max(fin),
+                   "phases_ms": {k: rg[k] for k in ("ms_sketch", "ms_srht_pass1", "ms_srht_pass2", "ms_qr",
+                                                    "ms_stage1", "ms_stage2", "ms_total")},
+                   "iters": [rg["iters_stage1"], rg["iters_stage2"]],
+                   "sketch_call_ms": ms_sk,
+                   "sketch_call": f"G X / sqrt(r), r={sg.r}: pack X to BF16, tensor-core product, split sum",
+                   "tensor_tflops": flops / ms_sk / 1e9, "tensor_peak_tflops": tpk,
+                   "frac_of_" + tkind: flops / ms_sk / 1e9 / tpk}
+        torch.cuda.empty_cache()
+
     # differentiation through the estimate at the N = 2^21, d = 128 FP32 workload (forward
     # fit, backward normal-equation solve and the one-pass input gradients)
     diff = None
@@ -546,6 +605,7 @@ def run_ours(args, rank, ws, local_rank):
         "countsketch": cs,
         "tuning": tun,
         "fp8": f8,
+        "gaussian": gau,
         "differentiation": diff,
         "phases_ms": {k: rep[k] for k in ("ms_draws", "ms_sketch", "ms_srht_pass1", "ms_srht_pass2", "ms_qr",
                                           "ms_stage1", "ms_stage2", "ms_total")},
