@@ -23,17 +23,40 @@ namespace {
 constexpr int kStreamG = 5;
 
 // ------------------------------------------------------------------ normals
+// single-instruction approximations (the operands here are normal numbers: ftz changes nothing)
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sin_approx(float x) {
+  float y;
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float cos_approx(float x) {
+  float y;
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ uint32_t box_muller_bf16x2(uint32_t w) {
-  // (lo + 1/2) 2^-16 exactly: 1 + lo 2^-16 minus (1 - 2^-17) (both in [1/2, 2]: exact)
-  const float u1 = __uint_as_float(0x3F800000u | ((w & 0xFFFFu) << 7)) - 0.99999237060546875f;
-  const float u2 = __uint_as_float(0x3F800000u | ((w >> 16) << 7)) - 0.99999237060546875f;
-  const float t = fmaxf(-1.3862943611198906f * __log2f(u1), 0x1p-30f);  // -2 ln u1
-  const float rad = t * rsqrtf(t);
-  float sn, cs;
-  // 2 pi u2 - pi lies in (-pi, pi), where the hardware sine and cosine are accurate;
+  // (lo + 1/2) 2^-16 exactly: the float 1 + lo 2^-16 minus (1 - 2^-17) (both in [1/2, 2]: exact)
+  const float u1 = __uint_as_float(((w << 7) & 0x007FFF80u) | 0x3F800000u) - 0.99999237060546875f;
+  const float u2 = __uint_as_float(((w >> 9) & 0x007FFF80u) | 0x3F800000u) - 0.99999237060546875f;
+  // t = -2 ln u1 >= -2 ln(1 - 2^-17) = 1.5e-5, far above the 2^-22 absolute error of lg2 near 1,
+  // so t > 0 and the reciprocal square root is finite
+  const float t = -1.3862943611198906f * lg2_approx(u1);
+  const float nrad = -t * rsqrt_approx(t);  // -sqrt(t)
+  // theta = 2 pi u2 - pi lies in (-pi, pi), where the hardware sine and cosine are accurate;
   // cos(2 pi u2) = -cos(theta), sin(2 pi u2) = -sin(theta)
-  __sincosf(fmaf(u2, 6.2831853071795865f, -3.1415926535897932f), &sn, &cs);
-  const __nv_bfloat162 h = __floats2bfloat162_rn(-rad * cs, -rad * sn);
+  const float th = fmaf(u2, 6.2831853071795865f, -3.1415926535897932f);
+  const __nv_bfloat162 h = __floats2bfloat162_rn(nrad * cos_approx(th), nrad * sin_approx(th));
   return *reinterpret_cast<const uint32_t *>(&h);
 }
 
@@ -45,6 +68,30 @@ __device__ __forceinline__ void box_muller_f64(uint32_t w, double &a, double &b)
   sincospi(2.0 * u2, &sn, &cs);
   a = rad * cs;
   b = rad * sn;
+}
+
+// Philox4x32-10 with the round keys precomputed (they are the same for every call of a
+// thread): per round two 32x32->64-bit products and two three-input XORs.
+struct RoundKeys {
+  uint32_t k0[10], k1[10];
+};
+__device__ __forceinline__ RoundKeys round_keys(uint32_t k0, uint32_t k1) {
+  RoundKeys r;
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    r.k0[i] = k0 + (uint32_t)i * 0x9E3779B9u;
+    r.k1[i] = k1 + (uint32_t)i * 0xBB67AE85u;
+  }
+  return r;
+}
+__device__ __forceinline__ U4 philox_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, const RoundKeys &K) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c0, p1 = (uint64_t)0xCD9E8D57u * c2;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ K.k0[i], n2 = (uint32_t)(p0 >> 32) ^ c3 ^ K.k1[i];
+    c0 = n0; c1 = (uint32_t)p1; c2 = n2; c3 = (uint32_t)p0;
+  }
+  return U4{c0, c1, c2, c3};
 }
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -78,8 +125,7 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 // Waits for the phase of parity `parity` to complete.  Gives up (returns false) when the CTA's
 // abort flag is set, or after 2 s, which raises the flag and ST_TIMEOUT.
-__device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_f, unsigned *status) {
-  if (mbar_try_wait(bar, parity)) return true;
+__device__ __noinline__ bool mbar_wait_slow(uint64_t *bar, uint32_t parity, volatile int *abort_f, unsigned *status) {
   const uint64_t t0 = global_ns();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
@@ -92,6 +138,9 @@ __device__ __noinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile 
       }
     }
   }
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_f, unsigned *status) {
+  return mbar_try_wait(bar, parity) || mbar_wait_slow(bar, parity, abort_f, status);
 }
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -146,16 +195,23 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 }
 
 // ------------------------------------------------------------------ tensor-core path
+// A chunk is 32 rows of X (two MMAs of K = 16).  Operands sit in shared memory as K-major
+// core matrices (8 rows x 16 bytes): element (row, k) of a tile at byte
+// (row div 8) 512 + (k div 8) 128 + (row mod 8) 16 + (k mod 8) 2, so the descriptors use a
+// leading byte offset of 128 (next core matrix along K) and a stride byte offset of 512
+// (next group of 8 rows).
 constexpr int kBM = 128;               // rows of G per CTA (MMA M)
-constexpr int kBK = 64;                // rows of X per chunk (4 MMAs of K = 16)
-constexpr int kTileA = kBM * kBK * 2;  // 16 KiB
-constexpr int kProdWarps = 8;
-constexpr int kLoadWarp = 8, kMmaWarp = 9;
-constexpr int kTcThreads = 320;
+constexpr int kBK = 32;                // rows of X per chunk
+constexpr int kSBO = kBK * 16;         // bytes between 8-row groups of a tile
+constexpr int kTileA = kBM * kBK * 2;  // 8 KiB
+constexpr int kProdWarps = 16;         // 512 producer threads: one Philox call (8 entries) each per chunk
+constexpr int kLoadWarp = kProdWarps, kMmaWarp = kProdWarps + 1;
+constexpr int kTcThreads = (kProdWarps + 2) * 32;
 constexpr int kMaxStages = 8;
+static_assert(kProdWarps * 32 == kBM * (kBK / 8), "one 8-entry octet per producer thread and chunk");
 
 struct TcArgs {
-  const uint8_t *xt;   // nchunk packed X chunks of ncp * 128 bytes
+  const uint8_t *xt;   // nchunk packed X chunks of ncp * 64 bytes
   float *part;         // [splits][mpad][ncp]
   unsigned *status;
   int64_t nchunk, cps; // chunks, chunks per split
@@ -166,11 +222,14 @@ struct TcArgs {
   uint32_t seed_lo, seed_hi;
 };
 
+// Pipeline per CTA (rows m0 .. m0 + 127 of G, chunks c0 .. c1 - 1): stage s of S holds one G
+// tile (producer warps) and one X chunk (bulk copy); the MMA thread waits for both, issues the
+// chunk's MMAs and commits them to empty[s], which frees the stage for both producers.
 __global__ void __launch_bounds__(kTcThreads, 1) k_gauss_tc(const TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int S = a.stages;
-  const uint32_t bB = (uint32_t)a.ncp * 128u;
+  const uint32_t bB = (uint32_t)a.ncp * (kBK * 2);
   uint8_t *sA = sm;
   uint8_t *sB = sm + (size_t)S * kTileA;
   uint64_t *full_g = reinterpret_cast<uint64_t *>(sB + (size_t)S * bB);
@@ -183,7 +242,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gauss_tc(const TcArgs a) {
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
-      mbar_init(&full_g[s], kProdWarps * 32);
+      mbar_init(&full_g[s], kProdWarps);  // one arrival per producer warp
       mbar_init(&full_x[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -207,31 +266,35 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gauss_tc(const TcArgs a) {
   const int64_t m0 = (int64_t)blockIdx.x * kBM;
 
   if (warp < kProdWarps) {
-    // producers: row = thread mod 128, octets 4h .. 4h + 3 of each chunk (h = thread div 128)
+    // producers: row = thread mod 128, octet (8 entries along K) = thread div 128
     const int row = threadIdx.x & (kBM - 1);
-    const int h = threadIdx.x >> 7;
+    const int oct = threadIdx.x >> 7;
     const int64_t gi = m0 + row;
     const bool live = gi < a.m;
-    uint8_t *dst0 = sA + (row >> 3) * 1024 + (row & 7) * 16 + h * 4 * 128;
+    uint8_t *dst0 = sA + (row >> 3) * kSBO + (row & 7) * 16 + oct * 128;
+    // the Philox words of chunk k + 1 are drawn beside the Box-Muller step of chunk k (two
+    // independent dependency chains per thread)
+    const RoundKeys K = round_keys(a.seed_lo, a.seed_hi);
+    uint64_t q = (uint64_t)c0 * (kBK / 8) + (uint64_t)oct;  // octet index of chunk k along K
+    U4 wn = philox_rk((uint32_t)q, (uint32_t)(q >> 32), kStreamG, (uint32_t)gi, K);
+    int s = 0;
+    uint32_t ph = 0;
     for (int k = 0; k < nk; ++k) {
-      const int s = k % S;
-      const uint32_t ph = (uint32_t)(k / S) & 1u;
-      if (!mbar_wait(&empty[s], ph ^ 1u, abort_f, a.status)) break;
-      uint8_t *dst = dst0 + (size_t)s * kTileA;
-      const uint64_t q0 = (uint64_t)(c0 + k) * 8u + (uint64_t)h * 4u;
-#pragma unroll
-      for (int o = 0; o < 4; ++o) {
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (live) {
-          const uint64_t q = q0 + o;
-          const U4 w = philox4x32_10((uint32_t)q, (uint32_t)(q >> 32), kStreamG, (uint32_t)gi, a.seed_lo, a.seed_hi);
-          v = make_uint4(box_muller_bf16x2(w.x), box_muller_bf16x2(w.y), box_muller_bf16x2(w.z),
-                         box_muller_bf16x2(w.w));
-        }
-        *reinterpret_cast<uint4 *>(dst + o * 128) = v;
-      }
+      // warp-uniform: a lane that gave up takes its whole warp out of the loop
+      if (!__all_sync(0xFFFFFFFFu, mbar_wait(&empty[s], ph ^ 1u, abort_f, a.status))) break;
+      const U4 w = wn;
+      if (k + 1 < nk) q += kBK / 8;
+      wn = philox_rk((uint32_t)q, (uint32_t)(q >> 32), kStreamG, (uint32_t)gi, K);
+      uint4 v = make_uint4(box_muller_bf16x2(w.x), box_muller_bf16x2(w.y), box_muller_bf16x2(w.z),
+                           box_muller_bf16x2(w.w));
+      if (!live) v = make_uint4(0u, 0u, 0u, 0u);
+      *reinterpret_cast<uint4 *>(dst0 + (size_t)s * kTileA) = v;
+      // each thread orders its own store before the MMA's (async-proxy) read; the warp then
+      // arrives once
       fence_proxy_async_smem();
-      mbar_arrive(&full_g[s]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&full_g[s]);
+      if (++s == S) { s = 0; ph ^= 1u; }
     }
     if (warp < 4) {
       // epilogue: TMEM lanes 32 warp .. 32 warp + 31 hold rows m0 + 32 warp + lane
@@ -252,14 +315,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gauss_tc(const TcArgs a) {
     }
   } else if (warp == kLoadWarp) {
     if (lane == 0) {
-      int issued = 0;
+      int issued = 0, s = 0;
+      uint32_t ph = 0;
       for (int k = 0; k < nk; ++k) {
-        const int s = k % S;
-        const uint32_t ph = (uint32_t)(k / S) & 1u;
         if (!mbar_wait(&empty[s], ph ^ 1u, abort_f, a.status)) break;
         mbar_arrive_expect_tx(&full_x[s], bB);
         bulk_g2s(sB + (size_t)s * bB, a.xt + (size_t)(c0 + k) * bB, bB, &full_x[s]);
         issued = k + 1;
+        if (++s == S) { s = 0; ph ^= 1u; }
       }
       // copies in flight land before the CTA exits: the last use of each stage completes
       // (on the normal path the MMA thread has already seen every one of them)
@@ -274,9 +337,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gauss_tc(const TcArgs a) {
       const int n0 = a.ncp < 256 ? a.ncp : 256;
       const uint32_t id0 = umma_idesc_bf16(kBM, n0);
       const uint32_t id1 = a.ncp > 256 ? umma_idesc_bf16(kBM, a.ncp - 256) : 0u;
+      int s = 0;
+      uint32_t ph = 0;
       for (int k = 0; k < nk; ++k) {
-        const int s = k % S;
-        const uint32_t ph = (uint32_t)(k / S) & 1u;
         if (!mbar_wait(&full_x[s], ph, abort_f, a.status)) break;
         if (!mbar_wait(&full_g[s], ph, abort_f, a.status)) break;
         tc_fence_after();
@@ -285,12 +348,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gauss_tc(const TcArgs a) {
 #pragma unroll
         for (int ks = 0; ks < kBK / 16; ++ks) {
           // K step ks covers core-matrix columns 2 ks, 2 ks + 1 (128 bytes apart)
-          const uint64_t ad = umma_desc(ab + ks * 256, 128, 1024);
+          const uint64_t ad = umma_desc(ab + ks * 256, 128, kSBO);
           const uint32_t acc = (k > 0 || ks > 0) ? 1u : 0u;
-          umma_bf16(tmem, ad, umma_desc(bb + ks * 256, 128, 1024), id0, acc);
-          if (a.ncp > 256) umma_bf16(tmem + 256, ad, umma_desc(bb + 32 * 1024 + ks * 256, 128, 1024), id1, acc);
+          umma_bf16(tmem, ad, umma_desc(bb + ks * 256, 128, kSBO), id0, acc);
+          if (a.ncp > 256) umma_bf16(tmem + 256, ad, umma_desc(bb + 32 * kSBO + ks * 256, 128, kSBO), id1, acc);
         }
         umma_commit(&empty[s]);
+        if (++s == S) { s = 0; ph ^= 1u; }
       }
       umma_commit(accum);  // arrives once every MMA issued above has completed
     }
@@ -303,44 +367,70 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gauss_tc(const TcArgs a) {
   }
 }
 
-// X (F32, rows k of chunk c) -> BF16 chunk in the K-major core-matrix layout of the MMA's B
-// operand: element (n, k) at byte (n div 8) 1024 + (k div 8) 128 + (n mod 8) 16 + (k mod 8) 2.
-// Packed column j is X column c0 + j for j < nx, Y for j == ycol, zero otherwise; rows >= N
-// are zero.
+// X (F32) -> BF16 chunks of 32 rows in the K-major core-matrix layout of the MMA's B operand:
+// element (n, k) of chunk c (k = row - 32 c) at byte (n div 8) 512 + (k div 8) 128 + (n mod 8) 16
+// + (k mod 8) 2.  Packed column n is X column c0 + n for n < nx, Y for n == ycol, zero otherwise;
+// rows >= N are zero.  One CTA per 64 rows (two chunks): each warp reads 8 whole rows
+// (float4 loads when VEC), rounds them to BF16 and stores them transposed in shared memory,
+// word (n, kw) (rows 2 kw, 2 kw + 1 of column n) at n 32 + (kw + n div 4) mod 32 so that the
+// 32 lanes of a store hit 32 banks; then 16-byte units are written out contiguously.
+template <bool VEC>
 __global__ void __launch_bounds__(256) k_pack_xt(const float *__restrict__ X, int64_t ldx, const float *__restrict__ Y,
                                                  int64_t N, int c0, int nx, int ycol, int ncp,
                                                  uint8_t *__restrict__ xt) {
-  __shared__ float s[kBK][65];
-  const int64_t k0 = (int64_t)blockIdx.x * kBK;
-  uint8_t *blk = xt + (size_t)blockIdx.x * ncp * 128;
-  for (int sc = 0; sc < ncp; sc += 64) {
-    const int w = ncp - sc < 64 ? ncp - sc : 64;
-    for (int idx = threadIdx.x; idx < kBK * 64; idx += 256) {
-      const int r = idx >> 6, j = idx & 63;
-      const int64_t k = k0 + r;
-      const int col = sc + j;
-      float v = 0.f;
-      if (k < N && j < w) {
-        if (col < nx) v = X[k * ldx + c0 + col];
-        else if (col == ycol) v = Y[k];
-      }
-      s[r][j] = v;
-    }
-    __syncthreads();
-    const int units = (w / 8) * 64;
-    for (int u = threadIdx.x; u < units; u += 256) {
-      const int ng = u >> 6, k8 = (u >> 3) & 7, n7 = u & 7;
-      const int j = ng * 8 + n7;
-      uint32_t p[4];
+  extern __shared__ uint32_t s32[];  // ncp x 32 words
+  uint16_t *s16 = reinterpret_cast<uint16_t *>(s32);
+  const int64_t k0 = (int64_t)blockIdx.x * 64;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int idx = threadIdx.x; idx < ncp * 32; idx += 256) s32[idx] = 0u;
+  __syncthreads();
+  auto put = [&](int n, int r, float f) {
+    const int w = n * 32 + (((r >> 1) + (n >> 2)) & 31);
+    const __nv_bfloat16 b = __float2bfloat16_rn(f);
+    s16[2 * w + (r & 1)] = *reinterpret_cast<const uint16_t *>(&b);
+  };
+  for (int rr = 0; rr < 8; ++rr) {
+    const int r = warp * 8 + rr;
+    const int64_t k = k0 + r;
+    if (k >= N) break;
+    const float *xr = X + k * ldx + c0;
+    if (VEC) {
+      const int ng4 = nx >> 2;  // nx <= 512: at most 4 float4 per lane
+      float4 v[4];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(s[k8 * 8 + 2 * e][j], s[k8 * 8 + 2 * e + 1][j]);
-        p[e] = *reinterpret_cast<const uint32_t *>(&h);
+      for (int it = 0; it < 4; ++it) {
+        const int g = lane + 32 * it;
+        v[it] = g < ng4 ? __ldg(reinterpret_cast<const float4 *>(xr) + g) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      *reinterpret_cast<uint4 *>(blk + (size_t)(sc / 8 + ng) * 1024 + k8 * 128 + n7 * 16) =
-          make_uint4(p[0], p[1], p[2], p[3]);
+#pragma unroll
+      for (int it = 0; it < 4; ++it) {
+        const int g = lane + 32 * it;
+        if (g < ng4) {
+          put(4 * g, r, v[it].x);
+          put(4 * g + 1, r, v[it].y);
+          put(4 * g + 2, r, v[it].z);
+          put(4 * g + 3, r, v[it].w);
+        }
+      }
+      if (lane < nx - 4 * ng4) put(4 * ng4 + lane, r, xr[4 * ng4 + lane]);
+    } else {
+      for (int n = lane; n < nx; n += 32) put(n, r, xr[n]);
     }
-    __syncthreads();
+    if (ycol >= 0 && lane == 0) put(ycol, r, Y[k]);
+  }
+  __syncthreads();
+  // unit v of chunk half hc: column n = (v div 32) 8 + v mod 8, row octet k8 = 4 hc + (v div 8) mod 4
+  const int per = ncp * 4;
+  for (int u = threadIdx.x; u < 2 * per; u += 256) {
+    const int hc = u >= per ? 1 : 0;
+    const int v = u - hc * per;
+    const int n = (v >> 5) * 8 + (v & 7);
+    const int k8 = 4 * hc + ((v >> 3) & 3);
+    uint32_t p[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) p[j] = s32[n * 32 + ((4 * k8 + j + (n >> 2)) & 31)];
+    *reinterpret_cast<uint4 *>(xt + ((size_t)(2 * blockIdx.x + hc) * ncp * 64) + (size_t)v * 16) =
+        make_uint4(p[0], p[1], p[2], p[3]);
   }
 }
 
@@ -468,7 +558,7 @@ GaussPlan gauss_plan(int64_t N, int d, int prec, int64_t m, bool with_y, int nsm
   int tc = 32;
   while (tc < p.ncp) tc <<= 1;
   p.tmem_cols = tc;
-  const size_t bB = (size_t)p.ncp * 128;
+  const size_t bB = (size_t)p.ncp * kBK * 2;
   int S = (int)((232448 - 2048) / (kTileA + bB));
   if (S > kMaxStages) S = kMaxStages;
   p.stages = S;
@@ -487,7 +577,7 @@ GaussPlan gauss_plan(int64_t N, int d, int prec, int64_t m, bool with_y, int nsm
   p.splits = (int)cdiv(p.nchunk, p.cps);
   p.mpad = mt * kBM;
   p.o_xt = 0;
-  p.o_part = al256((size_t)p.nchunk * bB);
+  p.o_part = al256((size_t)cdiv(N, 2 * kBK) * 2 * bB);  // the pack writes chunks in pairs
   p.total = p.o_part + al256((size_t)p.splits * p.mpad * p.ncp * 4) + 256;
   p.o_status = p.total - 256;
   return p;
@@ -534,8 +624,18 @@ cudaError_t launch_gaussian(const GaussPlan &p, int xdtype, const void *X, int64
     const int nx = p.d - c0 < w ? (p.d - c0 > 0 ? p.d - c0 : 0) : w;
     const int ycol = p.with_y && p.d >= c0 && p.d < c0 + w ? p.d - c0 : -1;
     const int ncp = (w + 15) & ~15;
-    k_pack_xt<<<(unsigned)p.nchunk, 256, 0, s>>>(static_cast<const float *>(X), ldx, static_cast<const float *>(Y),
-                                                 p.N, c0, nx, ycol, ncp, xt);
+    const bool vec = ldx % 4 == 0 && reinterpret_cast<uintptr_t>(X) % 16 == 0;
+    const size_t psm = (size_t)ncp * 128;
+    const unsigned pgrid = (unsigned)cdiv(p.N, 2 * kBK);
+    if (vec) {
+      if ((e = cudaFuncSetAttribute(k_pack_xt<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm))) return e;
+      k_pack_xt<true><<<pgrid, 256, psm, s>>>(static_cast<const float *>(X), ldx, static_cast<const float *>(Y), p.N,
+                                             c0, nx, ycol, ncp, xt);
+    } else {
+      if ((e = cudaFuncSetAttribute(k_pack_xt<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm))) return e;
+      k_pack_xt<false><<<pgrid, 256, psm, s>>>(static_cast<const float *>(X), ldx, static_cast<const float *>(Y), p.N,
+                                              c0, nx, ycol, ncp, xt);
+    }
     if ((e = cudaGetLastError())) return e;
     TcArgs a{};
     a.xt = xt; a.part = part; a.status = status; a.nchunk = p.nchunk; a.cps = p.cps; a.m = p.m; a.ncp = ncp;
