@@ -269,6 +269,15 @@ double slse_ai_bound(double omega, int64_t m_prev, int64_t m_i, int32_t d);
 
 const char *slse_status_string(int32_t status);
 
+/* Fault injection for tests (no paper counterpart).  Sets how many polls a grid-wide wait of
+ * the library (the grid barrier of the FP64 Householder QR, slse_qr and the FP64 fit) makes
+ * before it gives up; the call then reports SLSE_ETIMEOUT and every CTA of the grid stops at
+ * that barrier or the next.  polls <= 0 restores the built-in limit (2^25 polls, about a
+ * second).  Process-wide; takes effect for calls started afterwards.  Returns the previous
+ * setting (0 = built-in).  The mbarrier waits of the tensor-core kernel keep their own fixed
+ * time limit. */
+int64_t slse_debug_spin_limit(int64_t polls);
+
 /* Library version: major*10000 + minor*100 + patch. */
 int32_t slse_version(void);
 

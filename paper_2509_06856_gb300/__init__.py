@@ -97,11 +97,13 @@ _lib.slse_ai_bound.argtypes = [ctypes.c_double, _i64, _i64, _i32]
 _lib.slse_status_string.restype = ctypes.c_char_p
 _lib.slse_status_string.argtypes = [_i32]
 _lib.slse_version.restype = _i32
+_lib.slse_debug_spin_limit.restype = _i64
+_lib.slse_debug_spin_limit.argtypes = [_i64]
 
 EXPORTED = ["slse_workspace_size", "slse_fit", "slse_sketch", "slse_grad", "slse_grad_noalloc", "slse_draws", "slse_qr",
             "slse_default_schedule", "slse_default_schedule_for", "slse_ai_bound", "slse_status_string",
             "slse_version", "slse_solve_normal", "slse_solve_normal_workspace", "slse_ols_vjp",
-            "slse_tuning_schedule"]
+            "slse_tuning_schedule", "slse_debug_spin_limit"]
 
 
 class SlseError(RuntimeError):
@@ -112,6 +114,12 @@ class SlseError(RuntimeError):
 
 def status_string(s: int) -> str:
     return _lib.slse_status_string(s).decode()
+
+
+def debug_spin_limit(polls: int) -> int:
+    """slse_debug_spin_limit: fault injection for tests; sets the polls a grid-wide wait makes
+    before giving up with ETIMEOUT (<= 0 restores the built-in limit); returns the previous value."""
+    return int(_lib.slse_debug_spin_limit(int(polls)))
 
 
 def version() -> int:

@@ -1,6 +1,7 @@
 // C ABI of the SLSE-FRS library: argument validation, workspace layout, and the
 // host-side stage loop of Algorithm 2 (paper Sec. 3).  All arithmetic runs in the
 // kernels of draws.cu, srht.cu, grad.cu and linalg.cu.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -19,6 +20,11 @@ bool slse::is_host_pointer(const void *ptr) {
   }
   return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
 }
+
+namespace {
+std::atomic<long long> g_spin_limit{0};
+}
+long long slse::debug_spin_limit() { return g_spin_limit.load(std::memory_order_relaxed); }
 
 bool slse::valid_problem(const slse_problem *p) {
   if (!p || !p->X || !p->Y) return false;
@@ -237,10 +243,11 @@ size_t grad_ws(const slse_problem *p, int nsm) {
 }
 
 // ------------------------------------------------------------------ helpers
-__global__ void k_init_state(DevState *st, int rebase) {
+__global__ void k_init_state(DevState *st, int rebase, long long spin_limit) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     DevState z = {};
     z.rebase = rebase;
+    z.spin_limit = spin_limit;
     *st = z;
   }
 }
@@ -421,7 +428,7 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     prob.Y = yd;
     prob.ldx = d;
   }
-  k_init_state<<<1, 32, 0, st>>>(dst, 0);
+  k_init_state<<<1, 32, 0, st>>>(dst, 0, debug_spin_limit());
   CK(cudaGetLastError());
   ++kernels;
   const size_t eu = elem_bytes_u(s.prec);
@@ -797,7 +804,7 @@ slse_status slse_grad(const slse_problem *prob, const double *beta, double *g_ou
   double *part = reinterpret_cast<double *>(base + kStateBytes);
   const int nb = grad_blocks(prob->N, 2 * nsm);
   const bool mixed = prec == SLSE_PREC_MIXED_BF16;
-  k_init_state<<<1, 32, 0, st>>>(dst, mixed ? 1 : 0);
+  k_init_state<<<1, 32, 0, st>>>(dst, mixed ? 1 : 0, debug_spin_limit());
   CK(cudaGetLastError());
   CK(launch_grad(mixed ? GM_MIXED : GM_F64, prob->dtype, prob->X, prob->ldx, prob->Y, prob->N, prob->d, beta, dst,
                  nullptr, nullptr, nullptr, part, nb, 0, st));
@@ -833,7 +840,7 @@ slse_status slse_qr(const double *A, int64_t r, int32_t d, int64_t lda, double *
   char *base = static_cast<char *>(W.ptr);
   DevState *dst = reinterpret_cast<DevState *>(base + o_state);
   double *Ac = reinterpret_cast<double *>(base + o_a);
-  k_init_state<<<1, 32, 0, st>>>(dst, 0);
+  k_init_state<<<1, 32, 0, st>>>(dst, 0, debug_spin_limit());
   CK(cudaGetLastError());
   CK(cudaMemcpy2DAsync(Ac, (size_t)d * 8, A, (size_t)lda * 8, (size_t)d * 8, (size_t)r, cudaMemcpyDeviceToDevice, st));
   CK(launch_qr(Ac, r, d, d, R, Hinv, base + o_qr, dst, st));
@@ -917,5 +924,9 @@ const char *slse_status_string(int32_t s) {
 }
 
 int32_t slse_version(void) { return 100; }
+
+int64_t slse_debug_spin_limit(int64_t polls) {
+  return (int64_t)g_spin_limit.exchange(polls > 0 ? (long long)polls : 0, std::memory_order_relaxed);
+}
 
 }  // extern "C"

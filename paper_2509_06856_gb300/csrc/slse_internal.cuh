@@ -28,7 +28,8 @@ struct DevState {
   unsigned bar_count;  // grid barrier (QR)
   unsigned bar_gen;
   double rel_step;     // last ||b+ - b|| / ||b+||
-  double pad[3];
+  long long spin_limit; // polls of a grid-wide wait before it gives up (0: the built-in 2^25)
+  double pad[2];
 };
 
 // ----------------------------------------------------------------------------------
@@ -82,9 +83,10 @@ __device__ __forceinline__ bool grid_barrier(DevState *st, unsigned nblocks) {
       atomicAdd(&st->bar_gen, 1u);
     } else {
       long long spins = 0;
+      const long long lim = st->spin_limit > 0 ? st->spin_limit : (1ll << 25);
       while (*genp == g) {
         if (spins > 512) __nanosleep(32);
-        if (++spins > (1ll << 25)) { atomicOr(&st->status, ST_TIMEOUT); ok = 0; break; }
+        if (++spins > lim) { atomicOr(&st->status, ST_TIMEOUT); ok = 0; break; }
         if ((spins & 255) == 0 && (((volatile unsigned *)&st->status)[0] & ST_TIMEOUT)) { ok = 0; break; }
       }
     }
@@ -98,6 +100,9 @@ __device__ __forceinline__ bool grid_barrier(DevState *st, unsigned nblocks) {
 
 // ----------------------------------------------------------------------------------
 // Host-side helpers and launchers implemented in the .cu files.
+
+// api.cu: the spin limit every new DevState starts with (slse_debug_spin_limit; 0 = built-in)
+long long debug_spin_limit();
 
 constexpr int64_t kMaxPaddedRows = int64_t(1) << 24;  // N' limit of this build
 // api.cu

@@ -139,3 +139,11 @@ def test_tuning_schedule_matches_oracle(lib):
         x = slse.tuning_schedule(N, d, kind=kind)
         y = osl.tuning_schedule(N, d, kind=kind)
         assert x.m == y.m and x.a == y.a and x.r == y.r
+
+
+def test_debug_spin_limit_set_and_restore(lib):
+    import paper_2509_06856_gb300 as slse
+    assert slse.debug_spin_limit(0) == 0
+    assert slse.debug_spin_limit(7) == 0
+    assert slse.debug_spin_limit(-3) == 7      # <= 0 restores the built-in limit
+    assert slse.debug_spin_limit(0) == 0
