@@ -7,13 +7,14 @@
 // u2 = (w div 2^16 + 1/2) 2^-16: G[i, 8q + 2j] = sqrt(-2 ln u1) cos(2 pi u2),
 // G[i, 8q + 2j + 1] = sqrt(-2 ln u1) sin(2 pi u2).
 //
-// MIXED_BF16 (X F32): X is packed once into BF16 chunks of 64 rows laid out as the K-major
+// MIXED_BF16 (X F32): X is packed once into BF16 chunks of 32 rows laid out as the K-major
 // operand of tcgen05.mma (8 x 16-byte core matrices); k_gauss_tc gives each CTA 128 rows of
-// G and a range of chunks.  Eight producer warps draw the G tile in FP32 (hardware log2,
-// sin, cos, rsqrt), round it to BF16 and store it in the same layout; one thread copies the
-// X chunk with cp.async.bulk; one thread issues the 128 x ncp x 64 MMAs into an FP32
-// accumulator in tensor memory; four warps read it back (tcgen05.ld) into per-split
-// partial sums, which k_gauss_reduce adds in a fixed order.
+// G and a range of chunks, in a pipeline of up to 8 stages.  Sixteen producer warps draw the
+// G tile in FP32 (hardware log2, sin, cos, rsqrt; the Philox words of the next chunk are drawn
+// beside the Box-Muller step of the current one), round it to BF16 and store it in the same
+// layout; one thread copies the X chunk with cp.async.bulk; one thread issues the
+// 128 x ncp x 32 MMAs into an FP32 accumulator in tensor memory; four warps read it back
+// (tcgen05.ld) into per-split partial sums, which k_gauss_reduce adds in a fixed order.
 // FP64: the same entries in double precision (log, sincospi) and an FP64 CUDA-core product.
 #include "slse_internal.cuh"
 
