@@ -189,7 +189,7 @@ FitLayout fit_layout(const slse_problem *p, const Sched &s, int nsm) {
   L.o_R = w.take((size_t)d * d * 8);
   L.o_Hinv = w.take((size_t)d * d * 8);
   L.o_qr = w.take(qr_ws_bytes(s.r, d, nsm > 0 ? nsm : 152));
-  L.o_chol = w.take(s.prec != SLSE_PREC_FP64 ? chol_ws_bytes(s.r, d) : 0);
+  L.o_chol = w.take(s.prec != SLSE_PREC_FP64 ? sweep_ws_bytes(s.r, d) : 0);
   L.o_part = w.take((size_t)L.nblk * d * 8);
   L.o_g = w.take((size_t)d * 8);
   L.o_ring = w.take((size_t)3 * d * 8);
@@ -251,7 +251,7 @@ __global__ void k_init_state(DevState *st, int rebase, long long spin_limit) {
     *st = z;
   }
 }
-// Clears the non-positive-pivot flag of the Cholesky route before the QR fallback; any
+// Clears the non-positive-pivot flag of the Gram-sweep route before the QR fallback; any
 // other status bit (a timeout) is kept for the final report.
 __global__ void k_clear_numeric(DevState *st) {
   if (threadIdx.x == 0 && blockIdx.x == 0) st->status &= ~ST_NUMERIC;
@@ -476,7 +476,7 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     }
     if (L.gauss) {
       // S-hat X = G X / sqrt(r) (Gaussian sketch, Sec. 2) in place of sampled SRHT rows:
-      // BF16 rows for the Gram-Cholesky route, FP64 rows straight into the QR input
+      // BF16 rows for the Gram-sweep route, FP64 rows straight into the QR input
       void *hout = mixed ? static_cast<void *>(base + L.o_hat16) : static_cast<void *>(A);
       const int64_t ldo = mixed ? L.ld16 : d;
       if (mixed) CK(cudaMemsetAsync(hout, 0, (size_t)s.r * L.ld16 * 2, st));
@@ -488,9 +488,10 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
   CK(cudaEventRecord(e_sketch, st));
   // sketch scales: SRHT S_i X = sqrt(N'/m_i) U[rows], S-hat X = sqrt(N'/r) U[h0 ..]; CountSketch: 1
   auto sq_scale = [&](int64_t m) { return L.cs ? 1.0 : (double)L.Np / (double)m; };
-  // a5: R of S-hat X = sqrt(N'/r) U[h0 : h0 + r], then H-hat^{-1} = R^{-1} R^{-T}.  FP64 path:
-  // Householder QR.  Mixed path: FP64 Cholesky of the exactly accumulated Gram matrix of the
-  // BF16 rows (the same R), with the Householder QR as fallback on a non-positive pivot.
+  // a5: H-hat^{-1} = R^{-1} R^{-T} for the R of S-hat X = sqrt(N'/r) U[h0 : h0 + r].  FP64 path:
+  // Householder QR, then R^{-1} and H-hat^{-1}.  Mixed path: the same matrix as the inverse of
+  // the exactly accumulated Gram matrix R^T R of the BF16 rows, by the blocked sweep operator
+  // in FP64, with the Householder QR as fallback on a non-positive pivot.
   bool use_qr = !mixed;
   // the Hessian-sketch rows as BF16 (the FP8 form is widened exactly)
   const void *Uh = U;
@@ -509,9 +510,9 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     Uh = h16; ldh = L.ld16; h0 = 0;
   }
   if (mixed) {
-    CK(launch_gram_chol(Uh, ldh, h0, s.r, d, hat_scale2, R, Hinv, base + L.o_chol, dst, st));
-    const int nt = (d + 31) / 32;
-    kernels += 2 + 3 * nt + 2;
+    CK(launch_gram_sweep(Uh, ldh, h0, s.r, d, hat_scale2, Hinv, base + L.o_chol, dst, st));
+    const int nb = (d + 31) / 32;
+    kernels += 3 + 2 * nb;
     DevState *mb = t_mailbox.get();
     if (!mb) return SLSE_ECUDA;
     CK(cudaMemcpyAsync(&mb[3], dst, sizeof(DevState), cudaMemcpyDeviceToHost, st));

@@ -201,12 +201,18 @@ __global__ void __launch_bounds__(256) k_form_hinv(const double *Rinv, int d, do
   }
 }
 
-// ---------------------------------------------------------------- Gram + Cholesky route
-// For the BF16 Hessian sketch (mixed path) R is obtained as the Cholesky factor of
-// G = (S-hat X)^T (S-hat X) (the R of a Householder QR with non-negative diagonal is the
-// same matrix).  G is accumulated from exact FP32 products of the BF16 entries with a
-// two-word (TwoSum) accumulator per entry, split over row ranges, and summed in FP64 in a
-// fixed order; the factorisation is FP64.
+// ---------------------------------------------------------------- Gram + sweep route
+// For the BF16 Hessian sketch (mixed path) H-hat^{-1} is formed directly from
+// G = (S-hat X)^T (S-hat X), which equals R^T R for the R of a Householder QR of S-hat X.
+// G is accumulated from exact FP32 products of the BF16 entries with a two-word (TwoSum)
+// accumulator per entry, split over row ranges, and summed in FP64 in a fixed order.
+// G^{-1} then comes from the sweep operator (Goodnight 1979) applied block by block in FP64:
+// sweeping the diagonal block P = A_kk of a symmetric matrix A gives
+//   A_kk <- -P^{-1},  A_ik <- A_ik P^{-1},  A_kj <- P^{-1} A_kj,  A_ij <- A_ij - A_ik P^{-1} A_kj,
+// and sweeping every block leaves -G^{-1}.  Each pivot P is a Schur complement of the
+// positive definite G, hence positive definite; a non-positive scalar pivot inside it
+// raises ST_NUMERIC (the caller then takes the Householder QR of the rows).  Rows and
+// columns past d are padded with the identity.
 
 constexpr int kTile = 32;
 
@@ -253,151 +259,144 @@ __global__ void __launch_bounds__(256) k_gram_bf16(const __nv_bfloat16 *U, int64
   }
 }
 
-// G[i][k] = G[k][i] = scale * sum_s part[s][i][k] for i <= k.
-__global__ void k_gram_reduce(const double *part, int ksplit, int d, double scale, double *G) {
+// A (dp x dp, dp = d rounded up to 32): A[i][k] = A[k][i] = scale * sum_s part[s][i][k] for
+// i <= k < d, the identity outside the d x d block.
+__global__ void k_sweep_load(const double *part, int ksplit, int d, int dp, double scale, double *A) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (int64_t)d * d) return;
-  const int i = (int)(e / d), k = (int)(e % d);
-  if (k < i) return;
-  double s = 0.0;
-  for (int sp = 0; sp < ksplit; ++sp) s += part[((size_t)sp * d + i) * d + k];
-  G[(size_t)i * d + k] = scale * s;
-  G[(size_t)k * d + i] = scale * s;
+  if (e >= (int64_t)dp * dp) return;
+  const int i = (int)(e / dp), k = (int)(e % dp);
+  double v;
+  if (i < d && k < d) {
+    const int a = i < k ? i : k, b = i < k ? k : i;
+    double s = 0.0;
+    for (int sp = 0; sp < ksplit; ++sp) s += part[((size_t)sp * d + a) * d + b];
+    v = scale * s;
+  } else {
+    v = i == k ? 1.0 : 0.0;
+  }
+  A[e] = v;
 }
 
-// Diagonal block [k0, k0+nb) of the right-looking blocked Cholesky (lower, in place), and
-// the inverse of that block for the panel solve.  Four warps (one per SM sub-partition:
-// a warp's FP64 instruction occupies its sub-partition's FP64 pipe for many cycles on this
-// part, so the work is spread over all four).  Lane i holds row i; warp w holds columns
-// l = w + 4t (t < 8) in registers.  Step j: the owner of column j takes the pivot (rsqrt),
-// scales the column and publishes it in shared memory; after one barrier every warp
-// updates its columns l > j.  The inverse is formed by a column sweep with the same split.
-// Rows past d are identity rows; a non-positive pivot raises ST_NUMERIC.
-__global__ void __launch_bounds__(128) k_potrf(double *A, int d, int k0, double *Linv, DevState *st) {
-  __shared__ double s_col[kTile][kTile + 1];  // s_col[j][i] = L[i][j]
-  __shared__ double s_rinv[kTile];
+// 1 / v from the FP32 reciprocal refined by one FP64 Newton step (relative error ~2^-46),
+// the exact quotient when v is outside the FP32 range.
+__device__ __forceinline__ double recip_fast(double v) {
+  const float f = (float)v;
+  if (!(fabsf(f) > 0x1p-120f) || !(fabsf(f) < 0x1p120f)) return 1.0 / v;
+  const double x0 = (double)__frcp_rn(f);
+  return fma(x0, fma(-v, x0, 1.0), x0);
+}
+
+// Pivot step k, CTA (b, q4): sweeps its own copy of P = A_kk (32 scalar sweeps in shared
+// memory) into S = -P^{-1}; CTA (k, q4) stores columns 8 q4 .. 8 q4 + 7 of S in W_k, every
+// other CTA the same columns of C_b = A_bk (the column block before the step) and of
+// W_b = A_bk P^{-1} = -A_bk S.  Only the lower triangle of A is kept: A_bk for b < k is read
+// as (A_kb)^T.  In the sweep, thread t owns entries (t div 8, t mod 8 + 8q), q < 4; the
+// thread that writes the next pivot also forms its reciprocal.
+__global__ void __launch_bounds__(256) k_sweep_pivot(const double *A, int dp, int k, double *W, double *C,
+                                                     DevState *st) {
+  __shared__ double P[kTile][kTile + 1];
+  __shared__ double T[kTile][kTile + 1];
+  __shared__ double s_inv[2];
   __shared__ int s_bad;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int nb = min(kTile, d - k0);
-  constexpr int TC = kTile / 4;  // columns per warp
-  double a[TC];
-#pragma unroll
-  for (int t = 0; t < TC; ++t) {
-    const int l = w + 4 * t;
-    a[t] = (lane < nb && l < nb && l <= lane) ? A[(size_t)(k0 + lane) * d + k0 + l] : (l == lane ? 1.0 : 0.0);
+  const int t = threadIdx.x, b = blockIdx.x, q4 = blockIdx.y;
+  const int r = t >> 3, c0 = t & 7;
+  const double *Akk = A + (size_t)k * kTile * dp + (size_t)k * kTile;
+  for (int e = t; e < kTile * kTile; e += 256) {
+    const int er = e >> 5, ec = e & 31;
+    P[er][ec] = er >= ec ? Akk[(size_t)er * dp + ec] : Akk[(size_t)ec * dp + er];
+    if (b > k) T[er][ec] = A[(size_t)(b * kTile + er) * dp + k * kTile + ec];
+    else if (b < k) T[er][ec] = A[(size_t)(k * kTile + ec) * dp + b * kTile + er];
   }
-  if (threadIdx.x == 0) s_bad = 0;
+  if (t == 0) s_bad = 0;
   __syncthreads();
-#pragma unroll 1
+  if (t == 0) {
+    const double p0 = P[0][0];
+    if (!(p0 > 0.0)) s_bad = 1;
+    s_inv[0] = recip_fast(p0);
+  }
+  __syncthreads();
+  // One FMA per entry: v = h - f_r g_c with f_r = P[r][j]/p (r != j) or -1/p (r == j),
+  // g_c = P[j][c] (c != j) or -1 (c == j), and h = P[r][c] off row and column j, else 0;
+  // this gives P[r][c] - P[r][j] P[j][c]/p, P[j][c]/p, P[r][j]/p and -1/p in the four cases.
   for (int j = 0; j < kTile; ++j) {
-    if (w == (j & 3)) {
-      const int tj = j >> 2;
-      double aj = 0.0;
+    const double inv = s_inv[j & 1];
+    const double prj = P[r][j];
+    double g[4], h[4];
 #pragma unroll
-      for (int t = 0; t < TC; ++t)
-        if (t == tj) aj = a[t];
-      const double piv = __shfl_sync(0xffffffffu, aj, j);
-      const bool ok = piv > 0.0;
-      const double rs = ok ? rsqrt(piv) : 0.0;
-      const double lj = lane == j ? piv * rs : (lane > j ? aj * rs : 0.0);
+    for (int q = 0; q < 4; ++q) {
+      const int c = c0 + 8 * q;
+      g[q] = c == j ? -1.0 : P[j][c];
+      h[q] = (c == j || r == j) ? 0.0 : P[r][c];
+    }
+    __syncthreads();
+    const double f = r == j ? -inv : prj * inv;
 #pragma unroll
-      for (int t = 0; t < TC; ++t)
-        if (t == tj) a[t] = lj;
-      s_col[j][lane] = lj;
-      if (lane == 0) {
-        s_rinv[j] = rs;
-        if (!ok) s_bad = 1;
+    for (int q = 0; q < 4; ++q) {
+      const int c = c0 + 8 * q;
+      const double v = fma(-f, g[q], h[q]);
+      P[r][c] = v;
+      if (r == j + 1 && c == j + 1) {  // the next pivot
+        if (!(v > 0.0)) s_bad = 1;
+        s_inv[(j + 1) & 1] = recip_fast(v);
       }
     }
     __syncthreads();
-    if (s_bad) {
-      if (threadIdx.x == 0) atomicOr(&st->status, ST_NUMERIC);
-      return;
-    }
-    const double lij = s_col[j][lane];
-#pragma unroll
-    for (int t = 0; t < TC; ++t) {
-      const int l = w + 4 * t;
-      if (l > j) a[t] = fma(-lij, s_col[j][l], a[t]);
-    }
   }
-  // L back to A (lower triangle of the block)
-  if (lane < nb) {
-#pragma unroll
-    for (int t = 0; t < TC; ++t) {
-      const int l = w + 4 * t;
-      if (l < nb) A[(size_t)(k0 + lane) * d + k0 + l] = l <= lane ? a[t] : 0.0;
-    }
+  if (s_bad && t == 0 && q4 == 0) atomicOr(&st->status, ST_NUMERIC);
+  // columns 8 q4 .. 8 q4 + 7: one output per thread
+  const int c = 8 * q4 + c0;
+  double *Wb = W + (size_t)b * kTile * kTile;
+  if (b == k) {
+    Wb[r * kTile + c] = P[r][c];
+    return;
   }
-  // L^{-1}: column c = w + 4t of the inverse in x[t] (lane = row); sweep i = 0..31:
-  // x_i <- x_i / L_ii, then x_r <- x_r - L_ri x_i for r > i
-  double x[TC];
-#pragma unroll
-  for (int t = 0; t < TC; ++t) x[t] = (lane == w + 4 * t) ? 1.0 : 0.0;
-#pragma unroll 1
-  for (int i = 0; i < kTile; ++i) {
-    const double rinv = s_rinv[i], lri = s_col[i][lane];
-#pragma unroll
-    for (int t = 0; t < TC; ++t) {
-      const double xi = __shfl_sync(0xffffffffu, x[t], i) * rinv;
-      x[t] = lane == i ? xi : (lane > i ? fma(-lri, xi, x[t]) : x[t]);
-    }
-  }
-  if (lane < nb) {
-#pragma unroll
-    for (int t = 0; t < TC; ++t) {
-      const int c = w + 4 * t;
-      if (c < nb) Linv[lane * kTile + c] = lane >= c ? x[t] : 0.0;
-    }
-  }
+  double acc = 0.0;
+#pragma unroll 8
+  for (int l = 0; l < kTile; ++l) acc = fma(T[r][l], P[l][c], acc);
+  Wb[r * kTile + c] = -acc;
+  C[(size_t)b * kTile * kTile + r * kTile + c] = T[r][c];
 }
 
-// Panel below the diagonal block: A[i0:i0+8, k0:k0+nb] <- A * Linv^T, 8 rows per CTA (one
-// output per thread) so that the FP64 work spreads over many SMs.
-__global__ void __launch_bounds__(256) k_trsm(double *A, int d, int k0, const double *Linv) {
-  __shared__ double P[8][kTile + 1], T[kTile][kTile + 1];
-  const int nb = min(kTile, d - k0);
-  const int i0 = k0 + kTile + 8 * blockIdx.x;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  P[ty][tx] = (i0 + ty < d && tx < nb) ? A[(size_t)(i0 + ty) * d + k0 + tx] : 0.0;
-  for (int rr = ty; rr < kTile; rr += 8) T[rr][tx] = (rr < nb && tx < nb) ? Linv[rr * kTile + tx] : 0.0;
+// Update of lower tile (i, j), i >= j, for pivot step k (tile index from the linear block id):
+//   (k, k): -P^{-1};  (i, k): W_i;  (k, j): W_j^T;  otherwise A_ij - W_i C_j^T.
+__global__ void __launch_bounds__(256) k_sweep_update(double *A, int dp, int k, const double *W, const double *C) {
+  __shared__ double Ws[kTile][kTile + 1], Cs[kTile][kTile + 1];
+  int i = 0, rem = blockIdx.x;
+  while (rem > i) { rem -= i + 1; ++i; }
+  const int j = rem;
+  const int t = threadIdx.x, r = t >> 3, c0 = t & 7;
+  double *Aij = A + (size_t)i * kTile * dp + (size_t)j * kTile;
+  if (i == k || j == k) {
+    const double *src = W + (size_t)(j == k ? i : j) * kTile * kTile;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = c0 + 8 * q;
+      Aij[(size_t)r * dp + c] = j == k ? src[r * kTile + c] : src[c * kTile + r];
+    }
+    return;
+  }
+  const double *Wi = W + (size_t)i * kTile * kTile, *Cj = C + (size_t)j * kTile * kTile;
+  for (int e = t; e < kTile * kTile; e += 256) {
+    Ws[e >> 5][e & 31] = Wi[e];
+    Cs[e >> 5][e & 31] = Cj[e];
+  }
   __syncthreads();
-  double s = 0.0;
 #pragma unroll
-  for (int l = 0; l < kTile; ++l) s = fma(P[ty][l], T[tx][l], s);  // (P Linv^T)[ty][tx]
-  if (i0 + ty < d && tx < nb) A[(size_t)(i0 + ty) * d + k0 + tx] = s;
-}
-
-// Trailing update of the lower triangle: A[rows, cols] -= L[rows, k] L[cols, k]^T for the
-// 8-row slice blockIdx.y of the trailing part against the 32-column block blockIdx.x
-// (lower triangle only), one output per thread.
-__global__ void __launch_bounds__(256) k_syrk(double *A, int d, int k0) {
-  __shared__ double Li[8][kTile + 1], Lj[kTile][kTile + 1];
-  const int nb = min(kTile, d - k0);
-  const int base = k0 + kTile;
-  const int i0 = base + 8 * blockIdx.y, j0 = base + kTile * blockIdx.x;
-  if (j0 > i0 + 7) return;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  Li[ty][tx] = (i0 + ty < d && tx < nb) ? A[(size_t)(i0 + ty) * d + k0 + tx] : 0.0;
-  for (int rr = ty; rr < kTile; rr += 8) Lj[rr][tx] = (j0 + rr < d && tx < nb) ? A[(size_t)(j0 + rr) * d + k0 + tx] : 0.0;
-  __syncthreads();
-  const int gi = i0 + ty, gj = j0 + tx;
-  if (gi < d && gj < d && gj <= gi) {
-    double s = 0.0;
-#pragma unroll
-    for (int l = 0; l < kTile; ++l) s = fma(Li[ty][l], Lj[tx][l], s);
-    A[(size_t)gi * d + gj] -= s;
+  for (int q = 0; q < 4; ++q) {
+    const int c = c0 + 8 * q;
+    double acc = Aij[(size_t)r * dp + c];
+#pragma unroll 8
+    for (int l = 0; l < kTile; ++l) acc = fma(-Ws[r][l], Cs[c][l], acc);
+    Aij[(size_t)r * dp + c] = acc;
   }
 }
 
-// R = L^T (upper, positive diagonal) and Rt = L (lower with zeros above).
-__global__ void k_chol_to_r(const double *A, int d, double *R, double *Rt) {
+// Hinv = -G^{-1} read from the lower triangle of the swept matrix (leading d x d block).
+__global__ void k_sweep_final(const double *A, int d, int dp, double *Hinv) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)d * d) return;
   const int i = (int)(e / d), k = (int)(e % d);
-  const double l = k <= i ? A[e] : 0.0;  // L[i][k]
-  Rt[e] = l;
-  R[(size_t)k * d + i] = l;
+  Hinv[e] = i >= k ? -A[(size_t)i * dp + k] : -A[(size_t)k * dp + i];
 }
 
 template <class T> __device__ __forceinline__ double to_d(T v) { return (double)v; }
@@ -486,44 +485,33 @@ cudaError_t launch_qr(double *A, int64_t r, int d, int64_t lda, double *R, doubl
   return cudaGetLastError();
 }
 
-size_t chol_ws_bytes(int64_t r, int d) {
+size_t sweep_ws_bytes(int64_t r, int d) {
   const int ksplit = (int)((r + 255) / 256 < 8 ? (r + 255) / 256 : 8);
-  return align256((size_t)(ksplit > 0 ? ksplit : 1) * d * d * 8) + align256((size_t)d * d * 8) +
-         align256((size_t)kTile * kTile * 8) + 2 * align256((size_t)d * d * 8);
+  const size_t dp = (size_t)(d + kTile - 1) / kTile * kTile;
+  return align256((size_t)(ksplit > 0 ? ksplit : 1) * d * d * 8) + align256(dp * dp * 8) + 2 * align256(dp * kTile * 8);
 }
 
-cudaError_t launch_gram_chol(const void *U, int64_t ldu, int64_t row0, int64_t r, int d, double scale2, double *R,
-                             double *Hinv, void *ws, DevState *st, cudaStream_t s) {
+cudaError_t launch_gram_sweep(const void *U, int64_t ldu, int64_t row0, int64_t r, int d, double scale2,
+                              double *Hinv, void *ws, DevState *st, cudaStream_t s) {
   int ksplit = (int)((r + 255) / 256);
   if (ksplit > 8) ksplit = 8;
   if (ksplit < 1) ksplit = 1;
+  const int nb = (d + kTile - 1) / kTile, dp = nb * kTile;
   char *p = static_cast<char *>(ws);
   size_t off = 0;
   double *part = reinterpret_cast<double *>(p + off); off += align256((size_t)ksplit * d * d * 8);
-  double *G = reinterpret_cast<double *>(p + off); off += align256((size_t)d * d * 8);
-  double *Linv = reinterpret_cast<double *>(p + off); off += align256((size_t)kTile * kTile * 8);
-  double *Rinv = reinterpret_cast<double *>(p + off); off += align256((size_t)d * d * 8);
-  double *Rt = reinterpret_cast<double *>(p + off); off += align256((size_t)d * d * 8);
-  const int nt = (d + kTile - 1) / kTile;
-  k_gram_bf16<<<dim3(nt, nt, ksplit), 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(U), ldu, row0, r, d, ksplit, part);
+  double *A = reinterpret_cast<double *>(p + off); off += align256((size_t)dp * dp * 8);
+  double *W = reinterpret_cast<double *>(p + off); off += align256((size_t)dp * kTile * 8);
+  double *C = reinterpret_cast<double *>(p + off);
+  k_gram_bf16<<<dim3(nb, nb, ksplit), 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(U), ldu, row0, r, d, ksplit, part);
+  const int64_t ee = (int64_t)dp * dp;
+  k_sweep_load<<<(unsigned)((ee + 255) / 256), 256, 0, s>>>(part, ksplit, d, dp, scale2, A);
+  for (int k = 0; k < nb; ++k) {
+    k_sweep_pivot<<<dim3(nb, 4), 256, 0, s>>>(A, dp, k, W, C, st);
+    k_sweep_update<<<nb * (nb + 1) / 2, 256, 0, s>>>(A, dp, k, W, C);
+  }
   const int64_t dd = (int64_t)d * d;
-  k_gram_reduce<<<(unsigned)((dd + 255) / 256), 256, 0, s>>>(part, ksplit, d, scale2, G);
-  for (int kb = 0; kb < nt; ++kb) {
-    const int k0 = kb * kTile;
-    k_potrf<<<1, 128, 0, s>>>(G, d, k0, Linv, st);
-    const int below = nt - kb - 1;
-    if (below > 0) {
-      const int rows = d - k0 - kTile;  // rows below the diagonal block
-      const int slices = (rows + 7) / 8;
-      k_trsm<<<slices, 256, 0, s>>>(G, d, k0, Linv);
-      k_syrk<<<dim3(below, slices), 256, 0, s>>>(G, d, k0);
-    }
-  }
-  k_chol_to_r<<<(unsigned)((dd + 255) / 256), 256, 0, s>>>(G, d, R, Rt);
-  if (Hinv) {
-    k_tri_inv_sweep<<<(d + 7) / 8, 256, 0, s>>>(R, Rt, d, Rinv, st);
-    k_form_hinv<<<dim3(nt, nt), 256, 0, s>>>(Rinv, d, Hinv);
-  }
+  k_sweep_final<<<(unsigned)((dd + 255) / 256), 256, 0, s>>>(A, d, dp, Hinv);
   return cudaGetLastError();
 }
 

@@ -222,10 +222,11 @@ cudaError_t launch_gather_hessian_rows(int prec, const void *U, int64_t ldu, int
                                        int d, double scale, double *A, cudaStream_t s);
 cudaError_t launch_qr(double *A, int64_t r, int d, int64_t lda, double *R, double *Hinv, void *ws,
                       DevState *st, cudaStream_t s);
-// Mixed path: R from the FP64 Cholesky factor of G = scale2 * U[row0:row0+r]^T U[row0:row0+r]
-// (U in BF16), H-hat^{-1} = R^{-1} R^{-T}.  A non-positive pivot raises ST_NUMERIC.
-size_t chol_ws_bytes(int64_t r, int d);
-cudaError_t launch_gram_chol(const void *U, int64_t ldu, int64_t row0, int64_t r, int d, double scale2, double *R,
-                             double *Hinv, void *ws, DevState *st, cudaStream_t s);
+// Mixed path: H-hat^{-1} = G^{-1} for G = scale2 * U[row0:row0+r]^T U[row0:row0+r] (U in BF16,
+// G accumulated exactly), by the blocked sweep operator in FP64.  A non-positive pivot
+// raises ST_NUMERIC (the caller then takes the Householder QR).
+size_t sweep_ws_bytes(int64_t r, int d);
+cudaError_t launch_gram_sweep(const void *U, int64_t ldu, int64_t row0, int64_t r, int d, double scale2, double *Hinv,
+                              void *ws, DevState *st, cudaStream_t s);
 
 }  // namespace slse

@@ -1,7 +1,8 @@
 """GPU parity of the mixed path's Hessian factor: the H-hat^{-1} that slse_fit uses (exported
 through slse_trace.hinv_out) against the oracle's (R^T R)^{-1} from a Householder QR of the
 same BF16 sketch rows, scaled by sqrt(N'/r) (Appendix, implementation details).  The GPU forms
-R by an FP64 Cholesky factorisation of the exactly accumulated Gram matrix."""
+it as the inverse of the exactly accumulated Gram matrix R^T R by the blocked sweep operator
+in FP64."""
 import numpy as np
 import pytest
 
