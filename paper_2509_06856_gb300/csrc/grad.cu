@@ -439,10 +439,19 @@ __global__ void k_reduce(const double *partials, int nblk, int d, double scale, 
   if (check_done && st->done) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = blockIdx.x * 32 + lane;
-  double s = 0.0;
-  if (c < d)
-    for (int b = warp; b < nblk; b += 8) s += partials[(size_t)b * d + c];
-  sm[warp][lane] = s;
+  // four independent sums over CTAs warp, warp + 8, ... (loads overlap), combined in a fixed order
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  if (c < d) {
+    int b = warp;
+    for (; b + 24 < nblk; b += 32) {
+      s0 += partials[(size_t)b * d + c];
+      s1 += partials[(size_t)(b + 8) * d + c];
+      s2 += partials[(size_t)(b + 16) * d + c];
+      s3 += partials[(size_t)(b + 24) * d + c];
+    }
+    for (; b < nblk; b += 8) s0 += partials[(size_t)b * d + c];
+  }
+  sm[warp][lane] = (s0 + s1) + (s2 + s3);
   __syncthreads();
   if (warp == 0 && c < d) {
     double t = 0.0;
@@ -473,9 +482,17 @@ __global__ void __launch_bounds__(256) k_update(const UpdArgs A, DevState *st) {
   double ds = 0.0, nn = 0.0, dd = 0.0;
   if (i < d) {
     const double *Hrow = a.Hinv + (size_t)i * d;
-    double h = 0.0;
-    for (int k = lane; k < d; k += 32) h = fma(Hrow[k], a.g[k], h);
-    h = warp_sum(h);
+    // four independent partial sums (the FP64 FMA latency is long on this part), fixed order
+    double h0 = 0.0, h1 = 0.0, h2 = 0.0, h3 = 0.0;
+    int k = lane;
+    for (; k + 96 < d; k += 128) {
+      h0 = fma(Hrow[k], a.g[k], h0);
+      h1 = fma(Hrow[k + 32], a.g[k + 32], h1);
+      h2 = fma(Hrow[k + 64], a.g[k + 64], h2);
+      h3 = fma(Hrow[k + 96], a.g[k + 96], h3);
+    }
+    for (; k < d; k += 32) h0 = fma(Hrow[k], a.g[k], h0);
+    double h = warp_sum((h0 + h1) + (h2 + h3));
     if (lane == 0) {
       const double mom = a.first ? 0.0 : a.eta * (b[i] - bp[i]);
       const double v = b[i] + a.mu * h + mom;
@@ -503,14 +520,20 @@ __global__ void __launch_bounds__(256) k_update(const UpdArgs A, DevState *st) {
     s_last = (prev == gridDim.x - 1);
   }
   __syncthreads();
-  if (!s_last || threadIdx.x != 0) return;
+  if (!s_last || warp != 0) return;
   __threadfence();
+  // the last CTA sums the per-CTA partials with its first warp: lane l takes CTAs l, l + 32, ...
+  // in order, then a fixed shuffle tree (no serial chain of L2 round trips)
   double x0 = 0, x1 = 0, x2 = 0;
-  for (unsigned c = 0; c < gridDim.x; ++c) {
+  for (unsigned c = lane; c < gridDim.x; c += 32) {
     x0 += __ldcg(A.part + 3 * c + 0);
     x1 += __ldcg(A.part + 3 * c + 1);
     x2 += __ldcg(A.part + 3 * c + 2);
   }
+  x0 = warp_sum(x0);
+  x1 = warp_sum(x1);
+  x2 = warp_sum(x2);
+  if (lane != 0) return;
   st->upd_count = 0;
   const double rel = sqrt(x0) / (sqrt(x1) > 0.0 ? sqrt(x1) : 1.0);
   st->rel_step = rel;
