@@ -31,7 +31,7 @@
  *   deterministic estimate (all reductions have a fixed order).
  * - Gradient sign: g = X^T (Y - X beta), i.e. minus the paper's
  *   nabla f = X^T (X beta - Y) (Sec. 1); the M-IHS step adds mu H-hat^{-1} g.
- * - Kernel limits of this build: 1 <= d <= 512, d <= N, N' = 2^ceil(log2 N) <= 2^24.
+ * - Limits of the library: 1 <= d <= 512, d <= N, N' = 2^ceil(log2 N) <= 2^24.
  */
 #ifndef SLSE_H
 #define SLSE_H

@@ -9,7 +9,7 @@ costs O(N d): row k of X is added, with its sign, to row h(k) of S X.  Because e
 column of S has unit norm and distinct columns are orthogonal in expectation,
 E[S^T S] = I_N, so no scale factor is applied (unlike the sqrt(N/m) of the SRHT).
 
-Readings taken where the paper is silent (listed in the design doc):
+Readings taken where the paper is silent:
 * Rows are not padded: k ranges over [0, N).
 * Hash and sign of row k from Philox4x32-10 (``oracle.philox``) stream 3, counter k:
   h(k) = w0 (a uniform 32-bit word), s(k) = -1 if bit 0 of w1 is set, else +1.

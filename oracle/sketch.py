@@ -8,7 +8,7 @@ Sec. 3 (construction of the nested sketches, Algorithm 2): the full transform
 of its rows, scaled by sqrt(N/m_i); the rows of S_i are a subset of those of
 S_{i+1}.
 
-Readings taken where the paper leaves freedom (listed in the design doc):
+Readings taken where the paper leaves freedom:
 * N is padded with zero rows to N' = 2^ceil(log2 N); all scales use N'.
 * H is the Sylvester (natural-order) matrix H[k, j] = (-1)^popcount(k & j), and
   the 1/sqrt(N') normalisation is applied once, after the transform.

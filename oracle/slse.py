@@ -20,7 +20,7 @@
   the SRHT subproblems and takes S-hat X from the r x N Gaussian sketch of
   ``oracle.gaussian`` (Sec. 2) instead of the sampled SRHT rows.
 
-Readings taken where the paper is silent (listed in the design doc):
+Readings taken where the paper is silent:
 * beta_0 = 0 (Thm 4.2 allows any beta_0).
 * Momentum follows the listing of Algorithm 2: one global iteration counter t, so
   beta_{t-1} carries across subproblems and into the 2nd stage (default).

@@ -104,7 +104,7 @@ __device__ __forceinline__ bool grid_barrier(DevState *st, unsigned nblocks) {
 // api.cu: the spin limit every new DevState starts with (slse_debug_spin_limit; 0 = built-in)
 long long debug_spin_limit();
 
-constexpr int64_t kMaxPaddedRows = int64_t(1) << 24;  // N' limit of this build
+constexpr int64_t kMaxPaddedRows = int64_t(1) << 24;  // largest padded row count N' the library accepts
 // api.cu
 bool is_host_pointer(const void *ptr);
 bool valid_problem(const slse_problem *p);

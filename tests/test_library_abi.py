@@ -64,7 +64,7 @@ def test_invalid_arguments_rejected_before_any_launch(lib):
         slse.CProblem(3, 4, slse.F64, 1, 4, 1),        # d > N
         slse.CProblem(10, 4, 7, 1, 4, 1),              # bad dtype
         slse.CProblem(10, 4, slse.F64, None, 4, 1),    # null X
-        slse.CProblem(10, 600, slse.F64, 1, 600, 1),   # d above this build's limit
+        slse.CProblem(10, 600, slse.F64, 1, 600, 1),   # d above the library's limit
         slse.CProblem((1 << 24) + 1, 4, slse.F64, 1, 4, 1),  # N' above 2^24
     ]
     for p in bad:
