@@ -525,7 +525,7 @@ cudaError_t launch_group_t(const GroupArgs &a0, int64_t ngroups, cudaStream_t s)
 // One pass over groups of 2^L rows: the X columns by k_group, the Y column by k_ycol.
 // k_group works on 128-byte row segments (32 FP32 / 16 FP64 columns), 256 rows per CTA
 // (512 for L = 12) and clusters of up to 8 CTAs; stage A takes the top 4 row bits so
-// that 4 CTAs fit on an SM.
+// that several CTAs fit on an SM (MB per SM: the launch bound).
 template <class Tin, class Ts, class Tout, int VA, int VB, int VO, int SLAB_BYTES = 128, int MB = 4>
 cudaError_t launch_pass_t(const GroupArgs &a, int L, int64_t ngroups, cudaStream_t s) {
   constexpr int CP = SLAB_BYTES / (int)sizeof(Ts);
@@ -562,7 +562,7 @@ cudaError_t launch_small_t(const GroupArgs &a, int logn, cudaStream_t s) {
 }
 
 // Dispatch on (input type, working type, output type).
-template <class Tin, class Ts, class Tout, int C, int VA, int VB, int VO>
+template <class Tin, class Ts, class Tout, int C, int VA, int VB, int VO, int P1_SLAB = 128, int P1_MB = 4>
 cudaError_t run_plan(const SrhtPlan &pl, const void *X, int64_t ldx, const void *Y, int64_t N, int d,
                      const int32_t *Psd, const int32_t *pos, void *W, void *WY, int64_t ldw, void *U,
                      void *V, int64_t ldu, double scale, cudaStream_t s,
@@ -596,7 +596,7 @@ cudaError_t run_plan(const SrhtPlan &pl, const void *X, int64_t ldx, const void 
   a.ostride = 1; a.ogstride = n2;
   a.scale = 1.0;
   a.vec_out = vec_ok(W, ldw, sizeof(Tout), VO) ? 1 : 0;
-  cudaError_t e = launch_pass_t<Tin, Ts, Tout, VA, VB, VO>(a, pl.log2, n1, s);
+  cudaError_t e = launch_pass_t<Tin, Ts, Tout, VA, VB, VO, P1_SLAB, P1_MB>(a, pl.log2, n1, s);
   if (e != cudaSuccess) return e;
   if (ev_mid && (e = cudaEventRecord(ev_mid, s)) != cudaSuccess) return e;
   // pass 2: groups g = k2 (n2 of them), rows rho = j1 at stride n2, outputs kappa = k1
@@ -641,16 +641,18 @@ cudaError_t launch_srht(const SrhtPlan &pl, int prec, int xdtype, const void *X,
     return run_plan<float, double, double, 16, 1, 1, 2>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale, s, p2, ev_mid);
   }
   if (prec == SLSE_PREC_MIXED_BF16 && xdtype == SLSE_F32) {
-    auto p2 = &launch_pass_t<bf16, float, bf16, 2, 2, 4>;
-    return run_plan<float, float, bf16, 32, 2, 2, 4>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale, s, p2, ev_mid);
+    // five CTAs per SM in both passes (more row gathers in flight; measured against 3, 4 and 6)
+    auto p2 = &launch_pass_t<bf16, float, bf16, 2, 2, 4, 128, 5>;
+    return run_plan<float, float, bf16, 32, 2, 2, 4, 128, 5>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale,
+                                                             s, p2, ev_mid);
   }
   if (prec == SLSE_PREC_MIXED_FP8 && xdtype == SLSE_F32) {
     // pass 1 as in the BF16 form; pass 2 writes E4M3 rows with 32-column block scales
     // (single-pass sizes are handled by the caller through the BF16 form)
     if (pl.single || !Uscale) return cudaErrorInvalidValue;
     auto p2 = &launch_pass_t<bf16, float, mx8, 2, 2, 4>;
-    return run_plan<float, float, bf16, 32, 2, 2, 4>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale, s, p2,
-                                                     ev_mid, Uscale, ld_scale, hat, hat_row0, hat_ld);
+    return run_plan<float, float, bf16, 32, 2, 2, 4, 128, 5>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale,
+                                                             s, p2, ev_mid, Uscale, ld_scale, hat, hat_row0, hat_ld);
   }
   return cudaErrorInvalidValue;
 }
