@@ -95,6 +95,27 @@ __device__ __forceinline__ U4 philox_rk(uint32_t c0, uint32_t c1, uint32_t c2, u
   return U4{c0, c1, c2, c3};
 }
 
+// Two words at once: the same arithmetic as box_muller_bf16x2 with the FP32 additions and
+// multiplications in the packed two-lane instructions (the results are identical).
+__device__ __forceinline__ uint2 box_muller_bf16x2_pair(uint32_t wa, uint32_t wb) {
+  const float2 one_m = make_float2(-0.99999237060546875f, -0.99999237060546875f);
+  const float2 u1 = __fadd2_rn(make_float2(__uint_as_float(((wa << 7) & 0x007FFF80u) | 0x3F800000u),
+                                           __uint_as_float(((wb << 7) & 0x007FFF80u) | 0x3F800000u)),
+                               one_m);
+  const float2 u2 = __fadd2_rn(make_float2(__uint_as_float(((wa >> 9) & 0x007FFF80u) | 0x3F800000u),
+                                           __uint_as_float(((wb >> 9) & 0x007FFF80u) | 0x3F800000u)),
+                               one_m);
+  const float2 t = __fmul2_rn(make_float2(-1.3862943611198906f, -1.3862943611198906f),
+                              make_float2(lg2_approx(u1.x), lg2_approx(u1.y)));
+  const float2 nrad = __fmul2_rn(make_float2(-t.x, -t.y), make_float2(rsqrt_approx(t.x), rsqrt_approx(t.y)));
+  const float2 th = __ffma2_rn(u2, make_float2(6.2831853071795865f, 6.2831853071795865f),
+                               make_float2(-3.1415926535897932f, -3.1415926535897932f));
+  const float2 ca = __fmul2_rn(nrad, make_float2(cos_approx(th.x), cos_approx(th.y)));
+  const float2 sa = __fmul2_rn(nrad, make_float2(sin_approx(th.x), sin_approx(th.y)));
+  const __nv_bfloat162 ha = __floats2bfloat162_rn(ca.x, sa.x), hb = __floats2bfloat162_rn(ca.y, sa.y);
+  return make_uint2(*reinterpret_cast<const uint32_t *>(&ha), *reinterpret_cast<const uint32_t *>(&hb));
+}
+
 // ------------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -286,8 +307,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gauss_tc(const TcArgs a) {
       const U4 w = wn;
       if (k + 1 < nk) q += kBK / 8;
       wn = philox_rk((uint32_t)q, (uint32_t)(q >> 32), kStreamG, (uint32_t)gi, K);
-      uint4 v = make_uint4(box_muller_bf16x2(w.x), box_muller_bf16x2(w.y), box_muller_bf16x2(w.z),
-                           box_muller_bf16x2(w.w));
+      const uint2 v01 = box_muller_bf16x2_pair(w.x, w.y), v23 = box_muller_bf16x2_pair(w.z, w.w);
+      uint4 v = make_uint4(v01.x, v01.y, v23.x, v23.y);
       if (!live) v = make_uint4(0u, 0u, 0u, 0u);
       *reinterpret_cast<uint4 *>(dst0 + (size_t)s * kTileA) = v;
       // each thread orders its own store before the MMA's (async-proxy) read; the warp then
