@@ -46,21 +46,6 @@ __device__ __forceinline__ float cos_approx(float x) {
   return y;
 }
 
-__device__ __forceinline__ uint32_t box_muller_bf16x2(uint32_t w) {
-  // (lo + 1/2) 2^-16 exactly: the float 1 + lo 2^-16 minus (1 - 2^-17) (both in [1/2, 2]: exact)
-  const float u1 = __uint_as_float(((w << 7) & 0x007FFF80u) | 0x3F800000u) - 0.99999237060546875f;
-  const float u2 = __uint_as_float(((w >> 9) & 0x007FFF80u) | 0x3F800000u) - 0.99999237060546875f;
-  // t = -2 ln u1 >= -2 ln(1 - 2^-17) = 1.5e-5, far above the 2^-22 absolute error of lg2 near 1,
-  // so t > 0 and the reciprocal square root is finite
-  const float t = -1.3862943611198906f * lg2_approx(u1);
-  const float nrad = -t * rsqrt_approx(t);  // -sqrt(t)
-  // theta = 2 pi u2 - pi lies in (-pi, pi), where the hardware sine and cosine are accurate;
-  // cos(2 pi u2) = -cos(theta), sin(2 pi u2) = -sin(theta)
-  const float th = fmaf(u2, 6.2831853071795865f, -3.1415926535897932f);
-  const __nv_bfloat162 h = __floats2bfloat162_rn(nrad * cos_approx(th), nrad * sin_approx(th));
-  return *reinterpret_cast<const uint32_t *>(&h);
-}
-
 __device__ __forceinline__ void box_muller_f64(uint32_t w, double &a, double &b) {
   const double u1 = ((double)(w & 0xFFFFu) + 0.5) * 0x1p-16;
   const double u2 = ((double)(w >> 16) + 0.5) * 0x1p-16;
@@ -95,8 +80,13 @@ __device__ __forceinline__ U4 philox_rk(uint32_t c0, uint32_t c1, uint32_t c2, u
   return U4{c0, c1, c2, c3};
 }
 
-// Two words at once: the same arithmetic as box_muller_bf16x2 with the FP32 additions and
-// multiplications in the packed two-lane instructions (the results are identical).
+// Box-Muller pairs of two words at once, rounded to BF16 (word -> (cos entry, sin entry)),
+// with the FP32 additions and multiplications in the packed two-lane instructions:
+//   u = (h + 1/2) 2^-16 exactly, as the float 1 + h 2^-16 minus (1 - 2^-17) (both in [1/2, 2]);
+//   t = -2 ln u1 >= -2 ln(1 - 2^-17) = 1.5e-5, far above the 2^-22 absolute error of lg2 near 1,
+//     so t > 0 and the reciprocal square root is finite;
+//   theta = 2 pi u2 - pi lies in (-pi, pi), where the hardware sine and cosine are accurate, and
+//     cos(2 pi u2) = -cos(theta), sin(2 pi u2) = -sin(theta): the radius is carried negated.
 __device__ __forceinline__ uint2 box_muller_bf16x2_pair(uint32_t wa, uint32_t wb) {
   const float2 one_m = make_float2(-0.99999237060546875f, -0.99999237060546875f);
   const float2 u1 = __fadd2_rn(make_float2(__uint_as_float(((wa << 7) & 0x007FFF80u) | 0x3F800000u),
