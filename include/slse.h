@@ -154,7 +154,10 @@ size_t slse_workspace_size(const slse_problem *prob, const slse_schedule *sched,
  * Synchronous: returns after beta_out is written.  sched == NULL selects the paper's
  * experimental defaults (slse_default_schedule) in FP64.  With host X and Y the copy to the
  * device runs on a side stream while the random draws run on `stream`; the workspace then
- * also holds the device copy (slse_workspace_size accounts for it). */
+ * also holds the device copy (slse_workspace_size accounts for it).  Tracing: each phase's
+ * enqueue is wrapped in an NVTX range ("slse_fit: draws", "...: sketch", "...: Hessian factor",
+ * "...: stage 1", "...: stage 2"); with SLSE_LOG set in the environment every call prints a
+ * one-line summary of its phase times (CUDA events) to stderr. */
 slse_status slse_fit(const slse_problem *prob, const slse_schedule *sched, uint64_t seed,
                      double *beta_out, slse_report *report, slse_trace *trace,
                      void *workspace, size_t ws_bytes, slse_stream_t stream);

@@ -1,6 +1,8 @@
 // C ABI of the SLSE-FRS library: argument validation, workspace layout, and the
 // host-side stage loop of Algorithm 2 (paper Sec. 3).  All arithmetic runs in the
 // kernels of draws.cu, srht.cu, grad.cu and linalg.cu.
+#include <nvtx3/nvToolsExt.h>
+
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -289,6 +291,20 @@ slse_status acquire(Workspace &w, void *user, size_t user_bytes, size_t need, cu
   return SLSE_OK;
 }
 
+// NVTX range for the phase of slse_fit being enqueued (draws, sketch, Hessian factor, stage 1,
+// stage 2); the range in flight is closed on every exit path.
+struct NvtxPhase {
+  bool open = false;
+  void set(const char *name) {
+    if (open) nvtxRangePop();
+    nvtxRangePushA(name);
+    open = true;
+  }
+  ~NvtxPhase() {
+    if (open) nvtxRangePop();
+  }
+};
+
 struct Events {
   std::vector<cudaEvent_t> ev;
   cudaEvent_t make() {
@@ -403,6 +419,8 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     return cudaSuccess;
   };
 
+  NvtxPhase phase;
+  phase.set("slse_fit: draws");
   CK(cudaEventRecord(e_start, st));
   // host inputs: copy into the workspace on a side stream, overlapped with the draws
   struct SideStream {
@@ -436,6 +454,7 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     // CountSketch family (Sec. 2; SLSE-FRS-CS of Sec. 5): its hashes are drawn inside the
     // one sort-and-gather pass, so the draws phase is empty.
     CK(cudaEventRecord(e_draws, st));
+    phase.set("slse_fit: sketch");
     if (L.host_in) CK(cudaStreamWaitEvent(st, e_copied, 0));
     void *lvX[25] = {}, *lvY[25] = {};
     for (size_t i = 0; i < s.m.size(); ++i) {
@@ -456,6 +475,7 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     CK(launch_pos_map(sigma, L.Np, 0, L.n_samp, L.sp.single ? L.sp.logN : L.sp.log2, pos, st));
     kernels += 1;
     CK(cudaEventRecord(e_draws, st));
+    phase.set("slse_fit: sketch");
     if (L.host_in) CK(cudaStreamWaitEvent(st, e_copied, 0));
     // a2-a4: SRHT into the sampled rows (U = Z[sigma] with Z = H D P X / sqrt(N'); sketch scales applied later)
     __nv_bfloat16 *h16 = fp8 ? reinterpret_cast<__nv_bfloat16 *>(base + L.o_hat16) : nullptr;
@@ -486,6 +506,7 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     }
   }
   CK(cudaEventRecord(e_sketch, st));
+  phase.set("slse_fit: Hessian factor");
   // sketch scales: SRHT S_i X = sqrt(N'/m_i) U[rows], S-hat X = sqrt(N'/r) U[h0 ..]; CountSketch: 1
   auto sq_scale = [&](int64_t m) { return L.cs ? 1.0 : (double)L.Np / (double)m; };
   // a5: H-hat^{-1} = R^{-1} R^{-T} for the R of S-hat X = sqrt(N'/r) U[h0 : h0 + r].  FP64 path:
@@ -534,6 +555,7 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     kernels += 3;
   }
   CK(cudaEventRecord(e_qr, st));
+  phase.set("slse_fit: stage 1");
   if (tr && tr->hinv_out)
     CK(cudaMemcpyAsync(tr->hinv_out, Hinv, (size_t)d * d * 8, cudaMemcpyDeviceToDevice, st));
   CK(cudaMemsetAsync(ring, 0, (size_t)3 * d * 8, st));
@@ -570,6 +592,7 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
   }
   const int t1 = t;
   CK(cudaEventRecord(e_s1, st));
+  phase.set("slse_fit: stage 2");
   // a8 stage 2: full-data M-IHS steps until the relative step is small or T is reached.
   // Iteration k+1 is enqueued before the stop flag of iteration k is read back; its
   // kernels return at once when the flag is already set.
@@ -617,27 +640,31 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
   CK(cudaStreamSynchronize(st));
   const DevState fin = mb[2];
   slse_status status = status_from_bits(fin.status);
-  if (rep) {
-    rep->ms_copy_in = L.host_in ? ms_between(e_start, e_copied) : 0.0;
-    rep->ms_draws = ms_between(e_start, e_draws);
-    rep->ms_sketch = ms_between(e_draws, e_sketch);
-    rep->ms_srht_pass1 = (L.sp.single || L.cs) ? rep->ms_sketch : ms_between(e_draws, e_mid);
-    rep->ms_srht_pass2 = (L.sp.single || L.cs) ? 0.0 : ms_between(e_mid, e_sketch);
-    rep->ms_qr = ms_between(e_sketch, e_qr);
-    rep->ms_stage1 = ms_between(e_qr, e_s1);
-    rep->ms_total = ms_between(e_start, e_end);
-    rep->ms_stage2 = rep->ms_total - ms_between(e_start, e_s1);
+  // the report (also formed for the SLSE_LOG trace when the caller passed none)
+  slse_report local_rep{};
+  const bool log = getenv("SLSE_LOG") != nullptr;
+  slse_report *RP = rep ? rep : (log ? &local_rep : nullptr);
+  if (RP) {
+    RP->ms_copy_in = L.host_in ? ms_between(e_start, e_copied) : 0.0;
+    RP->ms_draws = ms_between(e_start, e_draws);
+    RP->ms_sketch = ms_between(e_draws, e_sketch);
+    RP->ms_srht_pass1 = (L.sp.single || L.cs) ? RP->ms_sketch : ms_between(e_draws, e_mid);
+    RP->ms_srht_pass2 = (L.sp.single || L.cs) ? 0.0 : ms_between(e_mid, e_sketch);
+    RP->ms_qr = ms_between(e_sketch, e_qr);
+    RP->ms_stage1 = ms_between(e_qr, e_s1);
+    RP->ms_total = ms_between(e_start, e_end);
+    RP->ms_stage2 = RP->ms_total - ms_between(e_start, e_s1);
     // gradient launches that ran a full pass (the speculative one after the stop returns at once)
     const int full = fin.iter - t1;
     double mg = 0.0;
     for (int k = 0; k < full && k < (int)e_grad.size(); ++k) mg += ms_between(e_grad[k].first, e_grad[k].second);
-    rep->ms_grad2 = mg;
-    rep->n_grad2 = full;
-    rep->kernels = kernels;
-    rep->iters_stage1 = t1;
-    rep->iters_stage2 = fin.iter - t1;
-    rep->final_rel_step = fin.rel_step;
-    rep->rebases = fin.rebases;
+    RP->ms_grad2 = mg;
+    RP->n_grad2 = full;
+    RP->kernels = kernels;
+    RP->iters_stage1 = t1;
+    RP->iters_stage2 = fin.iter - t1;
+    RP->final_rel_step = fin.rel_step;
+    RP->rebases = fin.rebases;
     const double bx = p->dtype == SLSE_F64 ? 8.0 : 4.0, bu = (double)elem_bytes_u(s.prec);
     double bytes = 0.0;
     if (L.cs) bytes += 2.0 * (double)p->N * (d + 1) * bx + (double)L.n_samp * (d + 1) * bu;  // nested and S-hat passes
@@ -647,11 +674,19 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     if (L.gauss) bytes += (double)p->N * d * bx + (mixed ? 2.0 * (double)p->N * L.gp.ncp * 2.0 : 0.0);
     for (size_t i = 0; i < s.m.size(); ++i) bytes += (double)s.a[i] * (double)s.m[i] * (d + 1) * bu;
     // a 2nd-stage pass reads X and one N-vector (Y in FP64 / rebase passes, r0 otherwise)
-    rep->bytes_grad2 = (double)p->N * d * bx + (double)p->N * (mixed ? 4.0 : bx);
-    bytes += (double)full * rep->bytes_grad2;
-    rep->bytes_moved = bytes;
-    rep->status = status;
+    RP->bytes_grad2 = (double)p->N * d * bx + (double)p->N * (mixed ? 4.0 : bx);
+    bytes += (double)full * RP->bytes_grad2;
+    RP->bytes_moved = bytes;
+    RP->status = status;
   }
+  if (log && RP)
+    fprintf(stderr,
+            "slse_fit: N=%lld d=%d kind=%d prec=%d status=%d | draws %.3f ms, sketch %.3f ms (pass 1 %.3f, pass 2 "
+            "%.3f), Hessian factor %.3f ms, stage 1 %.3f ms (%d its), stage 2 %.3f ms (%d its, %d full passes, "
+            "%.3f ms in gradients), total %.3f ms, %d kernels\n",
+            (long long)p->N, d, s.kind, s.prec, (int)status, RP->ms_draws, RP->ms_sketch, RP->ms_srht_pass1,
+            RP->ms_srht_pass2, RP->ms_qr, RP->ms_stage1, RP->iters_stage1, RP->ms_stage2, RP->iters_stage2, RP->n_grad2,
+            RP->ms_grad2, RP->ms_total, RP->kernels);
   if (tr) {
     tr->count = fin.iter < hist_cap ? fin.iter : hist_cap;
     if (tr->ms_hist)
