@@ -469,17 +469,21 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     kernels += 12;
     CK(cudaEventRecord(e_mid, st));
   } else {
-    // a1: random draws
-    CK(launch_draws(L.Np, seed, Psd, nullptr, sigma, nullptr, big, st));
-    kernels += 9;
-    CK(launch_pos_map(sigma, L.Np, 0, L.n_samp, L.sp.single ? L.sp.logN : L.sp.log2, pos, st));
-    kernels += 1;
+    // a1: random draws (none when nothing is sampled: a Gaussian Hessian sketch without subproblems)
+    if (L.n_samp > 0) {
+      CK(launch_draws(L.Np, seed, Psd, nullptr, sigma, nullptr, big, st));
+      kernels += 9;
+      CK(launch_pos_map(sigma, L.Np, 0, L.n_samp, L.sp.single ? L.sp.logN : L.sp.log2, pos, st));
+      kernels += 1;
+    }
     CK(cudaEventRecord(e_draws, st));
     phase.set("slse_fit: sketch");
     if (L.host_in) CK(cudaStreamWaitEvent(st, e_copied, 0));
     // a2-a4: SRHT into the sampled rows (U = Z[sigma] with Z = H D P X / sqrt(N'); sketch scales applied later)
     __nv_bfloat16 *h16 = fp8 ? reinterpret_cast<__nv_bfloat16 *>(base + L.o_hat16) : nullptr;
-    if (fp8 && L.sp.single) {  // one-pass sizes: BF16 rows, then the FP8 form (S-hat rows stay BF16)
+    if (L.n_samp == 0) {
+      CK(cudaEventRecord(e_mid, st));
+    } else if (fp8 && L.sp.single) {  // one-pass sizes: BF16 rows, then the FP8 form (S-hat rows stay BF16)
       CK(launch_srht(L.sp, SLSE_PREC_MIXED_BF16, p->dtype, p->X, p->ldx, p->Y, p->N, d, Psd, pos, nullptr, nullptr,
                      L.ld16, big, V, L.ld16, 1.0 / std::sqrt((double)L.Np), st, nullptr));
       CK(launch_quantize_mx(static_cast<const __nv_bfloat16 *>(big), L.ld16, L.n_samp, d, static_cast<uint8_t *>(U),

@@ -170,3 +170,21 @@ def test_fit_gaussian_mixed_reaches_ols_1e8(slse, N, d):
         H = ex.T @ ex
         E = host(res.hinv) @ H - np.eye(d)
         assert np.linalg.norm(E, 2) < 0.05
+
+
+def test_fit_gaussian_fp64_stage2_only_matches_oracle(slse):
+    # no subproblems: nothing is sampled from the SRHT (the draws and passes are skipped) and
+    # every iteration is a full-data M-IHS step preconditioned by the Gaussian sketch
+    N, d = 6000, 20
+    p = workloads.gaussian(N, d, seed=8)
+    X, Y = p["X"], p["Y"]
+    T = 12
+    sched = slse.Schedule(m=[], a=[], r=120, mu=(1 - 1 / 6) ** 2, eta=1 / 6, T=T, kind=slse.GAUSSIAN)
+    res = slse.fit(dev(X), dev(Y), sched, seed=5, trace_cap=T)
+    ores = osl.slse_fit(X, Y, osl.Schedule(m=[], a=[], r=120, mu=sched.mu, eta=sched.eta, T=T, kind="gaussian"),
+                        seed=5, trace=True)
+    bh = linalg.ols(X, Y)
+    hist = host(res.beta_hist)
+    assert hist.shape[0] == len(ores.trace) == T and res.report["iters_stage1"] == 0
+    for t, (g, o) in enumerate(zip(hist, ores.trace)):
+        assert np.linalg.norm(g - o) <= 1e-10 * np.linalg.norm(bh), t
