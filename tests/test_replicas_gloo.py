@@ -34,7 +34,7 @@ def _worker(rank, ws, port, out):
 def test_two_replicas_over_gloo():
     ws = 2
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.start_processes(_worker, args=(ws, port, out), nprocs=ws, join=True, start_method="spawn")
     assert out[0] == (11.0, 200.0, 2) and out[1] == (11.0, 200.0, 2)
