@@ -277,6 +277,14 @@ def fit(X, Y, schedule: Schedule | None = None, seed: int = 0, workspace=None, t
     return out
 
 
+def solve_normal_workspace(X, schedule: Schedule) -> int:
+    """slse_solve_normal_workspace: bytes of workspace slse_solve_normal needs for X."""
+    if X.dim() != 2 or X.stride(1) != 1:
+        raise ValueError("X must be a row-major 2-D tensor")
+    p = CProblem(X.shape[0], X.shape[1], _dtype_code(X), X.data_ptr(), X.stride(0), X.data_ptr())
+    return int(_lib.slse_solve_normal_workspace(ctypes.byref(p), PREC[schedule.prec]))
+
+
 def solve_normal(X, Hinv, v, schedule: Schedule, workspace=None, stream=None, raise_on_error: bool = True):
     """slse_solve_normal: w = (X^T X)^{-1} v by preconditioned M-IHS steps (device float64).
     Returns (w, report)."""
@@ -298,14 +306,21 @@ def solve_normal(X, Hinv, v, schedule: Schedule, workspace=None, stream=None, ra
     return w, {f: getattr(rep, f) for f, _ in CReport._fields_}
 
 
-def ols_vjp(X, Y, beta, w, stream=None):
-    """slse_ols_vjp: (dL/dX, dL/dY) = (r w^T - (X w) beta^T, X w), r = Y - X beta, in X's dtype."""
+def ols_vjp(X, Y, beta, w, stream=None, out=None):
+    """slse_ols_vjp: (dL/dX, dL/dY) = (r w^T - (X w) beta^T, X w), r = Y - X beta, in X's dtype.
+    out: optional (dX, dY) device tensors to write into (dX row-major, X's shape and dtype)."""
     torch = _torch()
     p = problem(X, Y)
     beta = torch.as_tensor(beta, dtype=torch.float64, device=X.device).contiguous()
     w = w.to(torch.float64).contiguous()
-    dX = torch.empty_like(X, memory_format=torch.contiguous_format)
-    dY = torch.empty_like(Y)
+    if out is None:
+        dX = torch.empty_like(X, memory_format=torch.contiguous_format)
+        dY = torch.empty_like(Y)
+    else:
+        dX, dY = out
+        if (dX.shape != X.shape or dX.dtype != X.dtype or dX.stride(1) != 1 or dY.shape != Y.shape
+                or dY.dtype != Y.dtype or not dY.is_contiguous()):
+            raise ValueError("out must be (dX, dY) shaped and typed like (X, Y), dX row-major")
     st = _lib.slse_ols_vjp(ctypes.byref(p), beta.data_ptr(), w.data_ptr(), dX.data_ptr(), dX.stride(0), dY.data_ptr(),
                            _stream(stream))
     _check(st, "slse_ols_vjp")

@@ -116,6 +116,143 @@ __global__ void __launch_bounds__(256) k_vjp_rows(const T *X, int64_t ldx, const
   }
 }
 
+// Packed FP32 pairs: one instruction does both halves.  a - b is fma(b, -1, a), which
+// rounds once, exactly as the subtraction does.
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// Knuth's TwoSum on each half: s + e = a + b exactly.
+__device__ __forceinline__ void p_two_sum(float2 a, float2 b, float2 &s, float2 &e) {
+  s = p_add(a, b);
+  const float2 bb = p_sub(s, a);
+  e = p_add(p_sub(a, p_sub(s, bb)), p_sub(b, bb));
+}
+
+template <int VMAX, int RPW>
+__device__ __forceinline__ void vjp_load(const float *X, int64_t ldx, int64_t N, int d, int lane, int64_t i0,
+                                         float4 (&x)[RPW][VMAX]) {
+#pragma unroll
+  for (int q = 0; q < RPW; ++q)
+#pragma unroll
+    for (int v = 0; v < VMAX; ++v) {
+      const int c = 4 * lane + 128 * v;
+      const int64_t i = i0 + q;
+      x[q][v] = (i < N && c < d) ? __ldcs(reinterpret_cast<const float4 *>(X + i * ldx + c))
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// FP32 rows, 16-byte aligned, d % 4 == 0: lane l holds columns 4 l + 128 v .. + 3
+// (v < VMAX) of RPW rows at once (RPW * VMAX = 4), and the next RPW rows are loaded while
+// this group is written.  Both dot products run as one Dot2 sum (error-free products and
+// sums, the vector split into FP32 head + tail, as in the mixed gradient) on packed FP32
+// pairs: the .x half accumulates -x . beta and the .y half -x . w, so a = x . w is as
+// accurate as the residual (a row whose a cancels still gets a to ~2^-24 |a|).  The RPW
+// sums of a warp are reduced together: each of the first log2(RPW) butterfly steps hands
+// half of the rows to the partner lane, so that lane l ends with row l / (32 / RPW) after
+// a plain butterfly over the remaining lanes; r = y - p is formed there and broadcast with
+// a.  dX = r w - a beta needs no x.
+template <int VMAX, int RPW, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_vjp_rows_f32v(const float *X, int64_t ldx, const float *Y, int64_t N,
+                                                            int d, const double *beta, const double *w, float *dX,
+                                                            int64_t lddx, float *dY) {
+  constexpr int LR = RPW == 8 ? 3 : RPW == 4 ? 2 : RPW == 2 ? 1 : 0;  // log2 RPW
+  constexpr int GL = 32 >> LR;                                         // lanes per row at the end
+  static_assert((1 << LR) == RPW && RPW * VMAX == 4, "RPW must be 4 / VMAX, a power of two");
+  const int lane = threadIdx.x & 31;
+  // per column: (beta, w) heads, their negations, and the negated tails
+  float2 b2[VMAX][4], nb2[VMAX][4], nl2[VMAX][4];
+#pragma unroll
+  for (int v = 0; v < VMAX; ++v)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int c = 4 * lane + 128 * v + e;
+      const double bv = c < d ? beta[c] : 0.0, wv = c < d ? w[c] : 0.0;
+      b2[v][e] = make_float2((float)bv, (float)wv);
+      nb2[v][e] = make_float2(-b2[v][e].x, -b2[v][e].y);
+      nl2[v][e] = make_float2(-(float)(bv - (double)b2[v][e].x), -(float)(wv - (double)b2[v][e].y));
+    }
+  const int64_t step = (((int64_t)gridDim.x * blockDim.x) >> 5) * RPW;
+  int64_t i0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * RPW;
+  float4 x[RPW][VMAX];
+  vjp_load<VMAX, RPW>(X, ldx, N, d, lane, i0, x);
+  for (; i0 < N; i0 += step) {
+    const int64_t iy = i0 + (lane / GL);  // the row this lane holds after the reduction
+    const float y = iy < N ? __ldcs(Y + iy) : 0.f;
+    float2 ns[RPW], nc[RPW];  // (-x . beta, -x . w) = ns + nc
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+      float2 sum = make_float2(0.f, 0.f), cor = sum;
+#pragma unroll
+      for (int v = 0; v < VMAX; ++v)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float xv = e == 0 ? x[q][v].x : e == 1 ? x[q][v].y : e == 2 ? x[q][v].z : x[q][v].w;
+          const float2 xx = make_float2(xv, xv);
+          const float2 qn = p_mul(xx, nb2[v][e]);     // -fl(x head)
+          const float2 ee = p_fma(xx, b2[v][e], qn);  // x head - fl(x head), exact
+          float2 t, err;
+          p_two_sum(sum, qn, t, err);
+          sum = t;
+          cor = p_fma(xx, nl2[v][e], p_add(cor, p_sub(err, ee)));
+        }
+      ns[q] = sum;
+      nc[q] = cor;
+    }
+#pragma unroll
+    for (int sp = 0; sp < LR; ++sp) {
+      const int off = 16 >> sp, half = RPW >> (sp + 1);
+      const bool up = (lane & off) != 0;  // keeps the upper half of the rows left
+#pragma unroll
+      for (int k = 0; k < half; ++k) {
+        const float2 s_send = up ? ns[k] : ns[k + half], c_send = up ? nc[k] : nc[k + half];
+        const float2 s_keep = up ? ns[k + half] : ns[k], c_keep = up ? nc[k + half] : nc[k];
+        const float2 s_r = make_float2(__shfl_xor_sync(0xffffffffu, s_send.x, off),
+                                       __shfl_xor_sync(0xffffffffu, s_send.y, off));
+        const float2 c_r = make_float2(__shfl_xor_sync(0xffffffffu, c_send.x, off),
+                                       __shfl_xor_sync(0xffffffffu, c_send.y, off));
+        float2 t, err;
+        p_two_sum(s_keep, s_r, t, err);
+        ns[k] = t;
+        nc[k] = p_add(p_add(c_keep, c_r), err);
+      }
+    }
+#pragma unroll
+    for (int off = GL / 2; off > 0; off >>= 1) {
+      const float2 s_r = make_float2(__shfl_xor_sync(0xffffffffu, ns[0].x, off),
+                                     __shfl_xor_sync(0xffffffffu, ns[0].y, off));
+      const float2 c_r = make_float2(__shfl_xor_sync(0xffffffffu, nc[0].x, off),
+                                     __shfl_xor_sync(0xffffffffu, nc[0].y, off));
+      float2 t, err;
+      p_two_sum(ns[0], s_r, t, err);
+      ns[0] = t;
+      nc[0] = p_add(p_add(nc[0], c_r), err);
+    }
+    vjp_load<VMAX, RPW>(X, ldx, N, d, lane, i0 + step, x);
+    float rh, re;
+    two_sum(y, ns[0].x, rh, re);
+    const float r = rh + (re + nc[0].x);
+    const float a = -(ns[0].y + nc[0].y);
+    if ((lane & (GL - 1)) == 0 && iy < N) dY[iy] = a;
+#pragma unroll
+    for (int q = 0; q < RPW; ++q) {
+      const float rq = __shfl_sync(0xffffffffu, r, q * GL), aq = __shfl_sync(0xffffffffu, a, q * GL);
+      const int64_t i = i0 + q;
+      const float2 r2 = make_float2(rq, rq), na2 = make_float2(-aq, -aq);
+#pragma unroll
+      for (int v = 0; v < VMAX; ++v) {
+        const int col = 4 * lane + 128 * v;
+        if (i < N && col < d) {
+          const float2 o0 = p_fma(r2, make_float2(b2[v][0].y, b2[v][1].y), p_mul(na2, make_float2(b2[v][0].x, b2[v][1].x)));
+          const float2 o1 = p_fma(r2, make_float2(b2[v][2].y, b2[v][3].y), p_mul(na2, make_float2(b2[v][2].x, b2[v][3].x)));
+          __stcs(reinterpret_cast<float4 *>(dX + i * lddx + col), make_float4(o0.x, o0.y, o1.x, o1.y));
+        }
+      }
+    }
+  }
+}
+
 // Pinned mailbox for the stop flag (one per host thread).
 struct MailboxA {
   DevState *h = nullptr;
@@ -330,6 +467,19 @@ extern "C" slse_status slse_ols_vjp(const slse_problem *prob, const double *beta
     if (d <= 128) run(double{}, std::integral_constant<int, 4>{});
     else if (d <= 256) run(double{}, std::integral_constant<int, 8>{});
     else run(double{}, std::integral_constant<int, 16>{});
+  } else if (d % 4 == 0 && prob->ldx % 4 == 0 && lddx % 4 == 0 && ((uintptr_t)prob->X & 15) == 0 &&
+             ((uintptr_t)dX & 15) == 0) {
+    // 3 CTAs per SM with the next rows in flight (0.81 of the HBM copy rate at d = 128, where
+    // the packed Dot2 arithmetic sets the pace); 2 above d = 128, where 3 would spill
+    auto runv = [&](auto vmax) {
+      constexpr int V = decltype(vmax)::value, MB = V == 1 ? 3 : 2;
+      k_vjp_rows_f32v<V, 4 / V, MB><<<(unsigned)(MB * nsm), 256, 0, s>>>(
+          static_cast<const float *>(prob->X), prob->ldx, static_cast<const float *>(prob->Y), prob->N, d, beta, w,
+          static_cast<float *>(dX), lddx, static_cast<float *>(dY));
+    };
+    if (d <= 128) runv(std::integral_constant<int, 1>{});
+    else if (d <= 256) runv(std::integral_constant<int, 2>{});
+    else runv(std::integral_constant<int, 4>{});
   } else {
     if (d <= 128) run(float{}, std::integral_constant<int, 4>{});
     else if (d <= 256) run(float{}, std::integral_constant<int, 8>{});

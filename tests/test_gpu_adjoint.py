@@ -66,6 +66,10 @@ def test_solve_normal_matches_oracle(slse, N, d, prec):
     wo = oadj.normal_solve(np.asarray(X, np.float64), v)
     err = np.linalg.norm(host(w) - wo) / np.linalg.norm(wo)
     assert err <= (1e-10 if prec == "fp64" else 1e-8), err
+    # a caller workspace gives the same bits (fixed reduction order)
+    ws = slse.alloc_workspace(slse.solve_normal_workspace(Xd, sched))
+    w2, _ = slse.solve_normal(Xd, res.hinv, dev(v), sched, workspace=ws)
+    assert np.array_equal(host(w2), host(w))
     assert rep["status"] == 0 and 0 < rep["iters_stage2"] < 100
 
 
@@ -106,6 +110,36 @@ def test_vjp_fp32_at_full_size_on_sampled_rows(slse):
     scale = np.abs(np.outer(r, wo)) + np.abs(np.outer(a, beta))
     assert np.all(np.abs(got - ref) <= 1e-6 * scale.max(axis=1, keepdims=True) + 1e-6 * np.abs(ref))
     np.testing.assert_allclose(host(dY)[rows], a, rtol=1e-5, atol=1e-6 * np.abs(a).max())
+
+
+@pytest.mark.parametrize("N,d,pad", [(1037, 36, 0), (4099, 200, 0), (3001, 512, 0), (2053, 130, 0), (5003, 128, 4),
+                                     (777, 4, 0), (300, 256, 8)])
+def test_vjp_fp32_widths_match_oracle(slse, N, d, pad):
+    # FP32 X of each register layout of the row kernel (d <= 128, <= 256, <= 512), the
+    # scalar kernel (d % 4 != 0), rows with a leading dimension above d, ragged row counts,
+    # and the form that writes into caller buffers; against the oracle's dense formulas
+    torch = torch_cuda()
+    p = workloads.cfg5(N=N, d=d, seed=11)
+    X, Y = p["X"], p["Y"]
+    X64, Y64 = X.astype(np.float64), Y.astype(np.float64)
+    bh = linalg.ols(X64, Y64)
+    v = np.random.default_rng(12).standard_normal(d)
+    wo, dXo, dYo = oadj.ols_vjp(X64, Y64, bh, v)
+    Xw = torch.zeros((N, d + pad), dtype=torch.float32, device="cuda")
+    Xw[:, :d] = dev(X)
+    Xd = Xw[:, :d]
+    Yd = dev(Y)
+    outs = (torch.full((N, d), np.nan, dtype=torch.float32, device="cuda"),
+            torch.full((N,), np.nan, dtype=torch.float32, device="cuda"))
+    for out in (None, outs):
+        dX, dY = slse.ols_vjp(Xd, Yd, bh, dev(wo), out=out)
+        torch.cuda.synchronize()
+        got, gy = host(dX), host(dY)
+        r = Y64 - X64 @ bh
+        scale = np.abs(np.outer(r, wo)) + np.abs(np.outer(X64 @ wo, bh))
+        assert np.all(np.abs(got - dXo) <= 1e-6 * scale.max(axis=1, keepdims=True) + 1e-6 * np.abs(dXo))
+        np.testing.assert_allclose(gy, dYo, rtol=1e-5, atol=1e-6 * np.abs(dYo).max())
+    assert outs[0].data_ptr() == dX.data_ptr()
 
 
 def test_autograd_mixed_fp32_gradients(slse):
