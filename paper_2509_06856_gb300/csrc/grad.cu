@@ -15,8 +15,12 @@
 // words) and stores r0 in FP32; later passes compute r_i = r0_i - x_i (beta - beta_0)
 // in FP32, whose rounding error scales with ||beta - beta_0|| and vanishes as the
 // iteration converges.  x_i r_i is accumulated in FP32 and folded every 16 rows into
-// a two-word (TwoSum) accumulator.  The update kernel re-bases when
-// ||beta - beta_0|| > 2^-10 ||beta||.
+// a two-word (TwoSum) accumulator.  The update kernel re-bases when the drift
+// ||beta - beta_0|| exceeds both 2^-10 ||beta|| and 2^10 times the last step
+// ||beta+ - beta||: the FP32 residual's error (~2^-24 of the drift) then stays below
+// ~2^-14 of the step, i.e. of the iterate's current error, so passes far from the
+// solution (the first steps from beta = 0) keep one base point instead of re-basing at
+// every step, and the final base point lies within 2^-10 of the solution.
 #include "slse_internal.cuh"
 
 namespace slse {
@@ -549,7 +553,8 @@ __global__ void __launch_bounds__(256) k_update(const UpdArgs A, DevState *st) {
       st->done = 1;
       if (a.thr > 0.0) st->status |= ST_NOTCONV;
     }
-    if (a.mixed) st->rebase = (x2 > 0x1p-20 * x1) ? 1 : 0;
+    // x2 = ||beta+ - beta_0||^2, x1 = ||beta+||^2, x0 = ||beta+ - beta||^2
+    if (a.mixed) st->rebase = (x2 > 0x1p-20 * x1 && x2 > 0x1p20 * x0) ? 1 : 0;
   }
 }
 
