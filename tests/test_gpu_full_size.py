@@ -5,7 +5,8 @@ times (the library picks the same kernels for the same shapes):
   1e-10 of the oracle's Householder-QR least-squares solution;
 * mixed precision on the benchmark workload (N = 2^22, d = 512, X FP32, AR(1) rows): the
   mixed fit within 1e-8 and the FP64 fit within 1e-10 of the oracle's OLS; the mixed
-  residual-gradient pass against the oracle's FP64 gradient;
+  residual-gradient pass against the oracle's FP64 gradient; sampled entries of the BF16
+  sketch with N/2 rows kept;
 * heavy tails (N = 2^24, d = 256, Student-t entries, 0.1% of rows x100): the BF16 and FP8
   forms of the fit within 1e-8 and FP64 within 1e-10; sampled sketch entries of each
   stored form against the definition computed one by one, within that form's rounding.
@@ -79,6 +80,25 @@ def test_cfg3_mixed_gradient_full_size(slse, cfg3):
         rb = np.asarray(Y[lo:lo + (1 << 16)], np.float64) - xb @ beta
         bound += np.abs(xb).T @ np.abs(rb)
     np.testing.assert_array_less(np.abs(g - go), 4e-7 * bound + 1e-300)
+
+
+def test_cfg3_bf16_sketch_entries_full_size(slse, cfg3):
+    # the benchmark's sketch shape (N' = 2^22, m = N/2 rows kept, BF16 form): sampled entries,
+    # across column-slab boundaries, against the definition computed one by one
+    torch = torch_cuda()
+    X, Y = cfg3["X"], cfg3["Y"]
+    N, d = X.shape
+    m, seed = N // 2, 5
+    D, P, sigma = osk.draws(padded(N), seed)
+    rows = [0, 1, (m // 2) + 3, m - 1]
+    cols = [0, 1, 31, 32, 63, 64, 100, d - 1, d]
+    ref = np.array([sketch_entry(X, Y, D, P, sigma, m, s, cols) for s in rows])
+    SXb, SYb = slse.sketch(dev(X), dev(Y), m, seed=seed, prec="mixed_bf16")
+    a = host(SXb.to(torch.float64))
+    b = host(SYb.to(torch.float64))
+    got = np.array([[a[s, c] if c < d else b[s] for c in cols] for s in rows])
+    colrms = np.sqrt(np.mean(ref ** 2, axis=0))
+    assert np.all(np.abs(got - ref) <= 2.0 ** -7 * np.abs(ref) + 2.0 ** -7 * colrms)
 
 
 @pytest.fixture(scope="module")
