@@ -173,6 +173,30 @@ def test_fit_fp64_iterates_match_oracle_momentum_reset(slse):
         assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(bh), t
 
 
+def test_fit_hessian_sketch_prefix_fallback(slse):
+    # m_K + r > N': S-hat takes the prefix rows sigma[0:r) (the disjoint block does not fit)
+    p = workloads.gaussian(3000, 20, seed=12)
+    X, Y = p["X"], p["Y"]
+    m = [120 * 2 ** t for t in range(6)]                 # m_K = 3840, r = 400, N' = 4096
+    sched = slse.Schedule(m=m, a=[2] * 6, r=400, mu=(1 - 20 / 400) ** 2, eta=20 / 400, T=40)
+    assert m[-1] + 400 > padded(3000)
+    res = slse.fit(dev(X), dev(Y), sched, seed=3, trace_cap=40)
+    ores = osl.slse_fit(X, Y, osl.Schedule(m=m, a=[2] * 6, r=400, mu=sched.mu, eta=sched.eta, T=40, tol=0.0),
+                        seed=3, trace=True)
+    bh = linalg.ols(X, Y)
+    nb = np.linalg.norm(bh)
+    for t, (a, b) in enumerate(zip(host(res.beta_hist), ores.trace)):
+        assert np.linalg.norm(a - b) <= 1e-10 * nb, t
+    # the mixed path (two-pass transform, N' = 8192) in the same situation
+    q = workloads.cfg3(N=6000, d=40, seed=13)
+    mm = [320, 640, 1280, 2560, 5120, 7800]              # m_K + r = 8280 > 8192
+    sm = slse.Schedule(m=mm, a=[2] * 6, r=480, mu=(1 - 40 / 480) ** 2, eta=40 / 480, T=100, tol=1e-10,
+                       prec="mixed_bf16")
+    rm = slse.fit(dev(q["X"]), dev(q["Y"]), sm, seed=4)
+    bq = linalg.ols(q["X"].astype(np.float64), q["Y"].astype(np.float64))
+    assert np.linalg.norm(rm.beta - bq) <= 1e-8 * np.linalg.norm(bq)
+
+
 @pytest.mark.parametrize("name,N,d,kappa", [("paper", 1 << 15, 32, 1e4), ("cfg2", 1 << 16, 64, 1e4)])
 def test_fit_fp64_reaches_ols(slse, name, N, d, kappa):
     p = workloads.paper(N, d, kappa=kappa, sigma2=1e-8, seed=1) if name == "paper" else \
