@@ -128,10 +128,10 @@ def test_prediction_efficiency_matches_srht_limit():
 def test_hessian_rows_disjoint_block_or_prefix():
     # reading of Sec. 4 / Thm 4.4: S-hat takes the r sampled rows after the largest nested
     # sketch (disjoint from every S_i), or the prefix when that block does not fit in N'
-    assert osk.hessian_rows(4096, 3000, 1000) == (3000, 4000)
-    assert osk.hessian_rows(4096, 3096, 1000) == (3096, 4096)
-    assert osk.hessian_rows(4096, 3840, 400) == (0, 400)
+    assert sk.hessian_rows(4096, 3000, 1000) == (3000, 4000)
+    assert sk.hessian_rows(4096, 3096, 1000) == (3096, 4096)
+    assert sk.hessian_rows(4096, 3840, 400) == (0, 400)
     for Np, mK, r in [(1 << 12, 1 << 11, 300), (1 << 10, 1000, 24)]:
-        h0, h1 = osk.hessian_rows(Np, mK, r)
+        h0, h1 = sk.hessian_rows(Np, mK, r)
         assert h1 - h0 == r and 0 <= h0 and h1 <= Np
         assert h0 >= mK or h0 == 0
