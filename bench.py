@@ -588,7 +588,8 @@ def run_ours(args, rank, ws, local_rank):
             e2e = {"value": reduce_max(statistics.mean(v for v, _ in ev), 1), "unit": "ms",
                    "h2d_bytes_per_step": int(Xh.numel() * 4 + Yh.numel() * 4), "d2h_bytes_per_step": d * 8,
                    "ms_copy_in": statistics.mean(c for _, c in ev),
-                   "how": "slse_fit with pinned host X, Y: H2D copy on a side stream overlapped with the draws, "
+                   "how": "slse_fit with pinned host X, Y: Y copied on a side stream during the draws, X read from host "
+                          "memory by the first SRHT pass, which also writes its device copy; "
                           "time from the call's first CUDA event to the first iterate within 1e-8"}
 
     if rank != 0:

@@ -120,7 +120,8 @@ typedef struct {
 } slse_schedule;
 
 typedef struct {
-  double ms_copy_in;      /* host inputs only: CUDA-event time of the host-to-device copy (overlaps ms_draws) */
+  double ms_copy_in;      /* host inputs only: CUDA-event time of the host-to-device copies on the side
+                             stream (overlaps ms_draws): Y, and X unless the first SRHT pass reads it */
   double ms_draws, ms_sketch, ms_qr, ms_stage1, ms_stage2, ms_total; /* CUDA-event phase times */
   double ms_srht_pass1, ms_srht_pass2; /* the two sketch passes (pass 2 is 0 for single-pass sizes) */
   double ms_grad2;        /* summed CUDA-event time of the 2nd-stage gradient launches */
@@ -154,7 +155,11 @@ size_t slse_workspace_size(const slse_problem *prob, const slse_schedule *sched,
  * Synchronous: returns after beta_out is written.  sched == NULL selects the paper's
  * experimental defaults (slse_default_schedule) in FP64.  With host X and Y the copy to the
  * device runs on a side stream while the random draws run on `stream`; the workspace then
- * also holds the device copy (slse_workspace_size accounts for it).  Tracing: each phase's
+ * also holds the device copy (slse_workspace_size accounts for it).  Pinned X with ldx == d
+ * and a two-pass transform (N' > 512, SRHT or Gaussian kind) is not copied ahead: the first
+ * SRHT pass reads its rows from host memory through the mapped address and stores the device
+ * copy as it goes (each row is read once; the estimate is the same bits as from device
+ * inputs).  Tracing: each phase's
  * enqueue is wrapped in an NVTX range ("slse_fit: draws", "...: sketch", "...: Hessian factor",
  * "...: stage 1", "...: stage 2"); with SLSE_LOG set in the environment every call prints a
  * one-line summary of its phase times (CUDA events) to stderr. */

@@ -422,24 +422,43 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
   NvtxPhase phase;
   phase.set("slse_fit: draws");
   CK(cudaEventRecord(e_start, st));
-  // host inputs: copy into the workspace on a side stream, overlapped with the draws
+  // host inputs: Y (and X, unless pass 1 reads it) is copied into the workspace on a side
+  // stream, overlapped with the draws.  Pinned X with contiguous rows on a two-pass SRHT plan
+  // is instead read by SRHT pass 1 straight from host memory (every row is gathered exactly
+  // once there), and that pass also stores each row segment into the workspace copy: the
+  // transfer over the host link and the pass are one step instead of two.
   struct SideStream {
     cudaStream_t h = nullptr;
     ~SideStream() {
       if (h) cudaStreamDestroy(h);
     }
   } side;
+  const void *x_mapped = nullptr;  // device address of host X read by pass 1 (fused path)
+  void *x_copy = nullptr;          // where pass 1 stores it
   if (L.host_in) {
     const size_t bx = p->dtype == SLSE_F64 ? 8 : 4;
     void *xd = base + L.o_xin;
     void *yd = base + L.o_yin;
+    if (!L.cs && L.n_samp > 0 && !L.sp.single && pin->ldx == d) {
+      cudaPointerAttributes at;
+      void *dp = nullptr;
+      if (cudaPointerGetAttributes(&at, pin->X) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+          cudaHostGetDevicePointer(&dp, const_cast<void *>(pin->X), 0) == cudaSuccess && dp) {
+        x_mapped = dp;
+        x_copy = xd;
+      }
+      cudaGetLastError();
+    }
     CK(cudaStreamCreateWithFlags(&side.h, cudaStreamNonBlocking));
     CK(cudaStreamWaitEvent(side.h, e_start, 0));
-    if (pin->ldx == d)  // contiguous rows: one linear copy (a pitched copy splits it per row)
+    if (x_mapped) {
+      // X arrives through pass 1
+    } else if (pin->ldx == d) {  // contiguous rows: one linear copy (a pitched copy splits it per row)
       CK(cudaMemcpyAsync(xd, pin->X, (size_t)p->N * d * bx, cudaMemcpyHostToDevice, side.h));
-    else
+    } else {
       CK(cudaMemcpy2DAsync(xd, (size_t)d * bx, pin->X, (size_t)pin->ldx * bx, (size_t)d * bx, (size_t)p->N,
                            cudaMemcpyHostToDevice, side.h));
+    }
     CK(cudaMemcpyAsync(yd, pin->Y, (size_t)p->N * bx, cudaMemcpyHostToDevice, side.h));
     CK(cudaEventRecord(e_copied, side.h));
     prob.X = xd;
@@ -493,9 +512,9 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
       kernels += 2;
     } else {
       // FP8 form: the Hessian-sketch rows (sampling positions >= h0) are written in BF16 to h16
-      CK(launch_srht(L.sp, s.prec, p->dtype, p->X, p->ldx, p->Y, p->N, d, Psd, pos, big, WY, L.ld16, U, V, L.ldu,
-                     1.0 / std::sqrt((double)L.Np), st, L.sp.single ? nullptr : e_mid, Us, L.nsb, h16,
-                     L.h0 > 0 ? L.h0 : INT64_MAX, L.ld16));
+      CK(launch_srht(L.sp, s.prec, p->dtype, x_mapped ? x_mapped : p->X, p->ldx, p->Y, p->N, d, Psd, pos, big, WY,
+                     L.ld16, U, V, L.ldu, 1.0 / std::sqrt((double)L.Np), st, L.sp.single ? nullptr : e_mid, Us, L.nsb,
+                     h16, L.h0 > 0 ? L.h0 : INT64_MAX, L.ld16, x_copy));
       kernels += L.sp.single ? 1 : 2;
     }
     if (L.gauss) {

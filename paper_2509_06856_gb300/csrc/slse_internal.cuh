@@ -186,7 +186,10 @@ cudaError_t launch_srht(const SrhtPlan &pl, int prec, int xdtype, const void *X,
                         cudaStream_t s, cudaEvent_t ev_mid /* nullable: recorded between the passes */,
                         uint8_t *Uscale = nullptr /* MIXED_FP8: block exponents of U */, int64_t ld_scale = 0,
                         __nv_bfloat16 *hat = nullptr /* MIXED_FP8: rows >= hat_row0 in BF16 here */,
-                        int64_t hat_row0 = 0, int64_t hat_ld = 0);
+                        int64_t hat_row0 = 0, int64_t hat_ld = 0,
+                        void *copy_out = nullptr /* two-pass plans: X rows read by pass 1 (e.g. from
+                                                    mapped host memory) are also stored here, same
+                                                    element offsets (ldx); 16-byte aligned */);
 
 // grad.cu
 enum GradMode { GM_F64 = 0, GM_MIXED = 1, GM_STAGE1_BF16 = 2, GM_STAGE1_F64 = 3 };

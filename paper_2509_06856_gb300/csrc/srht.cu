@@ -59,6 +59,8 @@ struct GroupArgs {
   __nv_bfloat16 *hat_out;  // FP8 form: output rows >= hat_row0 go here in BF16 (nullable)
   int64_t hat_row0, hat_ld;
   double scale;
+  void *copy_out;       // pass 1 reading host memory: every input row segment is also stored
+                        // here at the same element offset (the device copy of X)
 };
 
 // Smallest k with amax <= 448 2^k (448 = 1.75 2^8, the largest E4M3 value), clamped to
@@ -128,6 +130,10 @@ __device__ __forceinline__ void store_vec(Tout *p, const Ts (&v)[VEC]) {
     *reinterpret_cast<uint2 *>(p) = t;
   } else if constexpr (sizeof(Tout) == 8 && VEC == 2) {
     *reinterpret_cast<double2 *>(p) = make_double2((double)v[0], (double)v[1]);
+  } else if constexpr (sizeof(Tout) == 4 && VEC == 2) {
+    *reinterpret_cast<float2 *>(p) = make_float2((float)v[0], (float)v[1]);
+  } else if constexpr (sizeof(Tout) == 4 && VEC == 4) {
+    *reinterpret_cast<float4 *>(p) = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
   } else {
 #pragma unroll
     for (int e = 0; e < VEC; ++e) store_cvt(p + e, v[e]);
@@ -208,7 +214,8 @@ template <int R, int VEC, class T> __device__ __forceinline__ void fwht_cols(T (
 //   B: the remaining low LOGM - S0 bits, VB columns per thread, through the shared tile;
 //   O: the Q cluster bits (rows held by the Q CTAs, read through distributed shared
 //      memory), then scaling, conversion and VO-column vector stores.
-template <class Tin, class Ts, class Tout, int LOGM, int Q, int C, int VA, int VB, int VO, int NT, int MINB, int SA>
+template <class Tin, class Ts, class Tout, int LOGM, int Q, int C, int VA, int VB, int VO, int NT, int MINB, int SA,
+          bool CPY>
 __global__ void __launch_bounds__(NT, MINB) k_group(const GroupArgs a) {
   constexpr int M = 1 << LOGM;
   constexpr int S0 = LOGM < SA ? LOGM : SA;
@@ -256,7 +263,10 @@ __global__ void __launch_bounds__(NT, MINB) k_group(const GroupArgs a) {
   }
   __syncthreads();
 
-  // stage A
+  // stage A (CPY: the rows read are also written to the device copy a.copy_out; padding
+  // rows, multiplier 0, are not; a separate instantiation, so that the plain one keeps its
+  // registers)
+  Tin *cpy = CPY ? static_cast<Tin *>(a.copy_out) : nullptr;
   const bool fast_in = a.vec_in && col0 + C <= d;
   for (int it = threadIdx.x; it < ((C / VA) << S1); it += NT) {
     const int cq = it % (C / VA), b = it / (C / VA);
@@ -270,12 +280,27 @@ __global__ void __launch_bounds__(NT, MINB) k_group(const GroupArgs a) {
 #pragma unroll
         for (int e = 0; e < VA; ++e) v[e][k] = t[e];
       }
+      if constexpr (CPY) {
+#pragma unroll
+        for (int k = 0; k < RA; ++k) {
+          if (s_mul[b + (k << S1)] == Ts(0)) continue;
+          Ts t[VA];
+#pragma unroll
+          for (int e = 0; e < VA; ++e) t[e] = v[e][k];
+          store_vec<Tin, Ts, VA>(cpy + s_off[b + (k << S1)] + col, t);
+        }
+      }
     } else {
 #pragma unroll
       for (int k = 0; k < RA; ++k) {
         const int64_t off = s_off[b + (k << S1)];
 #pragma unroll
         for (int e = 0; e < VA; ++e) v[e][k] = col + e < d ? load_cvt<Ts>(in + off + col + e) : Ts(0);
+        if (CPY && s_mul[b + (k << S1)] != Ts(0)) {
+#pragma unroll
+          for (int e = 0; e < VA; ++e)
+            if (col + e < d) cpy[off + col + e] = (Tin)v[e][k];
+        }
       }
     }
 #pragma unroll
@@ -498,13 +523,14 @@ __global__ void __launch_bounds__(NT) k_small(const GroupArgs a, int logn) {
   }
 }
 
-template <class Tin, class Ts, class Tout, int LOGM, int Q, int C, int VA, int VB, int VO, int MINB = 3, int SA = 5>
+template <class Tin, class Ts, class Tout, int LOGM, int Q, int C, int VA, int VB, int VO, int MINB = 3, int SA = 5,
+          bool CPY = false>
 cudaError_t launch_group_t(const GroupArgs &a0, int64_t ngroups, cudaStream_t s) {
   constexpr int NT = 256;
   GroupArgs a = a0;
   a.nslab = (a.d + C - 1) / C;
   const size_t smem = (size_t)(1 << LOGM) * (C * sizeof(Ts) + 8 + sizeof(Ts) + 4);
-  auto kern = k_group<Tin, Ts, Tout, LOGM, Q, C, VA, VB, VO, NT, MINB, SA>;
+  auto kern = k_group<Tin, Ts, Tout, LOGM, Q, C, VA, VB, VO, NT, MINB, SA, CPY>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -526,19 +552,19 @@ cudaError_t launch_group_t(const GroupArgs &a0, int64_t ngroups, cudaStream_t s)
 // k_group works on 128-byte row segments (32 FP32 / 16 FP64 columns), 256 rows per CTA
 // (512 for L = 12) and clusters of up to 8 CTAs; stage A takes the top 4 row bits so
 // that several CTAs fit on an SM (MB per SM: the launch bound).
-template <class Tin, class Ts, class Tout, int VA, int VB, int VO, int SLAB_BYTES = 128, int MB = 4>
+template <class Tin, class Ts, class Tout, int VA, int VB, int VO, int SLAB_BYTES = 128, int MB = 4, bool CPY = false>
 cudaError_t launch_pass_t(const GroupArgs &a, int L, int64_t ngroups, cudaStream_t s) {
   constexpr int CP = SLAB_BYTES / (int)sizeof(Ts);
   cudaError_t e;
   switch (L) {
-    case 5: e = launch_group_t<Tin, Ts, Tout, 5, 1, CP, VA, VB, VO, MB, 4>(a, ngroups, s); break;
-    case 6: e = launch_group_t<Tin, Ts, Tout, 6, 1, CP, VA, VB, VO, MB, 4>(a, ngroups, s); break;
-    case 7: e = launch_group_t<Tin, Ts, Tout, 7, 1, CP, VA, VB, VO, MB, 4>(a, ngroups, s); break;
-    case 8: e = launch_group_t<Tin, Ts, Tout, 8, 1, CP, VA, VB, VO, MB, 4>(a, ngroups, s); break;
-    case 9: e = launch_group_t<Tin, Ts, Tout, 8, 2, CP, VA, VB, VO, MB, 4>(a, ngroups, s); break;
-    case 10: e = launch_group_t<Tin, Ts, Tout, 8, 4, CP, VA, VB, VO, MB, 4>(a, ngroups, s); break;
-    case 11: e = launch_group_t<Tin, Ts, Tout, 8, 8, CP, VA, VB, VO, MB, 4>(a, ngroups, s); break;
-    case 12: e = launch_group_t<Tin, Ts, Tout, 9, 8, CP, VA, VB, VO, 3, 4>(a, ngroups, s); break;
+    case 5: e = launch_group_t<Tin, Ts, Tout, 5, 1, CP, VA, VB, VO, MB, 4, CPY>(a, ngroups, s); break;
+    case 6: e = launch_group_t<Tin, Ts, Tout, 6, 1, CP, VA, VB, VO, MB, 4, CPY>(a, ngroups, s); break;
+    case 7: e = launch_group_t<Tin, Ts, Tout, 7, 1, CP, VA, VB, VO, MB, 4, CPY>(a, ngroups, s); break;
+    case 8: e = launch_group_t<Tin, Ts, Tout, 8, 1, CP, VA, VB, VO, MB, 4, CPY>(a, ngroups, s); break;
+    case 9: e = launch_group_t<Tin, Ts, Tout, 8, 2, CP, VA, VB, VO, MB, 4, CPY>(a, ngroups, s); break;
+    case 10: e = launch_group_t<Tin, Ts, Tout, 8, 4, CP, VA, VB, VO, MB, 4, CPY>(a, ngroups, s); break;
+    case 11: e = launch_group_t<Tin, Ts, Tout, 8, 8, CP, VA, VB, VO, MB, 4, CPY>(a, ngroups, s); break;
+    case 12: e = launch_group_t<Tin, Ts, Tout, 9, 8, CP, VA, VB, VO, 3, 4, CPY>(a, ngroups, s); break;
     default: return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;
@@ -568,7 +594,7 @@ cudaError_t run_plan(const SrhtPlan &pl, const void *X, int64_t ldx, const void 
                      void *V, int64_t ldu, double scale, cudaStream_t s,
                      cudaError_t (*pass2)(const GroupArgs &, int, int64_t, cudaStream_t), cudaEvent_t ev_mid,
                      uint8_t *Uscale = nullptr, int64_t ld_scale = 0, __nv_bfloat16 *hat = nullptr,
-                     int64_t hat_row0 = 0, int64_t hat_ld = 0) {
+                     int64_t hat_row0 = 0, int64_t hat_ld = 0, void *copy_out = nullptr) {
   GroupArgs a = {};
   a.d = d;
   a.nslab = (d + 1 + C - 1) / C;
@@ -595,14 +621,17 @@ cudaError_t run_plan(const SrhtPlan &pl, const void *X, int64_t ldx, const void 
   a.out = W; a.ldout = ldw; a.out_y = WY; a.pos = nullptr;
   a.ostride = 1; a.ogstride = n2;
   a.scale = 1.0;
+  a.copy_out = copy_out;
   a.vec_out = vec_ok(W, ldw, sizeof(Tout), VO) ? 1 : 0;
-  cudaError_t e = launch_pass_t<Tin, Ts, Tout, VA, VB, VO, P1_SLAB, P1_MB>(a, pl.log2, n1, s);
+  cudaError_t e = copy_out ? launch_pass_t<Tin, Ts, Tout, VA, VB, VO, P1_SLAB, P1_MB, true>(a, pl.log2, n1, s)
+                           : launch_pass_t<Tin, Ts, Tout, VA, VB, VO, P1_SLAB, P1_MB, false>(a, pl.log2, n1, s);
   if (e != cudaSuccess) return e;
   if (ev_mid && (e = cudaEventRecord(ev_mid, s)) != cudaSuccess) return e;
   // pass 2: groups g = k2 (n2 of them), rows rho = j1 at stride n2, outputs kappa = k1
   GroupArgs b = a;
   b.Psd = nullptr;
   b.N = 0;
+  b.copy_out = nullptr;
   b.in = W; b.ldin = ldw; b.in_y = WY;
   b.vec_in = vec_ok(W, ldw, sizeof(Tout), VA) ? 1 : 0;
   b.vec_out = vec_ok(U, ldu, sizeof(Tout), VO) ? 1 : 0;
@@ -632,19 +661,22 @@ cudaError_t launch_srht(const SrhtPlan &pl, int prec, int xdtype, const void *X,
                         int64_t N, int d, const int32_t *Psd, const int32_t *pos, void *W, void *WY,
                         int64_t ldw, void *U, void *V, int64_t ldu, double scale, cudaStream_t s,
                         cudaEvent_t ev_mid, uint8_t *Uscale, int64_t ld_scale, __nv_bfloat16 *hat,
-                        int64_t hat_row0, int64_t hat_ld) {
+                        int64_t hat_row0, int64_t hat_ld, void *copy_out) {
   using bf16 = __nv_bfloat16;
+  if (copy_out && (pl.single || (uintptr_t)copy_out % 16 != 0)) return cudaErrorInvalidValue;
   if (prec == SLSE_PREC_FP64) {
     auto p2 = &launch_pass_t<double, double, double, 1, 1, 2>;
     if (xdtype == SLSE_F64)
-      return run_plan<double, double, double, 16, 1, 1, 2>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale, s, p2, ev_mid);
-    return run_plan<float, double, double, 16, 1, 1, 2>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale, s, p2, ev_mid);
+      return run_plan<double, double, double, 16, 1, 1, 2>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale, s,
+                                                          p2, ev_mid, nullptr, 0, nullptr, 0, 0, copy_out);
+    return run_plan<float, double, double, 16, 1, 1, 2>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale, s,
+                                                       p2, ev_mid, nullptr, 0, nullptr, 0, 0, copy_out);
   }
   if (prec == SLSE_PREC_MIXED_BF16 && xdtype == SLSE_F32) {
     // five CTAs per SM in both passes (more row gathers in flight; measured against 3, 4 and 6)
     auto p2 = &launch_pass_t<bf16, float, bf16, 2, 2, 4, 128, 5>;
     return run_plan<float, float, bf16, 32, 2, 2, 4, 128, 5>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale,
-                                                             s, p2, ev_mid);
+                                                             s, p2, ev_mid, nullptr, 0, nullptr, 0, 0, copy_out);
   }
   if (prec == SLSE_PREC_MIXED_FP8 && xdtype == SLSE_F32) {
     // pass 1 as in the BF16 form; pass 2 writes E4M3 rows with 32-column block scales
@@ -652,7 +684,8 @@ cudaError_t launch_srht(const SrhtPlan &pl, int prec, int xdtype, const void *X,
     if (pl.single || !Uscale) return cudaErrorInvalidValue;
     auto p2 = &launch_pass_t<bf16, float, mx8, 2, 2, 4>;
     return run_plan<float, float, bf16, 32, 2, 2, 4, 128, 5>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale,
-                                                             s, p2, ev_mid, Uscale, ld_scale, hat, hat_row0, hat_ld);
+                                                             s, p2, ev_mid, Uscale, ld_scale, hat, hat_row0, hat_ld,
+                                                             copy_out);
   }
   return cudaErrorInvalidValue;
 }
