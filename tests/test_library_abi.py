@@ -147,3 +147,20 @@ def test_debug_spin_limit_set_and_restore(lib):
     assert slse.debug_spin_limit(7) == 0
     assert slse.debug_spin_limit(-3) == 7      # <= 0 restores the built-in limit
     assert slse.debug_spin_limit(0) == 0
+
+
+def test_solve_normal_workspace_holds_the_n_vectors(lib):
+    # the backward solve keeps a zero right-hand side (N values) and, on the mixed path, the
+    # FP32 base residual (N values) besides O(d) state: the size grows by those per row
+    import paper_2509_06856_gb300 as slse
+    torch = pytest.importorskip("torch")
+    d = 32
+    s64 = slse.default_schedule(1 << 14, d, prec="fp64")
+    smx = slse.default_schedule(1 << 14, d, prec="mixed_bf16")
+    X64 = torch.empty((1 << 14, d), dtype=torch.float64)
+    X32a = torch.empty((1 << 14, d), dtype=torch.float32)
+    X32b = torch.empty((1 << 15, d), dtype=torch.float32)
+    a64 = slse.solve_normal_workspace(X64, s64)
+    a, b = slse.solve_normal_workspace(X32a, smx), slse.solve_normal_workspace(X32b, smx)
+    assert a64 >= 8 * (1 << 14)
+    assert b - a == (4 + 4) * (1 << 14)   # r0 (FP32) + the zero right-hand side (FP32)
