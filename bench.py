@@ -237,9 +237,35 @@ def cpu_leg(X, Y, log2n, d, sample_log2n, time_it):
         scale = (1 << log2n) / ns
         base = {"value": dt * 1000.0 * scale, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
                 "sample": f"oracle slse_fit (FP64, numpy) on the first 2^{sample_log2n} rows of the workload "
-                          f"(d={d}, same schedule rule), wall time x {scale:.0f} (linear in N)",
+                          f"(d={d}, same schedule rule), wall time x {scale:.0f} (linear in N); "
+                          f"BLAS on all cores, and once more with one thread",
                 "sample_seconds": dt}
+        dt1 = oracle_one_thread(Xs, Ys)
+        if dt1 is not None:
+            base["value_1_thread"] = dt1 * 1000.0 * scale
+            base["sample_seconds_1_thread"] = dt1
     return bh, t_ref, base
+
+
+def oracle_one_thread(Xs, Ys):
+    """Wall time of the same oracle fit in a fresh interpreter with every BLAS/OpenMP pool
+    limited to one thread (the limit must be set before numpy loads); None if it fails."""
+    import tempfile
+    with tempfile.TemporaryDirectory() as td:
+        fx, fy = os.path.join(td, "x.npy"), os.path.join(td, "y.npy")
+        np.save(fx, Xs)
+        np.save(fy, Ys)
+        code = ("import sys, time, numpy as np; sys.path.insert(0, %r); from oracle import slse as osl; "
+                "X = np.load(%r); Y = np.load(%r); "
+                "s = osl.default_schedule(X.shape[0], X.shape[1], T=100, tol=1e-9); "
+                "t0 = time.time(); osl.slse_fit(X, Y, s, seed=0); print(time.time() - t0)") % (ROOT, fx, fy)
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+                   NUMEXPR_NUM_THREADS="1")
+        try:
+            r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+            return float(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
+        except (subprocess.TimeoutExpired, ValueError, IndexError):
+            return None
 
 
 def sketch_form_errors(slse, torch, seed=4):
