@@ -249,7 +249,7 @@ int32_t slse_default_schedule_for(int64_t N, int32_t d, int32_t kind, slse_sched
  * sched supplies mu, eta, T (iteration cap), tol (the fit's relative-step test with
  * rho = sqrt(d/r)), r and prec (FP64, or MIXED_BF16 for F32 X: compensated FP32 passes);
  * its sizes m, a and kind are ignored.  X device; Y unused.  v, w_out: device d doubles.
- * report (nullable): ms_total, iters_stage2, final_rel_step, status.  Returns after w_out
+ * report (nullable): ms_total, iters_stage2, final_rel_step, rebases, status.  Returns after w_out
  * is written (SLSE_ENOTCONV if tol > 0 was not met within T, w_out holds the last iterate).
  * Workspace: slse_solve_normal_workspace bytes, or NULL for a stream-ordered allocation. */
 slse_status slse_solve_normal(const slse_problem *prob, const double *Hinv, const double *v, double *w_out,
@@ -259,8 +259,9 @@ size_t slse_solve_normal_workspace(const slse_problem *prob, int32_t prec);
 
 /* The input gradients from w (above) in one pass over [X | Y]: dY[i] = x_i . w and
  * dX[i, :] = (y_i - x_i . beta) w - (x_i . w) beta.  dX (ld lddx >= d) and dY have the
- * dtype of X (F32 inputs: compensated FP32 dot products).  All pointers device.
- * Asynchronous on `stream`. */
+ * dtype of X (F32 inputs: both dot products as compensated FP32 sums, so a row whose x_i . w
+ * cancels still gets it to about 2^-24 of its size).  All pointers device.  Asynchronous on
+ * `stream`. */
 slse_status slse_ols_vjp(const slse_problem *prob, const double *beta, const double *w, void *dX, int64_t lddx,
                          void *dY, slse_stream_t stream);
 
