@@ -192,15 +192,16 @@ slse_status slse_grad(const slse_problem *prob, const double *beta, double *g_ou
                       void *workspace, size_t ws_bytes, slse_stream_t stream);
 
 /* Residual-gradient pass that allocates nothing, for callers that cannot allocate device
- * memory when they need a gradient (graph capture into a fixed memory plan, host
- * applications that own every device allocation, loops that forbid allocation after
- * start-up).  The paper has no counterpart: this is a deployment variant of slse_grad.
+ * memory when they need a gradient (host applications that own every device allocation
+ * and hand out only fixed buffers, loops that forbid allocation after start-up).  The paper has no counterpart: this is a deployment variant of slse_grad.
  * Same arguments, result and tolerances as slse_grad, but its scratch (a status word and
  * per-CTA partial gradients, 1 MiB + 4 KiB) is a fixed array inside the library that
  * every GPU loading the library keeps until the process exits.  No cudaMalloc, cudaFree
  * or allocating library call is made.  The first call on a device looks up that array's
- * device address (cudaGetSymbolAddress) with the device current; make that first call
- * before any stream capture.  All calls on a device share the one array: calls whose
+ * device address (cudaGetSymbolAddress) with the device current and loads the code of every
+ * kernel this entry point can launch; make that first call before any stream capture.  A
+ * cudaDeviceReset destroys the array, and the looked-up address goes stale with it: after a
+ * reset, this entry point must not be called again in the same process.  All calls on a device share the one array: calls whose
  * work may overlap on the GPU (different streams without ordering) race and must not be
  * issued.  Each call clears the state it needs and overwrites every partial it reads.
  * Limit: the per-CTA partials must fit in 1 MiB (d <= 512 always fits; fewer CTAs are

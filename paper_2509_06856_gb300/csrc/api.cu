@@ -849,7 +849,8 @@ slse_status slse_sketch(const slse_problem *prob, int32_t kind, int32_t prec, ui
 slse_status slse_grad(const slse_problem *prob, const double *beta, double *g_out, int32_t prec, void *workspace,
                       size_t ws_bytes, slse_stream_t stream) {
   if (!valid_problem(prob) || !beta || !g_out) return SLSE_EINVAL;
-  if (is_host_pointer(prob->X) || is_host_pointer(prob->Y) || is_host_pointer(beta)) return SLSE_EINVAL;
+  if (is_host_pointer(prob->X) || is_host_pointer(prob->Y) || is_host_pointer(beta) || is_host_pointer(g_out))
+    return SLSE_EINVAL;
   if (prec != SLSE_PREC_FP64 && prec != SLSE_PREC_MIXED_BF16) return SLSE_EINVAL;
   if (prec == SLSE_PREC_MIXED_BF16 && prob->dtype != SLSE_F32) return SLSE_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;

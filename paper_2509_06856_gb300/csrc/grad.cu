@@ -619,6 +619,24 @@ cudaError_t launch_grad(int mode, int xdtype, const void *X, int64_t ldx, const 
   }
 }
 
+cudaError_t preload_grad_kernels() {
+  // every kernel launch_grad (modes GM_F64 and GM_MIXED) and launch_reduce can pick
+  const void *k[] = {
+      (const void *)k_grad_f64<double, 2, 8>,    (const void *)k_grad_f64<double, 1, 16>,
+      (const void *)k_grad_f64<float, 2, 8>,     (const void *)k_grad_f64<float, 1, 16>,
+      (const void *)k_grad_mixed<1, 16, 1, 1>,   (const void *)k_grad_mixed<4, 1, 1, 8>,
+      (const void *)k_grad_mixed<4, 2, 1, 4>,    (const void *)k_grad_mixed<4, 4, 1, 2>,
+      (const void *)k_grad_mixed<1, 16, 0, 1>,   (const void *)k_grad_mixed<4, 1, 0, 8>,
+      (const void *)k_grad_mixed<4, 2, 0, 4>,    (const void *)k_grad_mixed<4, 4, 0, 2>,
+      (const void *)k_reduce};
+  for (const void *f : k) {
+    cudaFuncAttributes fa;
+    const cudaError_t e = cudaFuncGetAttributes(&fa, f);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_reduce(const double *partials, int nblk, int d, double scale, double *g, DevState *st,
                           int check_done, cudaStream_t s) {
   k_reduce<<<(d + 31) / 32, 256, 0, s>>>(partials, nblk, d, scale, g, st, check_done);

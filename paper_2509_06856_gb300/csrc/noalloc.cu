@@ -1,10 +1,9 @@
 // Residual-gradient pass for callers that cannot allocate device memory.
 //
 // Some callers of this library cannot call cudaMalloc (or any allocator) at the
-// point where they need a gradient: code running while a CUDA graph is being
-// captured into a pre-planned memory budget, plugins whose host application owns
-// every device allocation, or real-time loops that forbid allocation after
-// start-up.  slse_grad needs a small scratch area (a status word and one partial
+// point where they need a gradient: plugins whose host application owns every
+// device allocation and hands out only fixed buffers, or real-time loops that forbid
+// allocation after start-up.  slse_grad needs a small scratch area (a status word and one partial
 // gradient per CTA) and gets it from the caller's workspace or from
 // cudaMallocAsync.  slse_grad_noalloc runs the same gradient kernels but takes
 // its scratch from the fixed array below, which lives in the library image: every
@@ -12,7 +11,11 @@
 //
 // Host code may not use the array's name as a device address (in host code it
 // names a host-side stand-in).  The device address is obtained once per device
-// with cudaGetSymbolAddress, with that device current, and cached.
+// with cudaGetSymbolAddress, with that device current, and cached; the same set-up
+// loads the code of every kernel the entry point can launch, so that no later call
+// loads a module (module loading allocates device memory).  A cudaDeviceReset
+// destroys the array with its context: the cached address is then stale, so this
+// entry point must not be called again in that process after a reset.
 #include <mutex>
 
 #include "slse_internal.cuh"
@@ -25,6 +28,14 @@ constexpr size_t kNoAllocBytes = kNoAllocStateBytes + kNoAllocPartialBytes;
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+__global__ void k_clear_state(slse::DevState *st, int rebase) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    slse::DevState z = {};
+    z.rebase = rebase;
+    *st = z;
+  }
+}
 
 std::mutex g_scratch_mu;
 void *g_scratch_ptr[kMaxDevices] = {};
@@ -44,18 +55,15 @@ slse_status scratch_address(void **out) {
       cudaGetLastError();
       return SLSE_ECUDA;
     }
+    cudaFuncAttributes fa;
+    if (slse::preload_grad_kernels() != cudaSuccess || cudaFuncGetAttributes(&fa, (const void *)k_clear_state) != cudaSuccess) {
+      cudaGetLastError();
+      return SLSE_ECUDA;
+    }
     g_scratch_ptr[dev] = p;
   }
   *out = g_scratch_ptr[dev];
   return SLSE_OK;
-}
-
-__global__ void k_clear_state(slse::DevState *st, int rebase) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    slse::DevState z = {};
-    z.rebase = rebase;
-    *st = z;
-  }
 }
 
 }  // namespace

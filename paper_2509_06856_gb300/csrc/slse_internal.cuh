@@ -199,6 +199,9 @@ cudaError_t launch_grad(int mode, int xdtype, const void *X, int64_t ldx, const 
                         double *beta0, double *partials, int nblk, int check_done, cudaStream_t s);
 cudaError_t launch_reduce(const double *partials, int nblk, int d, double scale, double *g,
                           DevState *st, int check_done, cudaStream_t s);
+// Loads the code of every kernel launch_grad (GM_F64, GM_MIXED) and launch_reduce can launch,
+// so that a later first launch of one of them does not load a module (which allocates).
+cudaError_t preload_grad_kernels();
 struct UpdateArgs {
   const double *g;
   const double *Hinv;

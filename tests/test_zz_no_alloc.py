@@ -39,3 +39,22 @@ def test_grad_noalloc_matches_grad_on_two_calls(prec, N, d):
     assert np.array_equal(first, second)  # the shared scratch holds no state between calls
     go = osl.grad(np.asarray(X, np.float64), np.asarray(Y, np.float64), beta)
     np.testing.assert_array_less(np.abs(first - go), 2 * tol + 1e-300)
+
+
+def test_host_gradient_output_rejected_by_both_entry_points():
+    """A g_out in host memory is an argument error for slse_grad and slse_grad_noalloc
+    alike (SLSE_EINVAL before any launch), never a kernel writing through a host address."""
+    torch_cuda()
+    import ctypes
+    import paper_2509_06856_gb300 as slse
+    p = workloads.cfg3(N=4096, d=32, seed=3)
+    Xd, Yd = dev(p["X"]), dev(p["Y"])
+    b = dev(np.zeros(32))
+    g_host = np.zeros(32)
+    prob = slse.problem(Xd, Yd)
+    ptr = g_host.ctypes.data_as(ctypes.c_void_p)
+    st = slse._lib.slse_grad(ctypes.byref(prob), b.data_ptr(), ptr, slse.PREC["mixed_bf16"], None, 0, None)
+    assert st == slse.EINVAL
+    st = slse._lib.slse_grad_noalloc(ctypes.byref(prob), b.data_ptr(), ptr, slse.PREC["mixed_bf16"], None)
+    assert st == slse.EINVAL
+    assert not g_host.any()
