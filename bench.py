@@ -48,11 +48,16 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cs-steps", type=int, default=2, help="CountSketch-variant fits reported beside the SRHT line")
     ap.add_argument("--fp8-steps", type=int, default=2, help="fits with the FP8 form of the sketch")
+    ap.add_argument("--full-steps", type=int, default=2, help="fits with the full form of the 2nd stage")
+    ap.add_argument("--cfg2-steps", type=int, default=2, help="FP64 fits at N=2^20, d=256, cond 1e4")
+    ap.add_argument("--cfg4-steps", type=int, default=1, help="fits per form at N=2^24, d=256, heavy tails")
     ap.add_argument("--tuning-steps", type=int, default=2, help="fits with the SLSE-FRS-tuning schedule")
     ap.add_argument("--gauss-steps", type=int, default=2, help="fits with the Gaussian Hessian sketch")
     ap.add_argument("--diff-steps", type=int, default=2, help="forward+backward passes of the differentiation block")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--sample-log2n", type=int, default=15)
+    ap.add_argument("--sample-log2n", type=int, default=15, help="rows (log2) of each reference-arm step")
+    ap.add_argument("--cpu-rungs", default="16,17,18,19", help="log2 row counts of the oracle ladder")
+    ap.add_argument("--cpu-full", action="store_true", help="also time the oracle on the full workload (needs ~40 GB)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline timing (accuracy reference still runs)")
     return ap.parse_args()
 
@@ -209,6 +214,22 @@ def make_data(log2n, d):
     return workloads.cfg3(N=1 << log2n, d=d, seed=1003)
 
 
+def e4m3_values():
+    """The 256 values of the OCP E4M3 format (1 sign, 4 exponent bits with bias 7, 3 mantissa
+    bits; exponent field 0 is subnormal; S.1111.111 is NaN), indexed by the code byte."""
+    v = np.empty(256)
+    for c in range(256):
+        sgn = -1.0 if c & 0x80 else 1.0
+        e, f = (c >> 3) & 0xF, c & 0x7
+        if e == 0xF and f == 0x7:
+            v[c] = np.nan
+        elif e == 0:
+            v[c] = sgn * f * 2.0 ** -9
+        else:
+            v[c] = sgn * (1.0 + f / 8.0) * 2.0 ** (e - 7)
+    return v
+
+
 def first_crossing(hist, ms, bh, target):
     nb = np.linalg.norm(bh)
     errs = np.linalg.norm(hist - bh[None, :], axis=1) / nb
@@ -219,31 +240,71 @@ def first_crossing(hist, ms, bh, target):
 
 
 # ----------------------------------------------------------------------------- oracle legs
-def cpu_leg(X, Y, log2n, d, sample_log2n, time_it):
+def oracle_fit_seconds(X, Y, n, d, seed=0):
+    """Wall time of the oracle's Algorithm 2 (FP64, numpy) on the first n rows, with the
+    schedule rule of the workload at that size."""
+    from oracle import slse as osl
+    Xs, Ys = X[:n].astype(np.float64), Y[:n].astype(np.float64)
+    sched = osl.default_schedule(n, d, T=100, tol=1e-9)
+    t0 = time.time()
+    osl.slse_fit(Xs, Ys, sched, seed=seed)
+    return time.time() - t0
+
+
+def cost_model_fit(ns, ts):
+    """Least-squares fit of t(N) = c + a N log2 N + b N (Thm 4.4: the transform costs
+    N d log2 N, the passes O(N d) at fixed d; c is the size-independent QR of the r x d
+    Hessian sketch).  Returns a callable model."""
+    A = np.array([[1.0, n * math.log2(n), float(n)] for n in ns])
+    coef, *_ = np.linalg.lstsq(A, np.asarray(ts, np.float64), rcond=None)
+    return lambda n: float(coef[0] + coef[1] * n * math.log2(n) + coef[2] * n)
+
+
+def cpu_ladder(X, Y, log2n, d, rungs):
+    """The oracle timed on the first 2^k rows for each k in rungs (all host cores); the cost
+    model fitted on every rung but the largest predicts the largest (the check), and the fit
+    on all rungs gives the estimate at the full size."""
+    ts = [oracle_fit_seconds(X, Y, 1 << k, d) for k in rungs]
+    ns = [1 << k for k in rungs]
+    held = cost_model_fit(ns[:-1], ts[:-1])(ns[-1])
+    model = cost_model_fit(ns, ts)
+    return {"rungs": [{"rows": n, "seconds": t} for n, t in zip(ns, ts)],
+            "check": {"rows": ns[-1], "predicted_seconds": held, "measured_seconds": ts[-1],
+                      "rel_error": abs(held - ts[-1]) / ts[-1]},
+            "estimate_seconds": model(1 << log2n), "model": model}
+
+
+def cpu_leg(X, Y, log2n, d, rungs, full, time_it):
     """The only place the benchmark runs the oracle: the accuracy reference (OLS of the
-    full workload) and, optionally, the oracle's own SLSE-FRS timed on a bounded sample."""
-    from oracle import linalg, slse as osl
+    full workload) and, optionally, the oracle's own SLSE-FRS timed on the host cores: a
+    ladder of row counts fitted to the cost model (and, with ``full``, the full workload)."""
+    from oracle import linalg
     t0 = time.time()
     bh = linalg.ols_normal(X, Y)
     t_ref = time.time() - t0
     base = None
     if time_it:
-        ns = 1 << sample_log2n
-        Xs, Ys = X[:ns].astype(np.float64), Y[:ns].astype(np.float64)
-        sched = osl.default_schedule(ns, d, T=100, tol=1e-9)
-        t0 = time.time()
-        osl.slse_fit(Xs, Ys, sched, seed=0)
-        dt = time.time() - t0
-        scale = (1 << log2n) / ns
-        base = {"value": dt * 1000.0 * scale, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
-                "sample": f"oracle slse_fit (FP64, numpy) on the first 2^{sample_log2n} rows of the workload "
-                          f"(d={d}, same schedule rule), wall time x {scale:.0f} (linear in N); "
-                          f"BLAS on all cores, and once more with one thread",
-                "sample_seconds": dt}
-        dt1 = oracle_one_thread(Xs, Ys)
+        lad = cpu_ladder(X, Y, log2n, d, rungs)
+        est = lad.pop("model")(1 << log2n)
+        base = {"value": est * 1000.0, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+                "sample": (f"oracle slse_fit (FP64, numpy, BLAS on all cores) on the first 2^k rows of the workload "
+                           f"(d={d}, same schedule rule) for k in {list(rungs)}; value = the fit "
+                           f"t(N) = c + a N log2 N + b N of those times at N = 2^{log2n}; check: the fit "
+                           f"without the largest rung predicts it within rel_error"),
+                "ladder": lad}
+        if full:
+            tf = oracle_fit_seconds(X, Y, 1 << log2n, d)
+            base["value"] = tf * 1000.0
+            base["sample"] = f"oracle slse_fit on the full workload (2^{log2n} rows, d={d}), measured"
+            base["ladder_estimate_ms"] = est * 1000.0
+        # one thread: the same oracle in a fresh interpreter at the two smallest rungs; the
+        # estimate scales the all-core value by the measured one-thread / all-core ratio
+        k1 = rungs[1] if len(rungs) > 1 else rungs[0]
+        dt1 = oracle_one_thread(X[:1 << k1].astype(np.float64), Y[:1 << k1].astype(np.float64))
         if dt1 is not None:
-            base["value_1_thread"] = dt1 * 1000.0 * scale
-            base["sample_seconds_1_thread"] = dt1
+            tm = lad["rungs"][1 if len(rungs) > 1 else 0]["seconds"]
+            base["value_1_thread"] = base["value"] * dt1 / tm
+            base["one_thread"] = {"rows": 1 << k1, "seconds": dt1, "all_cores_seconds": tm}
     return bh, t_ref, base
 
 
@@ -266,6 +327,25 @@ def oracle_one_thread(Xs, Ys):
             return float(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
         except (subprocess.TimeoutExpired, ValueError, IndexError):
             return None
+
+
+def cpu_leg_cfg2(p):
+    """Oracle leg of the cfg2 block: the least-squares reference by Householder QR (cond(X) = 1e4)."""
+    from oracle import linalg
+    t0 = time.time()
+    bh = linalg.ols(p["X"], p["Y"])
+    return bh, time.time() - t0
+
+
+def cpu_leg_cfg4(p, m, seed, rows, cols):
+    """Oracle leg of the cfg4 block: the OLS reference (FP64 normal equations) and single sketch
+    entries from the definition with the oracle's own draws."""
+    from oracle import linalg, sketch as osk
+    t0 = time.time()
+    bh = linalg.ols_normal(p["X"], p["Y"])
+    D, P, sigma = osk.draws(osk.padded_size(p["X"].shape[0]), seed)
+    ref = osk.sketch_entries(p["X"], p["Y"], D, P, sigma, m, rows, cols)
+    return bh, ref, time.time() - t0
 
 
 def sketch_form_errors(slse, torch, seed=4):
@@ -297,31 +377,34 @@ def sketch_form_errors(slse, torch, seed=4):
 
 
 def run_reference(args, rank, ws):
+    """The reference arm: the oracle as it stands on the host cores (rank 0 only).  Each
+    step times the oracle fit on the first 2^sample rows of the workload; the step's
+    full-size figure scales that time by the cost model's ratio t(2^log2n) / t(2^sample),
+    the model fitted on a ladder of row counts timed once before the steps."""
     if rank != 0:
         return
-    from oracle import slse as osl
     import workloads
     d = args.d
     ns = 1 << args.sample_log2n
-    p = workloads.cfg3(N=ns, d=d, seed=1003)
-    Xs, Ys = p["X"].astype(np.float64), p["Y"].astype(np.float64)
-    sched = osl.default_schedule(ns, d, T=100, tol=1e-9)
+    rungs = [args.sample_log2n + k for k in range(4)]
+    p = workloads.cfg3(N=1 << rungs[-1], d=d, seed=1003)
+    X, Y = p["X"], p["Y"]
+    lad = cpu_ladder(X, Y, args.log2n, d, rungs)
+    model = lad.pop("model")
+    ratio = model(1 << args.log2n) / model(ns)
     for w in range(args.warmup):
-        osl.slse_fit(Xs, Ys, sched, seed=100 + w)
-    times = []
-    for k in range(args.steps):
-        t0 = time.time()
-        osl.slse_fit(Xs, Ys, sched, seed=k)
-        times.append(time.time() - t0)
-    scale = (1 << args.log2n) / ns
-    val = statistics.mean(times) * 1000.0 * scale
-    sample = (f"oracle slse_fit (FP64, numpy) per step on a 2^{args.sample_log2n}-row sample of the workload "
-              f"(d={d}, same schedule rule), wall time x {scale:.0f} (linear in N)")
+        oracle_fit_seconds(X, Y, ns, d, seed=100 + w)
+    times = [oracle_fit_seconds(X, Y, ns, d, seed=k) for k in range(args.steps)]
+    val = statistics.mean(times) * 1000.0 * ratio
+    sample = (f"oracle slse_fit (FP64, numpy) per step on the first 2^{args.sample_log2n} rows of the workload "
+              f"(d={d}, same schedule rule), times the ratio {ratio:.1f} of the cost model t(N) = c + a N log2 N "
+              f"+ b N fitted on rungs 2^{rungs[0]}..2^{rungs[-1]} at N = 2^{args.log2n} and 2^{args.sample_log2n}")
     out = {"metric": METRIC, "value": val, "unit": "ms", "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": statistics.mean(times) * 1000.0, "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
            "config": {"workload": workload_name(args.log2n, d), "N": 1 << args.log2n, "d": d, "sample_rows": ns},
-           "cpu_baseline": {"value": val, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": val, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle", "sample": sample,
+                            "ladder": lad},
            "e2e": {"value": val, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -348,7 +431,8 @@ def run_ours(args, rank, ws, local_rank):
     # accuracy reference (and CPU baseline at N = 1) from the oracle, rank 0
     bh, t_ref, cpu_base = (None, None, None)
     if rank == 0:
-        bh, t_ref, cpu_base = cpu_leg(X, Y, args.log2n, d, args.sample_log2n, time_it=(ws == 1 and not args.no_cpu))
+        rungs = [int(k) for k in args.cpu_rungs.split(",")]
+        bh, t_ref, cpu_base = cpu_leg(X, Y, args.log2n, d, rungs, args.cpu_full, time_it=(ws == 1 and not args.no_cpu))
 
     sched = slse.default_schedule(N, d, prec="mixed_bf16", T=100, tol=5e-9)
     wsz = slse.workspace_size(Xd, Yd, slse.OP_FIT, sched)
@@ -391,8 +475,12 @@ def run_ours(args, rank, ws, local_rank):
 
     # dominant kernel: 2nd-stage gradient vs the two sketch passes (summed CUDA-event times)
     rep = results[-1].report
+    # 2nd stage: the passes over X (exact passes of the correction form; the first also writes the
+    # BF16 copy) and the passes over the BF16 copy, each with its algorithmic bytes per launch
+    n_x = max(1, rep["n_grad2"])
     k_times = {
-        "grad_stage2": (rep["ms_grad2"], rep["n_grad2"], rep["bytes_grad2"]),
+        "grad_stage2": (rep["ms_grad2"], rep["n_grad2"], (n_x * rep["bytes_grad2"] + rep["bytes_xbf"]) / n_x),
+        "grad_stage2_bf16": (rep["ms_grad2_bf16"], rep["n_grad2_bf16"], rep["bytes_grad2_bf16"]),
         "srht_pass1": (rep["ms_srht_pass1"], 1, N * (d + 1) * 4.0 + N * (d + 1) * 2.0),
         "srht_pass2": (rep["ms_srht_pass2"], 1, N * (d + 1) * 2.0 + (sched.m[-1] + sched.r) * (d + 1) * 2.0),
     }
@@ -406,6 +494,7 @@ def run_ours(args, rank, ws, local_rank):
     ms_d, n_d, by_d = k_times[dom]
     achieved = by_d / (ms_d / n_d) / 1e6
     src = {"grad_stage2": ["paper_2509_06856_gb300/csrc/grad.cu"],
+           "grad_stage2_bf16": ["paper_2509_06856_gb300/csrc/grad.cu"],
            "srht_pass1": ["paper_2509_06856_gb300/csrc/srht.cu"],
            "srht_pass2": ["paper_2509_06856_gb300/csrc/srht.cu"]}[dom]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -439,6 +528,25 @@ def run_ours(args, rank, ws, local_rank):
                     "grad_stage2_ms_per_pass": r64["ms_grad2"] / max(1, r64["n_grad2"]),
                     "iters": [r64["iters_stage1"], r64["iters_stage2"]]}
         torch.cuda.empty_cache()
+
+    # the same fit with every 2nd-stage pass streaming X in FP32 (the full form), for comparison with
+    # the default correction form (passes over a BF16 copy between exact FP32 passes)
+    s2full = None
+    if args.full_steps > 0:
+        sf = slse.default_schedule(N, d, prec="mixed_bf16", T=100, tol=5e-9, stage2="full")
+        tf, fin = [], []
+        for k in range(args.full_steps + 1):
+            r = slse.fit(Xd, Yd, sf, seed=k, workspace=wbuf, trace_cap=cap)
+            if rank == 0 and k > 0:
+                a8, _ = first_crossing(r.beta_hist.cpu().numpy(), np.array(r.ms_hist), bh, TARGET)
+                tf.append(a8)
+                fin.append(float(np.linalg.norm(r.beta - bh) / np.linalg.norm(bh)))
+        if rank == 0:
+            rf = r.report
+            s2full = {"time_to_1e-8_ms": statistics.mean(tf) if all(v is not None for v in tf) else None,
+                      "final_rel_err": max(fin), "ms_stage2": rf["ms_stage2"],
+                      "passes_over_x": rf["n_grad2"], "iters": [rf["iters_stage1"], rf["iters_stage2"]],
+                      "grad_ms_per_pass": rf["ms_grad2"] / max(1, rf["n_grad2"])}
 
     # FP8 form of the sketch on the same workload (1st-stage sketches in E4M3 + block scales)
     f8 = None
@@ -597,6 +705,102 @@ def run_ours(args, rank, ws, local_rank):
         del X5, Y5, dX5, dY5
         torch.cuda.empty_cache()
 
+    # plain FP64 on the GPU at N = 2^20, d = 256, cond(X) = 1e4, sketch sizes 2d .. 64d (a_i = 2,
+    # r = 6d): time to 1e-10 and the final error against the oracle's QR least-squares solution
+    c2 = None
+    if args.cfg2_steps > 0:
+        import workloads
+        t0 = time.time()
+        p2 = workloads.cfg2()
+        gen2 = time.time() - t0
+        bh2, tref2 = cpu_leg_cfg2(p2) if rank == 0 else (None, None)
+        n2, d2 = p2["X"].shape
+        X2, Y2 = torch.from_numpy(p2["X"]).cuda(), torch.from_numpy(p2["Y"]).cuda()
+        m2 = [2 * d2 * 2 ** t for t in range(6)]
+        r2 = 6 * d2
+        s2 = slse.Schedule(m=m2, a=[2] * len(m2), r=r2, mu=(1 - d2 / r2) ** 2, eta=d2 / r2, T=100, tol=1e-13)
+        w2 = slse.alloc_workspace(slse.workspace_size(X2, Y2, slse.OP_FIT, s2))
+        t10, t8, fin, tot = [], [], [], []
+        for k in range(args.cfg2_steps + 1):
+            r = slse.fit(X2, Y2, s2, seed=k, workspace=w2, trace_cap=s2.T)
+            if rank == 0 and k > 0:
+                h, ms = r.beta_hist.cpu().numpy(), np.array(r.ms_hist)
+                t10.append(first_crossing(h, ms, bh2, 1e-10)[0])
+                t8.append(first_crossing(h, ms, bh2, 1e-8)[0])
+                fin.append(float(np.linalg.norm(r.beta - bh2) / np.linalg.norm(bh2)))
+                tot.append(r.report["ms_total"])
+        if rank == 0:
+            rr = r.report
+            c2 = {"workload": f"N=2^20, d={d2}, X fp64 = G diag(s) V^T, cond 1e4, sigma=1e-2",
+                  "schedule": f"m={m2[0]}..{m2[-1]} (x2), a_i=2, r={r2}, T=100, tol=1e-13",
+                  "time_to_1e-10_ms": statistics.mean(t10) if all(v is not None for v in t10) else None,
+                  "time_to_1e-8_ms": statistics.mean(t8) if all(v is not None for v in t8) else None,
+                  "ms_per_fit": statistics.mean(tot), "final_rel_err": max(fin),
+                  "reference": "oracle OLS by Householder QR", "reference_seconds": tref2,
+                  "data_gen_seconds": gen2,
+                  "phases_ms": {k: rr[k] for k in ("ms_draws", "ms_sketch", "ms_qr", "ms_stage1", "ms_stage2")},
+                  "iters": [rr["iters_stage1"], rr["iters_stage2"]],
+                  "grad_ms_per_pass": rr["ms_grad2"] / max(1, rr["n_grad2"]),
+                  "grad_fp64_tflops": 4.0 * n2 * d2 / (rr["ms_grad2"] / max(1, rr["n_grad2"])) / 1e9}
+        del X2, Y2, w2, p2
+        torch.cuda.empty_cache()
+
+    # heavy tails at N = 2^24, d = 256 (X FP32, Student-t(3), 0.1% of rows x100): per stored form of
+    # the sketch (FP64, BF16, FP8) the fit's time to its target and final error against the FP64
+    # oracle, and sampled entries of one m = 4096 sketch against the definition
+    c4 = None
+    if args.cfg4_steps > 0:
+        import workloads
+        t0 = time.time()
+        p4 = workloads.cfg4()
+        gen4 = time.time() - t0
+        n4, d4 = p4["X"].shape
+        m4, seed4 = 4096, 7
+        rows4, cols4 = [0, 1, 2047, m4 - 1], [0, 1, 100, d4 - 1, d4]
+        bh4, ref4, tref4 = cpu_leg_cfg4(p4, m4, seed4, rows4, cols4) if rank == 0 else (None, None, None)
+        X4, Y4 = torch.from_numpy(p4["X"]).cuda(), torch.from_numpy(p4["Y"]).cuda()
+        c4 = {"workload": "N=2^24, d=256, X fp32 Student-t(3), 0.1% of rows x100, beta~U(-1,1), sigma=1",
+              "reference": "oracle OLS, FP64 normal equations; sketch entries from the definition",
+              "reference_seconds": tref4, "data_gen_seconds": gen4, "by_form": {}}
+        colrms = np.sqrt(np.mean(ref4 ** 2, axis=0)) if rank == 0 else None
+        for prec, target in (("fp64", 1e-10), ("mixed_bf16", 1e-8), ("mixed_fp8", 1e-8)):
+            s4 = slse.default_schedule(n4, d4, prec=prec, T=100, tol=1e-13 if prec == "fp64" else 5e-9)
+            w4 = slse.alloc_workspace(slse.workspace_size(X4, Y4, slse.OP_FIT, s4))
+            tt, fin = [], []
+            for k in range(args.cfg4_steps + 1):
+                r = slse.fit(X4, Y4, s4, seed=k, workspace=w4, trace_cap=s4.T)
+                if rank == 0 and k > 0:
+                    tt.append(first_crossing(r.beta_hist.cpu().numpy(), np.array(r.ms_hist), bh4, target)[0])
+                    fin.append(float(np.linalg.norm(r.beta - bh4) / np.linalg.norm(bh4)))
+            del w4
+            torch.cuda.empty_cache()
+            # the stored sketch of this form at sampled entries
+            if prec == "mixed_fp8":
+                codes, scales, sy = slse.sketch(X4, Y4, m4, seed=seed4, prec=prec)
+                c8, s8, y8 = codes.cpu().numpy(), scales.cpu().numpy(), sy.float().cpu().numpy()
+                e4m3 = e4m3_values()
+                got = np.array([[e4m3[c8[i, c]] * 2.0 ** (int(s8[i, c // 32]) - 127) if c < d4 else y8[i]
+                                 for c in cols4] for i in rows4])
+            else:
+                sx, sy = slse.sketch(X4, Y4, m4, seed=seed4, prec=prec)
+                a_ = sx.double().cpu().numpy()
+                b_ = sy.double().cpu().numpy()
+                got = np.array([[a_[i, c] if c < d4 else b_[i] for c in cols4] for i in rows4])
+            torch.cuda.empty_cache()
+            if rank == 0:
+                rr = r.report
+                e = np.abs(got - ref4) / colrms
+                c4["by_form"][prec] = {
+                    "target": target,
+                    "time_to_target_ms": statistics.mean(tt) if all(v is not None for v in tt) else None,
+                    "final_rel_err_vs_fp64_oracle": max(fin),
+                    "phases_ms": {k: rr[k] for k in ("ms_sketch", "ms_qr", "ms_stage1", "ms_stage2", "ms_total")},
+                    "iters": [rr["iters_stage1"], rr["iters_stage2"]],
+                    "sketch_entry_err_over_col_rms": {"max": float(e.max()), "mean": float(e.mean()),
+                                                      "m": m4, "entries": len(rows4) * len(cols4)}}
+        del X4, Y4, p4
+        torch.cuda.empty_cache()
+
     # end to end through the public API with pinned host inputs (copy inside the call)
     e2e = None
     if args.e2e_steps > 0:
@@ -625,7 +829,7 @@ def run_ours(args, rank, ws, local_rank):
         "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_name(args.log2n, d), "N": N, "d": d, "X_dtype": "fp32", "precision": "mixed_bf16",
-                   "schedule": f"m={sched.m[0]}..{sched.m[-1]} (x2), a_i=2, r={sched.r}, T=100, tol=5e-9",
+                   "schedule": f"m={sched.m[0]}..{sched.m[-1]} (x2), a_i=2, r={sched.r}, T=100, tol=5e-9, 2nd stage {sched.stage2} form",
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "l2": "inputs larger than L2 (X is 8.6 GB)", "seeds": f"sketch seeds 0..{args.steps - 1}"},
         "roofline": roofline,
@@ -641,9 +845,13 @@ def run_ours(args, rank, ws, local_rank):
         "fp8": f8,
         "gaussian": gau,
         "differentiation": diff,
+        "cfg2": c2,
+        "cfg4": c4,
         "phases_ms": {k: rep[k] for k in ("ms_draws", "ms_sketch", "ms_srht_pass1", "ms_srht_pass2", "ms_qr",
                                           "ms_stage1", "ms_stage2", "ms_total")},
         "iters": [rep["iters_stage1"], rep["iters_stage2"]], "rebases": rep["rebases"],
+        "stage2": {"form": sched.stage2, "exact_passes": rep["n_grad2"], "bf16_passes": rep["n_grad2_bf16"],
+                   "fell_back_to_full": rep["stage2_full"], "full_form": s2full},
         "kernels": kernels_gbs, "data_gen_seconds": t_gen,
     }
     print(json.dumps(out), flush=True)

@@ -91,6 +91,23 @@ typedef enum { SLSE_SRHT = 0, SLSE_COUNTSKETCH = 1, SLSE_GAUSSIAN = 2, SLSE_COUN
  *   counterpart (the paper's sketches are double precision).  Requires X F32, kind SRHT. */
 typedef enum { SLSE_PREC_FP64 = 0, SLSE_PREC_MIXED_BF16 = 1, SLSE_PREC_MIXED_FP8 = 2 } slse_precision;
 
+/* Form of the 2nd-stage passes (Eq. (8)) on the mixed precisions; ignored by SLSE_PREC_FP64.
+ * SLSE_STAGE2_FULL: every 2nd-stage step streams X in FP32 (the compensated residual-gradient
+ *   pass of SLSE_PREC_MIXED_BF16).
+ * SLSE_STAGE2_CORRECTION: defect correction of the same iteration.  An exact pass (the FP32
+ *   pass above, which re-bases) gives g(b0) = X^T (Y - X b0); the steps after it use
+ *   g(b) = g(b0) - Xb^T Xb (b - b0), one pass over a BF16 copy Xb of X (half the bytes), which
+ *   the first exact pass writes while it streams X.  The next exact pass comes when a step falls
+ *   below 1/100 of the first step after the last exact pass, rises above it, or meets the
+ *   stopping test; the iteration stops only on the step of an exact pass, so the stopping test
+ *   and the fixed point (g(b) = 0, the least-squares estimate) are those of the full form.  When
+ *   a cycle (an exact pass and k BF16 passes) shrinks the exact step by less than
+ *   rho^(1 + k/2), rho = sqrt(d/r), i.e. less than full-form steps gain for the same bytes (the
+ *   BF16 Hessian term too coarse for an ill-conditioned X), the remaining steps take the full
+ *   form.  Requires d % 8 == 0 and 16-byte aligned rows (else the full form runs).  No paper counterpart (the paper streams X in
+ *   double precision); workspace grows to hold N x ceil(d/8)*8 BF16 values. */
+typedef enum { SLSE_STAGE2_FULL = 0, SLSE_STAGE2_CORRECTION = 1 } slse_stage2_form;
+
 typedef struct {
   int64_t N;       /* rows, N >= d */
   int32_t d;       /* columns, 1 <= d <= 512 */
@@ -117,6 +134,7 @@ typedef struct {
   int32_t prec;         /* slse_precision */
   int32_t momentum_reset; /* 0: momentum carries across subproblems (Algorithm 2's global t);
                              1: beta_{-1} = beta_0 at each subproblem and at the 2nd stage (proof of Thm 4.1) */
+  int32_t stage2;       /* slse_stage2_form (mixed precisions; ignored by FP64) */
 } slse_schedule;
 
 typedef struct {
@@ -131,8 +149,14 @@ typedef struct {
   double final_rel_step;  /* ||b_T - b_{T-1}|| / ||b_T|| of the last iteration */
   double bytes_moved;     /* algorithmic HBM bytes of the sketch passes and gradient passes */
   double bytes_grad2;     /* algorithmic HBM bytes of one 2nd-stage gradient pass */
-  int32_t rebases;        /* mixed path: number of 2nd-stage residual re-bases */
+  int32_t rebases;        /* mixed path: number of 2nd-stage residual re-bases (exact passes) */
   int32_t status;
+  double ms_grad2_bf16;   /* SLSE_STAGE2_CORRECTION: summed CUDA-event time of the passes over the BF16
+                             copy of X (not included in ms_grad2, which then covers the exact passes) */
+  int32_t n_grad2_bf16;   /* number of those passes */
+  int32_t stage2_full;    /* 1 if a correction run fell back to the full form */
+  double bytes_grad2_bf16; /* algorithmic HBM bytes of one pass over the BF16 copy */
+  double bytes_xbf;       /* bytes of the BF16 copy, written once by the first exact pass */
 } slse_report;
 
 typedef struct {
@@ -225,7 +249,8 @@ slse_status slse_qr(const double *A, int64_t r, int32_t d, int64_t lda, double *
 
 /* The paper's experimental schedule (Sec. 5 preamble): r = 6d, eta = d/r, mu = (1-eta)^2,
  * m_1 = 8d doubling while m_i <= N'/2, a_i = 2, T = 100, tol = 0, FP64, momentum carried
- * across subproblems as in Algorithm 2.
+ * across subproblems as in Algorithm 2; stage2 = SLSE_STAGE2_CORRECTION (used only if prec is
+ * set to a mixed precision).
  * Writes at most cap entries into m_buf/a_buf (host) and points out->m/out->a at them.
  * Returns K (the number of sizes the schedule wants; > cap means truncated). */
 int32_t slse_default_schedule(int64_t N, int32_t d, slse_schedule *out, int64_t *m_buf, int32_t *a_buf,

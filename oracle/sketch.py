@@ -128,3 +128,26 @@ def sketch_matrix_dense(N: int, m: int, seed: int) -> np.ndarray:
     B[np.arange(m), sigma[:m]] = 1.0
     S = math.sqrt(Np / m) * B @ H @ np.diag(D) @ Pm
     return S[:, :N]
+
+
+def sketch_entries(X, Y, D, P, sigma, m: int, rows, cols) -> np.ndarray:
+    """Single entries of the sketch S [X | Y] computed one by one from the definition of Sec. 3
+    (for sampled checks at sizes where the full transform is too large): entry (s, c) is
+    sqrt(N'/m) * (H D P [X | Y]_pad)[sigma[s], c] / sqrt(N') = sum_j (-1)^popcount(k & j) D_j
+    [X | Y][P_j, c] / sqrt(m) with k = sigma[s], over the j with P_j < N (the padding rows are
+    zero).  Column c = d is Y.  Returns a len(rows) x len(cols) array."""
+    X = np.asarray(X)
+    N, d = X.shape
+    Np = D.shape[0]
+    j = np.arange(Np, dtype=np.int64)
+    live = P < N
+    src = P[live]
+    cols_data = [np.asarray(Y if c == d else X[:, c], np.float64)[src] for c in cols]
+    out = np.empty((len(rows), len(cols)))
+    for a, s in enumerate(rows):
+        k = int(sigma[s])
+        sgn = np.where(np.bitwise_count(j & k) % 2 == 0, 1.0, -1.0) * D
+        w = sgn[live]
+        for b, col in enumerate(cols_data):
+            out[a, b] = float(np.dot(w, col)) / math.sqrt(m)
+    return out

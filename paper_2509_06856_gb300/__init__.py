@@ -30,6 +30,7 @@ F64, F32, BF16 = 0, 1, 2
 SRHT, COUNTSKETCH, GAUSSIAN, COUNTSKETCH_HAT = 0, 1, 2, 3
 KIND = {"srht": SRHT, "countsketch": COUNTSKETCH, "countsketch_hat": COUNTSKETCH_HAT, "gaussian": GAUSSIAN}
 PREC = {"fp64": 0, "mixed_bf16": 1, "mixed_fp8": 2}
+STAGE2 = {"full": 0, "correction": 1}
 OP_FIT, OP_SKETCH, OP_GRAD, OP_DRAWS, OP_QR = range(5)
 
 
@@ -42,7 +43,7 @@ class CSchedule(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int32), ("m", ctypes.POINTER(ctypes.c_int64)), ("a", ctypes.POINTER(ctypes.c_int32)),
                 ("r", ctypes.c_int64), ("mu", ctypes.c_double), ("eta", ctypes.c_double), ("T", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("kind", ctypes.c_int32), ("prec", ctypes.c_int32),
-                ("momentum_reset", ctypes.c_int32)]
+                ("momentum_reset", ctypes.c_int32), ("stage2", ctypes.c_int32)]
 
 
 class CReport(ctypes.Structure):
@@ -52,7 +53,9 @@ class CReport(ctypes.Structure):
                 ("ms_grad2", ctypes.c_double), ("n_grad2", ctypes.c_int32), ("kernels", ctypes.c_int32),
                 ("iters_stage1", ctypes.c_int32), ("iters_stage2", ctypes.c_int32),
                 ("final_rel_step", ctypes.c_double), ("bytes_moved", ctypes.c_double),
-                ("bytes_grad2", ctypes.c_double), ("rebases", ctypes.c_int32), ("status", ctypes.c_int32)]
+                ("bytes_grad2", ctypes.c_double), ("rebases", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("ms_grad2_bf16", ctypes.c_double), ("n_grad2_bf16", ctypes.c_int32), ("stage2_full", ctypes.c_int32),
+                ("bytes_grad2_bf16", ctypes.c_double), ("bytes_xbf", ctypes.c_double)]
 
 
 class CTrace(ctypes.Structure):
@@ -144,6 +147,7 @@ class Schedule:
     prec: str = "fp64"
     momentum_reset: bool = False
     kind: int = SRHT
+    stage2: str = "correction"   # mixed precisions: "full" or "correction" (see slse_stage2_form)
     _keep: list = field(default_factory=list, repr=False)
 
     def to_c(self) -> CSchedule:
@@ -154,11 +158,11 @@ class Schedule:
         return CSchedule(K, ctypes.cast(m_arr, ctypes.POINTER(ctypes.c_int64)),
                          ctypes.cast(a_arr, ctypes.POINTER(ctypes.c_int32)), int(self.r), float(self.mu),
                          float(self.eta), int(self.T), float(self.tol), int(self.kind), PREC[self.prec],
-                         1 if self.momentum_reset else 0)
+                         1 if self.momentum_reset else 0, STAGE2[self.stage2])
 
 
 def default_schedule(N: int, d: int, prec: str = "fp64", T: int = 100, tol: float = 0.0,
-                     kind: str = "srht") -> Schedule:
+                     kind: str = "srht", stage2: str | None = None) -> Schedule:
     """The paper's experimental schedule (Sec. 5 preamble), from the library; kind "countsketch"
     rounds m_1 = 8d up to a power of two."""
     c = CSchedule()
@@ -168,11 +172,12 @@ def default_schedule(N: int, d: int, prec: str = "fp64", T: int = 100, tol: floa
     if K < 0 or K > 64:
         raise ValueError("invalid problem size")
     return Schedule(m=list(mb[:K]), a=list(ab[:K]), r=c.r, mu=c.mu, eta=c.eta, T=T, tol=tol, prec=prec,
-                    momentum_reset=bool(c.momentum_reset), kind=c.kind)
+                    momentum_reset=bool(c.momentum_reset), kind=c.kind,
+                    stage2=stage2 or {v: n for n, v in STAGE2.items()}[c.stage2])
 
 
 def tuning_schedule(N: int, d: int, prec: str = "fp64", T: int = 100, tol: float = 0.0,
-                    kind: str = "srht") -> Schedule:
+                    kind: str = "srht", stage2: str | None = None) -> Schedule:
     """The SLSE-FRS-tuning schedule (Sec. 5, sketch size tuning), from the library."""
     c = CSchedule()
     mb = (ctypes.c_int64 * 64)()
@@ -181,7 +186,8 @@ def tuning_schedule(N: int, d: int, prec: str = "fp64", T: int = 100, tol: float
     if K < 0 or K > 64:
         raise ValueError("invalid problem size")
     return Schedule(m=list(mb[:K]), a=list(ab[:K]), r=c.r, mu=c.mu, eta=c.eta, T=T, tol=tol, prec=prec,
-                    momentum_reset=bool(c.momentum_reset), kind=c.kind)
+                    momentum_reset=bool(c.momentum_reset), kind=c.kind,
+                    stage2=stage2 or {v: n for n, v in STAGE2.items()}[c.stage2])
 
 
 # ----------------------------------------------------------------------------- helpers

@@ -67,6 +67,7 @@ struct Sched {
   double mu, eta, tol;
   int T, prec, momentum_reset;
   int kind = SLSE_SRHT;
+  int stage2 = SLSE_STAGE2_CORRECTION;
 };
 
 bool is_pow2(int64_t m) { return m >= 1 && (m & (m - 1)) == 0; }
@@ -84,8 +85,10 @@ bool make_sched(const slse_problem *p, const slse_schedule *s, Sched &o) {
     o.r = d.r; o.mu = d.mu; o.eta = d.eta; o.tol = d.tol; o.T = d.T; o.prec = d.prec;
     o.momentum_reset = d.momentum_reset;
     o.kind = SLSE_SRHT;
+    o.stage2 = d.stage2;
     return true;
   }
+  if (s->stage2 != SLSE_STAGE2_FULL && s->stage2 != SLSE_STAGE2_CORRECTION) return false;
   if (s->K < 0 || (s->K > 0 && (!s->m || !s->a))) return false;
   if (s->kind != SLSE_SRHT && s->kind != SLSE_COUNTSKETCH && s->kind != SLSE_GAUSSIAN) return false;
   if (s->prec != SLSE_PREC_FP64 && s->prec != SLSE_PREC_MIXED_BF16 && s->prec != SLSE_PREC_MIXED_FP8) return false;
@@ -105,6 +108,7 @@ bool make_sched(const slse_problem *p, const slse_schedule *s, Sched &o) {
   o.r = s->r; o.mu = s->mu; o.eta = s->eta; o.tol = s->tol; o.T = s->T; o.prec = s->prec;
   o.momentum_reset = s->momentum_reset;
   o.kind = s->kind;
+  o.stage2 = s->stage2;
   return true;
 }
 
@@ -129,7 +133,8 @@ struct FitLayout {
   std::vector<int64_t> lvl_off;  // CountSketch: first row in U of the sketch of each schedule size
   int nblk;
   bool host_in;
-  size_t o_xin, o_yin;
+  bool dc;                  // mixed 2nd stage in correction form (BF16 copy of X in the big region)
+  size_t o_xin, o_yin, o_g0, o_be, o_de;
   size_t o_state, o_psd, o_sigma, o_pos, o_big, o_wy, o_u, o_v, o_A, o_R, o_Hinv, o_qr, o_chol, o_part, o_g,
       o_ring, o_b0, o_d32, o_out, o_r0, o_us, o_hat16;
   size_t total;
@@ -181,6 +186,13 @@ FitLayout fit_layout(const slse_problem *p, const Sched &s, int nsm) {
     L.gp = gauss_plan(p->N, d, s.prec, s.r, false, nsm);
     if (L.gp.total > big) big = L.gp.total;
   }
+  // correction form of the mixed 2nd stage: vector rows (d % 8 == 0, 16-byte aligned FP32 rows; a host
+  // X is copied with ld = d into the 256-byte aligned workspace); its BF16 copy of X takes the big
+  // region, whose SRHT, CountSketch or Gaussian temporaries are dead by the 2nd stage
+  L.host_in = is_host_pointer(p->X);
+  L.dc = s.prec != SLSE_PREC_FP64 && s.stage2 == SLSE_STAGE2_CORRECTION && d % 8 == 0 &&
+         (L.host_in || (reinterpret_cast<uintptr_t>(p->X) % 16 == 0 && p->ldx % 4 == 0));
+  if (L.dc && (size_t)p->N * L.ld16 * 2 > big) big = (size_t)p->N * L.ld16 * 2;
   L.o_big = w.take(big);
   L.o_wy = L.o_big + align256(wbytes);
   L.o_u = w.take((size_t)L.n_samp * L.ldu * eu);
@@ -199,7 +211,9 @@ FitLayout fit_layout(const slse_problem *p, const Sched &s, int nsm) {
   L.o_d32 = w.take((size_t)d * 4);
   L.o_out = w.take((size_t)d * 8);
   L.o_r0 = w.take(s.prec != SLSE_PREC_FP64 ? (size_t)p->N * 4 : 0);
-  L.host_in = is_host_pointer(p->X);
+  L.o_g0 = w.take(L.dc ? (size_t)d * 8 : 0);
+  L.o_be = w.take(L.dc ? (size_t)d * 8 : 0);
+  L.o_de = w.take(L.dc ? (size_t)d * 4 : 0);
   if (L.host_in) {
     const size_t bx = p->dtype == SLSE_F64 ? 8 : 4;
     L.o_xin = w.take((size_t)p->N * d * bx);
@@ -258,10 +272,16 @@ __global__ void k_init_state(DevState *st, int rebase, long long spin_limit) {
 __global__ void k_clear_numeric(DevState *st) {
   if (threadIdx.x == 0 && blockIdx.x == 0) st->status &= ~ST_NUMERIC;
 }
-__global__ void k_set_stage2(DevState *st, int rebase) {
+__global__ void k_set_stage2(DevState *st, int rebase, int dc) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     st->rebase = rebase;
     st->done = 0;
+    st->dc = dc;
+    st->bfnext = 0;
+    st->dc_fell_back = 0;
+    st->step_ref = 0.0;
+    st->step_prev = 0.0;
+    st->ninner = 0;
   }
 }
 
@@ -620,30 +640,39 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
   // Iteration k+1 is enqueued before the stop flag of iteration k is read back; its
   // kernels return at once when the flag is already set.
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> e_grad;
+  // correction form: the BF16 copy of X in the big region, g(beta_0) beside the gradient
+  __nv_bfloat16 *xbf = L.dc ? static_cast<__nv_bfloat16 *>(big) : nullptr;
+  double *g0 = L.dc ? reinterpret_cast<double *>(base + L.o_g0) : nullptr;
+  float *de = L.dc ? reinterpret_cast<float *>(base + L.o_de) : nullptr;
+  ua.hist_base = t;
+  ua.beta_e = L.dc ? reinterpret_cast<double *>(base + L.o_be) : nullptr;
+  ua.delta_e = de;
   if (t < T) {
-    k_set_stage2<<<1, 32, 0, st>>>(dst, mixed ? 1 : 0);
+    k_set_stage2<<<1, 32, 0, st>>>(dst, mixed ? 1 : 0, L.dc ? 1 : 0);
     CK(cudaGetLastError());
     ++kernels;
     DevState *mb = t_mailbox.get();
     if (!mb) return SLSE_ECUDA;
     const double rho = std::sqrt((double)d / (double)s.r);
     const double thr = s.tol > 0.0 ? s.tol * (1.0 - rho) / rho : 0.0;
+    ua.rho = rho;
     const int nb = L.nblk;
     cudaEvent_t e_flag[2] = {E.make(), E.make()};
     if (!e_flag[0] || !e_flag[1]) return SLSE_ECUDA;
     for (int k = 0; t + k < T; ++k) {
-      cudaEvent_t g0 = E.make(), g1 = E.make();
-      if (!g0 || !g1) return SLSE_ECUDA;
-      CK(cudaEventRecord(g0, st));
-      CK(launch_grad(mixed ? GM_MIXED : GM_F64, p->dtype, p->X, p->ldx, p->Y, p->N, d, ring, dst, d32, r0, b0,
-                     part, nb, 1, st));
+      cudaEvent_t g0e = E.make(), g1 = E.make();
+      if (!g0e || !g1) return SLSE_ECUDA;
+      CK(cudaEventRecord(g0e, st));
+      // correction form: the first pass (exact, as every first 2nd-stage pass) also writes the BF16 copy
+      CK(launch_grad(L.dc ? GM_MIXED_DC : (mixed ? GM_MIXED : GM_F64), p->dtype, p->X, p->ldx, p->Y, p->N, d, ring,
+                     dst, d32, r0, b0, part, nb, 1, st, xbf, L.ld16, k == 0 ? 1 : 0, de));
       CK(cudaEventRecord(g1, st));
-      e_grad.emplace_back(g0, g1);
-      CK(launch_reduce(part, nb, d, 1.0, g, dst, 1, st));
+      e_grad.emplace_back(g0e, g1);
+      CK(launch_reduce(part, nb, d, 1.0, g, dst, 1, st, g0));
       ua.first = (k == 0 && s.momentum_reset) || (t + k) == 0;
       ua.stage2 = 1; ua.thr = thr; ua.mixed = mixed ? 1 : 0; ua.check_done = 1;
       CK(launch_update(ua, dst, st));
-      kernels += mixed ? 4 : 3;
+      kernels += L.dc ? 5 : (mixed ? 4 : 3);
       CK(mark_iter(t + k));
       CK(cudaMemcpyAsync(&mb[k & 1], dst, sizeof(DevState), cudaMemcpyDeviceToHost, st));
       CK(cudaEventRecord(e_flag[k & 1], st));
@@ -677,12 +706,26 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     RP->ms_stage1 = ms_between(e_qr, e_s1);
     RP->ms_total = ms_between(e_start, e_end);
     RP->ms_stage2 = RP->ms_total - ms_between(e_start, e_s1);
-    // gradient launches that ran a full pass (the speculative one after the stop returns at once)
+    // gradient launches that ran a full pass (the speculative one after the stop returns at once),
+    // split by pass kind: over X (exact or full form) or over its BF16 copy (correction form)
     const int full = fin.iter - t1;
-    double mg = 0.0;
-    for (int k = 0; k < full && k < (int)e_grad.size(); ++k) mg += ms_between(e_grad[k].first, e_grad[k].second);
+    double mg = 0.0, mb16 = 0.0;
+    int nx = 0, nb16 = 0;
+    for (int k = 0; k < full && k < (int)e_grad.size(); ++k) {
+      const double ms = ms_between(e_grad[k].first, e_grad[k].second);
+      if (k < (int)sizeof(fin.mode_hist) && fin.mode_hist[k] == 1) {
+        mb16 += ms;
+        ++nb16;
+      } else {
+        mg += ms;
+        ++nx;
+      }
+    }
     RP->ms_grad2 = mg;
-    RP->n_grad2 = full;
+    RP->n_grad2 = nx;
+    RP->ms_grad2_bf16 = mb16;
+    RP->n_grad2_bf16 = nb16;
+    RP->stage2_full = fin.dc_fell_back;
     RP->kernels = kernels;
     RP->iters_stage1 = t1;
     RP->iters_stage2 = fin.iter - t1;
@@ -698,7 +741,12 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     for (size_t i = 0; i < s.m.size(); ++i) bytes += (double)s.a[i] * (double)s.m[i] * (d + 1) * bu;
     // a 2nd-stage pass reads X and one N-vector (Y in FP64 / rebase passes, r0 otherwise)
     RP->bytes_grad2 = (double)p->N * d * bx + (double)p->N * (mixed ? 4.0 : bx);
-    bytes += (double)full * RP->bytes_grad2;
+    bytes += (double)nx * RP->bytes_grad2;
+    if (L.dc) {
+      RP->bytes_grad2_bf16 = (double)p->N * d * 2.0;
+      RP->bytes_xbf = (double)p->N * d * 2.0;
+      bytes += (double)nb16 * RP->bytes_grad2_bf16 + RP->bytes_xbf;
+    }
     RP->bytes_moved = bytes;
     RP->status = status;
   }
@@ -938,6 +986,7 @@ int32_t slse_default_schedule_for(int64_t N, int32_t d, int32_t kind, slse_sched
   out->kind = kind;
   out->prec = SLSE_PREC_FP64;
   out->momentum_reset = 0;  // Algorithm 2: one global counter t, momentum carries
+  out->stage2 = SLSE_STAGE2_CORRECTION;
   return K;
 }
 

@@ -21,6 +21,16 @@
 // ~2^-14 of the step, i.e. of the iterate's current error, so passes far from the
 // solution (the first steps from beta = 0) keep one base point instead of re-basing at
 // every step, and the final base point lies within 2^-10 of the solution.
+//
+// Correction form of the mixed 2nd stage (GM_MIXED_DC): exact passes stream X (the re-basing pass
+// above, which the first time also stores a BF16 copy Xb of X as it streams the rows, or the plain
+// FP32 pass); the reduction keeps their gradient g(beta_e).  The passes between exact ones read only
+// Xb and return -Xb^T (Xb delta), delta = fl32(beta - beta_e), so that
+// g(beta) = g(beta_e) - Xb^T Xb (beta - beta_e): half the bytes of an FP32 pass.  The update kernel
+// schedules the next exact pass (a step below 1/100 of the first step after the last exact pass, a
+// step above it, or one that meets the stopping test), makes it a re-basing pass only when the drift
+// from beta_0 exceeds 2^-10 ||beta||, stops only on an exact step, and switches to the plain FP32
+// passes when a cycle gains less than plain steps would for the same bytes.
 #include "slse_internal.cuh"
 
 namespace slse {
@@ -43,6 +53,9 @@ struct GradArgs {
   double *beta0;
   double *partials;
   int check_done;
+  __nv_bfloat16 *xbf;  // correction form: the BF16 copy of X (ld ldb)
+  int64_t ldb;
+  const float *delta_e;  // correction form: fl32(beta - beta_e)
 };
 
 template <class Tx, int VW> struct Vec;
@@ -166,23 +179,28 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_f64(const GradArgs a) {
 __device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
 
-template <int VMAX, int RPW>
+// CORR = 1: the correction-form pass over the BF16 copy of X (rows a.xbf, ld a.ldb): the vector
+// is delta_e = fl32(beta - beta_e), Y is zero, so the partial is -Xb^T (Xb delta); it runs only
+// when the device state selects it.
+template <int VMAX, int RPW, int CORR = 0>
 __global__ void __launch_bounds__(kGradThreads, 2) k_grad_bf16v(const GradArgs a) {
   __shared__ double sm[kWarps][512];
   if (a.check_done && a.st->done) return;
+  if (CORR && (a.st->rebase || !a.st->dc || !a.st->bfnext)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * kWarps + warp, nw = (int64_t)gridDim.x * kWarps;
   const int d = a.d;
   const double *beta = a.beta_ring + (size_t)(a.st->iter % 3) * d;
-  const __nv_bfloat16 *U = static_cast<const __nv_bfloat16 *>(a.X);
+  const __nv_bfloat16 *U = CORR ? a.xbf : static_cast<const __nv_bfloat16 *>(a.X);
   const __nv_bfloat16 *V = static_cast<const __nv_bfloat16 *>(a.Y);
+  const int64_t ldu = CORR ? a.ldb : a.ldx;
   float b[VMAX][8], g[VMAX][8];
 #pragma unroll
   for (int v = 0; v < VMAX; ++v)
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const int col = (v * 32 + lane) * 8 + e;
-      b[v][e] = col < d ? (float)beta[col] : 0.f;
+      b[v][e] = col < d ? (CORR ? a.delta_e[col] : (float)beta[col]) : 0.f;
       g[v][e] = 0.f;
     }
   for (int64_t i0 = gw * RPW; i0 < a.nrows; i0 += nw * RPW) {
@@ -195,10 +213,10 @@ __global__ void __launch_bounds__(kGradThreads, 2) k_grad_bf16v(const GradArgs a
 #pragma unroll
       for (int v = 0; v < VMAX; ++v) {
         const int col0 = (v * 32 + lane) * 8;
-        raw[q][v] = (rv && col0 < d) ? __ldg(reinterpret_cast<const uint4 *>(U + i * a.ldx + col0))
-                                     : make_uint4(0u, 0u, 0u, 0u);
+        const uint4 *src = reinterpret_cast<const uint4 *>(U + i * ldu + col0);
+        raw[q][v] = (rv && col0 < d) ? (CORR ? __ldcs(src) : __ldg(src)) : make_uint4(0u, 0u, 0u, 0u);
       }
-      y[q] = rv ? __bfloat162float(V[i]) : 0.f;
+      y[q] = (rv && !CORR) ? __bfloat162float(V[i]) : 0.f;
     }
     float s[RPW];
 #pragma unroll
@@ -289,11 +307,14 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_bf16s(const GradArgs a) {
 // residual r0 - x . delta32.  The host launches both; the one whose mode does not
 // match st->rebase returns at once.  The two-word accumulators (hi, lo) of each
 // warp live in shared memory (float2 per column), folded every kFlushRows rows.
-template <int VW, int VMAX, int REBASE, int RPW>
+// WBF = 1 (with REBASE): the pass also stores fl_bf16(x_i) into a.xbf (VW = 4 only).
+template <int VW, int VMAX, int REBASE, int RPW, int WBF = 0>
 __global__ void __launch_bounds__(kGradThreads, 2) k_grad_mixed(const GradArgs a) {
+  static_assert(!WBF || (REBASE && VW == 4), "the BF16 copy is written by the vector re-basing pass");
   __shared__ __align__(16) double sm[kWarps][512];
   if (a.check_done && a.st->done) return;
   if ((a.st->rebase != 0) != (REBASE != 0)) return;
+  if (!REBASE && a.st->dc && a.st->bfnext) return;  // correction form: the pass over the BF16 copy runs
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * kWarps + warp, nw = (int64_t)gridDim.x * kWarps;
   const int d = a.d;
@@ -339,6 +360,16 @@ __global__ void __launch_bounds__(kGradThreads, 2) k_grad_mixed(const GradArgs a
         }
 #pragma unroll
         for (int e = 0; e < VW; ++e) x[q][v][e] = (col0 + e < d) ? t[e] : 0.f;
+        if constexpr (WBF) {
+          if (rv && col0 < d) {
+            const __nv_bfloat162 lo = __floats2bfloat162_rn(t[0], t[1]);
+            const __nv_bfloat162 hi = __floats2bfloat162_rn(t[2], t[3]);
+            uint2 w;
+            w.x = *reinterpret_cast<const uint32_t *>(&lo);
+            w.y = *reinterpret_cast<const uint32_t *>(&hi);
+            *reinterpret_cast<uint2 *>(a.xbf + i * a.ldb + col0) = w;
+          }
+        }
       }
       yr[q] = rv ? (REBASE ? __ldcs(Y + i) : __ldcs(a.r0 + i)) : 0.f;
     }
@@ -438,7 +469,7 @@ __global__ void __launch_bounds__(kGradThreads, 2) k_grad_mixed(const GradArgs a
 
 // ---------------------------------------------------------------- reduction and update
 __global__ void k_reduce(const double *partials, int nblk, int d, double scale, double *g, const DevState *st,
-                         int check_done) {
+                         int check_done, double *g0) {
   __shared__ double sm[8][33];
   if (check_done && st->done) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -461,7 +492,12 @@ __global__ void k_reduce(const double *partials, int nblk, int d, double scale, 
     double t = 0.0;
 #pragma unroll
     for (int w = 0; w < 8; ++w) t += sm[w][lane];
-    g[c] = scale * t;
+    double v = scale * t;
+    if (g0) {
+      if (st->dc && st->bfnext && !st->rebase) v += g0[c];  // pass over the BF16 copy: g(beta_e) - Xb^T Xb delta
+      else g0[c] = v;                                        // exact pass: keep g(beta_e)
+    }
+    g[c] = v;
   }
 }
 
@@ -483,6 +519,9 @@ __global__ void __launch_bounds__(256) k_update(const UpdArgs A, DevState *st) {
   const double *bp = a.beta_ring + (size_t)((t + 2) % 3) * d;
   double *bn = a.beta_ring + (size_t)((t + 1) % 3) * d;
   const int i = blockIdx.x * 8 + warp;
+  // correction form: whether this iteration's pass was exact (over X); read before the last block
+  // of this kernel changes the state
+  const bool corr_exact = a.stage2 && a.mixed && st->dc && (st->rebase || !st->bfnext);
   double ds = 0.0, nn = 0.0, dd = 0.0;
   if (i < d) {
     const double *Hrow = a.Hinv + (size_t)i * d;
@@ -507,6 +546,10 @@ __global__ void __launch_bounds__(256) k_update(const UpdArgs A, DevState *st) {
         const double del = v - a.beta0[i];
         a.delta32[i] = (float)del;
         dd = del * del;
+        if (a.beta_e) {
+          if (corr_exact) a.beta_e[i] = b[i];  // the gradient of this pass is g(b)
+          a.delta_e[i] = (float)(v - a.beta_e[i]);
+        }
       }
       if (a.hist && t < a.hist_cap) a.hist[(size_t)t * d + i] = v;
     }
@@ -548,13 +591,48 @@ __global__ void __launch_bounds__(256) k_update(const UpdArgs A, DevState *st) {
     st->done = 1;
   }
   if (a.stage2) {
-    if (a.thr > 0.0 && rel <= a.thr) st->done = 1;
+    // x2 = ||beta+ - beta_0||^2, x1 = ||beta+||^2, x0 = ||beta+ - beta||^2
+    const bool corr = a.mixed && st->dc;
+    const int exact = !corr || st->rebase || !st->bfnext;  // this iteration's pass was over X
+    const int k2 = t - a.hist_base;
+    if (k2 >= 0 && k2 < (int)sizeof(st->mode_hist)) st->mode_hist[k2] = exact ? 0 : 1;
+    if (corr && exact) {
+      // a cycle (exact pass + k passes over the BF16 copy, 1 + k/2 passes' worth of bytes) that
+      // shrank the exact step by less than rho^(1 + k/2), what plain steps gain for those bytes:
+      // the BF16 Hessian term is too coarse for these data (ill-conditioned X), so the remaining
+      // steps take the full form (its next pass reads the r0 this exact pass wrote)
+      if (st->step_prev > 0.0 && x0 > st->step_prev * pow(a.rho, 1.0 + 0.5 * st->ninner)) {
+        st->dc = 0;
+        st->dc_fell_back = 1;
+      }
+      st->step_prev = x0;
+      st->step_ref = x0;
+      st->ninner = 0;
+    } else if (corr) {
+      st->ninner += 1;
+    }
+    const bool may_stop = !(corr && !exact);  // the correction form stops on exact steps only
+    if (may_stop && a.thr > 0.0 && rel <= a.thr) st->done = 1;
     else if (tn >= a.T) {
       st->done = 1;
       if (a.thr > 0.0) st->status |= ST_NOTCONV;
     }
-    // x2 = ||beta+ - beta_0||^2, x1 = ||beta+||^2, x0 = ||beta+ - beta||^2
-    if (a.mixed) st->rebase = (x2 > 0x1p-20 * x1 && x2 > 0x1p20 * x0) ? 1 : 0;
+    if (a.mixed) {
+      // next pass exact: the steps have shrunk to 1/100 of the cycle's first step, or one meets
+      // the stopping test (the stop itself waits for an exact step), or a step grew beyond the
+      // cycle's first step (the BF16 iteration diverging on an ill-conditioned X); the exact pass
+      // re-bases (error-free residuals) only when the drift from beta_0 exceeds 2^-10 ||beta||, so
+      // that the FP32 residual r0 - X (beta - beta_0) stays within ~2^-34 ||X|| ||beta||
+      if (st->dc) {
+        const bool next_exact =
+            !exact && (x0 < 1e-4 * st->step_ref || x0 > st->step_ref || (a.thr > 0.0 && rel <= a.thr));
+        st->bfnext = next_exact ? 0 : 1;
+        st->rebase = (next_exact && x2 > 0x1p-20 * x1) ? 1 : 0;
+      } else {
+        st->bfnext = 0;
+        st->rebase = (x2 > 0x1p-20 * x1 && x2 > 0x1p20 * x0) ? 1 : 0;
+      }
+    }
   }
 }
 
@@ -579,8 +657,9 @@ int grad_grid(int nsm) { return 2 * nsm; }
 
 cudaError_t launch_grad(int mode, int xdtype, const void *X, int64_t ldx, const void *Y, int64_t nrows, int d,
                         const double *beta_ring, DevState *st, const float *delta32, float *r0, double *beta0,
-                        double *partials, int nblk, int check_done, cudaStream_t s) {
-  GradArgs a{X, ldx, Y, nrows, d, beta_ring, st, delta32, r0, beta0, partials, check_done};
+                        double *partials, int nblk, int check_done, cudaStream_t s, __nv_bfloat16 *xbf, int64_t ldb,
+                        int write_xbf, const float *delta_e) {
+  GradArgs a{X, ldx, Y, nrows, d, beta_ring, st, delta32, r0, beta0, partials, check_done, xbf, ldb, delta_e};
   if (d > 512 || d < 1) return cudaErrorInvalidValue;
   switch (mode) {
     case GM_F64:
@@ -614,6 +693,22 @@ cudaError_t launch_grad(int mode, int xdtype, const void *X, int64_t ldx, const 
       if (d <= 256) return launch1(k_grad_mixed<4, 2, 0, 4>, nblk, a, s);
       return launch1(k_grad_mixed<4, 4, 0, 2>, nblk, a, s);
     }
+    case GM_MIXED_DC: {
+      // vector rows only: d % 8 == 0 (whole 16-byte BF16 words per lane), 16-byte aligned FP32 rows
+      if (xdtype != SLSE_F32 || !xbf || !delta_e || d % 8 != 0 || ldb % 8 != 0 || !aligned(X, ldx, 4, 4) ||
+          !aligned(xbf, ldb, 2, 8))
+        return cudaErrorInvalidValue;
+      cudaError_t e;
+      if (d <= 128) e = write_xbf ? launch1(k_grad_mixed<4, 1, 1, 8, 1>, nblk, a, s) : launch1(k_grad_mixed<4, 1, 1, 8>, nblk, a, s);
+      else if (d <= 256) e = write_xbf ? launch1(k_grad_mixed<4, 2, 1, 4, 1>, nblk, a, s) : launch1(k_grad_mixed<4, 2, 1, 4>, nblk, a, s);
+      else e = write_xbf ? launch1(k_grad_mixed<4, 4, 1, 2, 1>, nblk, a, s) : launch1(k_grad_mixed<4, 4, 1, 2>, nblk, a, s);
+      if (e != cudaSuccess) return e;
+      if (d <= 128) e = launch1(k_grad_mixed<4, 1, 0, 8>, nblk, a, s);
+      else if (d <= 256) e = launch1(k_grad_mixed<4, 2, 0, 4>, nblk, a, s);
+      else e = launch1(k_grad_mixed<4, 4, 0, 2>, nblk, a, s);
+      if (e != cudaSuccess) return e;
+      return d <= 256 ? launch1(k_grad_bf16v<1, 6, 1>, nblk, a, s) : launch1(k_grad_bf16v<2, 4, 1>, nblk, a, s);
+    }
     default:
       return cudaErrorInvalidValue;
   }
@@ -638,8 +733,8 @@ cudaError_t preload_grad_kernels() {
 }
 
 cudaError_t launch_reduce(const double *partials, int nblk, int d, double scale, double *g, DevState *st,
-                          int check_done, cudaStream_t s) {
-  k_reduce<<<(d + 31) / 32, 256, 0, s>>>(partials, nblk, d, scale, g, st, check_done);
+                          int check_done, cudaStream_t s, double *g0) {
+  k_reduce<<<(d + 31) / 32, 256, 0, s>>>(partials, nblk, d, scale, g, st, check_done, g0);
   return cudaGetLastError();
 }
 

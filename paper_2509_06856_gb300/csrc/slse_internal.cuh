@@ -29,8 +29,15 @@ struct DevState {
   unsigned bar_gen;
   double rel_step;     // last ||b+ - b|| / ||b+||
   long long spin_limit; // polls of a grid-wide wait before it gives up (0: the built-in 2^25)
-  double pad[2];
+  int dc;              // mixed 2nd stage, correction form active: passes between exact ones read the BF16 copy
+  int bfnext;          // correction form: the next pass reads the BF16 copy (else an exact pass over X)
+  int dc_fell_back;    // the correction form was switched off for this run
+  double step_ref;     // correction form: squared step of the last exact pass
+  double step_prev;    // correction form: squared step of the exact pass before it
+  int ninner;          // correction form: passes over the BF16 copy since the last exact pass
+  unsigned char mode_hist[128];  // 2nd-stage pass kind of iteration t (< 128): 0 over X, 1 over the BF16 copy
 };
+static_assert(sizeof(DevState) <= 512, "the per-CTA partials of the update kernel follow the state");
 
 // ----------------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11).  Counter (c0..c3), key (k0, k1).
@@ -192,13 +199,21 @@ cudaError_t launch_srht(const SrhtPlan &pl, int prec, int xdtype, const void *X,
                                                     element offsets (ldx); 16-byte aligned */);
 
 // grad.cu
-enum GradMode { GM_F64 = 0, GM_MIXED = 1, GM_STAGE1_BF16 = 2, GM_STAGE1_F64 = 3 };
+// GM_MIXED_DC: the mixed 2nd stage in correction form: the re-basing pass (error-free residuals),
+// the plain FP32 pass (the exact pass between re-bases, and every pass once the correction form is
+// switched off) and the pass over the BF16 copy xbf with vector delta_e; each returns at once unless
+// the device state selects it.  write_xbf: the re-basing pass also stores fl_bf16(X) into xbf (ld ldb).
+enum GradMode { GM_F64 = 0, GM_MIXED = 1, GM_STAGE1_BF16 = 2, GM_STAGE1_F64 = 3, GM_MIXED_DC = 4 };
 int grad_grid(int nsm);
 cudaError_t launch_grad(int mode, int xdtype, const void *X, int64_t ldx, const void *Y, int64_t nrows,
                         int d, const double *beta_ring, DevState *st, const float *delta32, float *r0,
-                        double *beta0, double *partials, int nblk, int check_done, cudaStream_t s);
+                        double *beta0, double *partials, int nblk, int check_done, cudaStream_t s,
+                        __nv_bfloat16 *xbf = nullptr, int64_t ldb = 0, int write_xbf = 0,
+                        const float *delta_e = nullptr);
+// g = scale * (sum of the per-CTA partials).  g0 (nullable; mixed 2nd stage in correction form):
+// after an exact pass (over X) g0 = g; after a pass over the BF16 copy g = g0 + that sum.
 cudaError_t launch_reduce(const double *partials, int nblk, int d, double scale, double *g,
-                          DevState *st, int check_done, cudaStream_t s);
+                          DevState *st, int check_done, cudaStream_t s, double *g0 = nullptr);
 // Loads the code of every kernel launch_grad (GM_F64, GM_MIXED) and launch_reduce can launch,
 // so that a later first launch of one of them does not load a module (which allocates).
 cudaError_t preload_grad_kernels();
@@ -218,6 +233,10 @@ struct UpdateArgs {
   int T;               // iteration cap
   int mixed;           // maintain delta32 / rebase flag
   int check_done;
+  int hist_base;       // iteration index of the first 2nd-stage step (mode_hist is indexed from it)
+  double rho;          // sqrt(d / r), the contraction of a plain 2nd-stage step (correction form's test)
+  double *beta_e;      // correction form: the iterate of the last exact pass
+  float *delta_e;      // correction form: fl32(beta - beta_e), the vector of the pass over the BF16 copy
 };
 cudaError_t launch_update(const UpdateArgs &a, DevState *st, cudaStream_t s);
 cudaError_t launch_copy_beta(const double *beta_ring, DevState *st, int d, double *out, cudaStream_t s);

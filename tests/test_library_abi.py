@@ -164,3 +164,18 @@ def test_solve_normal_workspace_holds_the_n_vectors(lib):
     a, b = slse.solve_normal_workspace(X32a, smx), slse.solve_normal_workspace(X32b, smx)
     assert a64 >= 8 * (1 << 14)
     assert b - a == (4 + 4) * (1 << 14)   # r0 (FP32) + the zero right-hand side (FP32)
+
+
+def test_stage2_form_field(lib):
+    """The 2nd-stage form is part of the schedule: the library's default is the correction form,
+    and a value outside slse_stage2_form is an argument error."""
+    import paper_2509_06856_gb300 as slse
+    assert slse.default_schedule(1 << 16, 64, prec="mixed_bf16").stage2 == "correction"
+    assert slse.default_schedule(1 << 16, 64, prec="mixed_bf16", stage2="full").stage2 == "full"
+    good = slse.CProblem(1 << 12, 16, slse.F32, 256, 16, 512)
+    sch = slse.default_schedule(1 << 12, 16, prec="mixed_bf16").to_c()
+    assert slse._lib.slse_workspace_size(ctypes.byref(good), ctypes.byref(sch), slse.OP_FIT, 0) > 0
+    sch.stage2 = 2
+    assert slse._lib.slse_workspace_size(ctypes.byref(good), ctypes.byref(sch), slse.OP_FIT, 0) == 0
+    beta = (ctypes.c_double * 16)()
+    assert slse._lib.slse_fit(ctypes.byref(good), ctypes.byref(sch), 0, beta, None, None, None, 0, None) == slse.EINVAL

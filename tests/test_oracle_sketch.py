@@ -135,3 +135,25 @@ def test_hessian_rows_disjoint_block_or_prefix():
         h0, h1 = sk.hessian_rows(Np, mK, r)
         assert h1 - h0 == r and 0 <= h0 and h1 <= Np
         assert h0 >= mK or h0 == 0
+
+
+@pytest.mark.parametrize("N,m,seed", [(40, 12, 2), (64, 64, 5), (300, 100, 9)])
+def test_sketch_entries_equal_dense_definition(N, m, seed):
+    # single entries from the definition against the dense matrix S built entry by entry
+    # (N' <= 512, padding included), so a sign, index or scale slip in either shows up
+    rng = np.random.default_rng(seed)
+    d = 5
+    X = rng.standard_normal((N, d))
+    Y = rng.standard_normal(N)
+    Np = sk.padded_size(N)
+    D, P, sigma = sk.draws(Np, seed)
+    rows = [0, m // 2, m - 1]
+    cols = [0, 2, d - 1, d]
+    got = sk.sketch_entries(X, Y, D, P, sigma, m, rows, cols)
+    S = sk.sketch_matrix_dense(N, m, seed) if Np <= 256 else None
+    if S is not None:
+        ref = (S @ np.column_stack([X, Y]))[np.ix_(rows, cols)]
+    else:
+        SX, SY = sk.sketch(X, Y, m, seed)
+        ref = np.column_stack([SX, SY])[np.ix_(rows, cols)]
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
