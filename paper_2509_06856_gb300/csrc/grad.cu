@@ -360,16 +360,6 @@ __global__ void __launch_bounds__(kGradThreads, 2) k_grad_mixed(const GradArgs a
         }
 #pragma unroll
         for (int e = 0; e < VW; ++e) x[q][v][e] = (col0 + e < d) ? t[e] : 0.f;
-        if constexpr (WBF) {
-          if (rv && col0 < d) {
-            const __nv_bfloat162 lo = __floats2bfloat162_rn(t[0], t[1]);
-            const __nv_bfloat162 hi = __floats2bfloat162_rn(t[2], t[3]);
-            uint2 w;
-            w.x = *reinterpret_cast<const uint32_t *>(&lo);
-            w.y = *reinterpret_cast<const uint32_t *>(&hi);
-            *reinterpret_cast<uint2 *>(a.xbf + i * a.ldb + col0) = w;
-          }
-        }
       }
       yr[q] = rv ? (REBASE ? __ldcs(Y + i) : __ldcs(a.r0 + i)) : 0.f;
     }
@@ -431,6 +421,26 @@ __global__ void __launch_bounds__(kGradThreads, 2) k_grad_mixed(const GradArgs a
       for (int v = 0; v < VMAX; ++v)
 #pragma unroll
         for (int e = 0; e < VW; ++e) gacc[v][e] = fmaf(x[q][v][e], r[q], gacc[v][e]);
+    if constexpr (WBF) {
+      // the BF16 copy, stored after every row load of this iteration has been issued (a store to a
+      // buffer that may alias X, placed between the loads, would serialise them on each row's data)
+#pragma unroll
+      for (int q = 0; q < RPW; ++q) {
+        const int64_t i = i0 + q;
+#pragma unroll
+        for (int v = 0; v < VMAX; ++v) {
+          const int col0 = (v * 32 + lane) * VW;
+          if (i < a.nrows && col0 < d) {
+            const __nv_bfloat162 lo = __floats2bfloat162_rn(x[q][v][0], x[q][v][1]);
+            const __nv_bfloat162 hi = __floats2bfloat162_rn(x[q][v][2], x[q][v][3]);
+            uint2 w;
+            w.x = *reinterpret_cast<const uint32_t *>(&lo);
+            w.y = *reinterpret_cast<const uint32_t *>(&hi);
+            __stcs(reinterpret_cast<uint2 *>(a.xbf + i * a.ldb + col0), w);
+          }
+        }
+      }
+    }
     nacc += RPW;
     if (nacc >= kFlushRows) {
       nacc = 0;
