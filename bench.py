@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--full-steps", type=int, default=2, help="fits with the full form of the 2nd stage")
     ap.add_argument("--cfg2-steps", type=int, default=2, help="FP64 fits at N=2^20, d=256, cond 1e4")
     ap.add_argument("--cfg4-steps", type=int, default=1, help="fits per form at N=2^24, d=256, heavy tails")
+    ap.add_argument("--one-fit", default=None, metavar="PREC:KIND",
+                    help="run one untimed fit of the workload at --log2n (e.g. mixed_bf16:srht) and exit; "
+                         "the command the committed kernel profiles were captured with")
     ap.add_argument("--tuning-steps", type=int, default=2, help="fits with the SLSE-FRS-tuning schedule")
     ap.add_argument("--gauss-steps", type=int, default=2, help="fits with the Gaussian Hessian sketch")
     ap.add_argument("--diff-steps", type=int, default=2, help="forward+backward passes of the differentiation block")
@@ -857,8 +860,28 @@ def run_ours(args, rank, ws, local_rank):
     print(json.dumps(out), flush=True)
 
 
+def one_fit(args):
+    """One fit of the benchmark workload (rows at --log2n, d = --d, data seed 1003, sketch seed 0)
+    with the default schedule of the given precision and kind; prints its report."""
+    import torch
+    import paper_2509_06856_gb300 as slse
+    prec, kind = args.one_fit.split(":")
+    N, d = 1 << args.log2n, args.d
+    data = make_data(args.log2n, d)
+    X, Y = torch.from_numpy(data["X"]).cuda(), torch.from_numpy(data["Y"]).cuda()
+    if prec == "fp64":
+        X, Y = X.double(), Y.double()
+    s = slse.default_schedule(N, d, prec=prec, T=100, tol=5e-9 if prec != "fp64" else 1e-13, kind=kind)
+    r = slse.fit(X, Y, s, seed=0)
+    print(json.dumps({"one_fit": args.one_fit, "N": N, "d": d, "status": r.status,
+                      "report": {k: v for k, v in r.report.items() if k.startswith(("ms_", "iters", "n_"))}}))
+
+
 def main():
     args = parse()
+    if args.one_fit:
+        one_fit(args)
+        return
     rank, ws, local_rank = dist_init()
     if args.impl == "reference":
         run_reference(args, rank, ws)

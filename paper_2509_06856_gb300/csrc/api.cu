@@ -534,7 +534,7 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
       // FP8 form: the Hessian-sketch rows (sampling positions >= h0) are written in BF16 to h16
       CK(launch_srht(L.sp, s.prec, p->dtype, x_mapped ? x_mapped : p->X, p->ldx, p->Y, p->N, d, Psd, pos, big, WY,
                      L.ld16, U, V, L.ldu, 1.0 / std::sqrt((double)L.Np), st, L.sp.single ? nullptr : e_mid, Us, L.nsb,
-                     h16, L.h0 > 0 ? L.h0 : INT64_MAX, L.ld16, x_copy));
+                     h16, L.h0 > 0 ? L.h0 : INT64_MAX, L.ld16, x_copy, &dst->status));
       kernels += L.sp.single ? 1 : 2;
     }
     if (L.gauss) {

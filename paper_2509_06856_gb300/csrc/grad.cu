@@ -116,8 +116,44 @@ __device__ __forceinline__ void cta_partial(double (*sm)[512], int d, double *ou
 }
 
 // ---------------------------------------------------------------- FP64 arithmetic
-// Tx = double (X F64 or U F64) or float (X F32, widened exactly).  VW = elements per lane load.
-template <class Tx, int VW, int VMAX>
+// Sums of R per-lane values (one per row) across the warp.  The first log2(R) levels are a
+// transposed butterfly: at each level a lane keeps half of its rows and adds the partner's values
+// of that half (one FP64 add per kept row instead of one per row), so after them lane l holds a
+// partial of row rowsel(l); the remaining levels sum that one value.  FP64 adds hold this part's
+// FP64 pipe for tens of cycles each, so the transposed form saves most of the reduction's cost
+// (R = 4: 6 adds instead of 20).  Returns the full sum of every row to every lane (fixed order).
+template <int R>
+__device__ __forceinline__ void warp_sum_rows(double (&v)[R], int lane) {
+  int off = 16;
+#pragma unroll
+  for (int n = R; n > 1; n >>= 1, off >>= 1) {
+    const bool upper = (lane & off) != 0;
+#pragma unroll
+    for (int j = 0; j < n / 2; ++j) {
+      const double send = upper ? v[j] : v[j + n / 2];
+      const double keep = upper ? v[j + n / 2] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+#pragma unroll
+  for (; off > 0; off >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], off);
+  // lane l holds row sum((lane bit 16 >> k) * (R >> (k + 1))); broadcast each row's total
+  double tot[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    int src = 0, o = 16;
+#pragma unroll
+    for (int n = R; n > 1; n >>= 1, o >>= 1)
+      if (q % n >= n / 2) src |= o;
+    tot[q] = __shfl_sync(0xffffffffu, v[0], src);
+  }
+#pragma unroll
+  for (int q = 0; q < R; ++q) v[q] = tot[q];
+}
+
+// Tx = double (X F64 or U F64) or float (X F32, widened exactly).  VW = elements per lane load,
+// VMAX = lane loads per row (sized to d), RPW = rows per warp iteration.
+template <class Tx, int VW, int VMAX, int RPW>
 __global__ void __launch_bounds__(kGradThreads) k_grad_f64(const GradArgs a) {
   __shared__ double sm[kWarps][512];
   if (a.check_done && a.st->done) return;
@@ -136,32 +172,46 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_f64(const GradArgs a) {
       b[v][e] = col < d ? beta[col] : 0.0;
       g[v][e] = 0.0;
     }
-  for (int64_t i = gw; i < a.nrows; i += nw) {
-    const Tx *row = X + i * a.ldx;
-    double x[VMAX][VW];
+  for (int64_t i0 = gw * RPW; i0 < a.nrows; i0 += nw * RPW) {
+    double x[RPW][VMAX][VW];
+    double yv[RPW];
 #pragma unroll
-    for (int v = 0; v < VMAX; ++v) {
-      const int col0 = (v * 32 + lane) * VW;
-      Tx t[VW];
-      if (col0 < d) Vec<Tx, VW>::load(row + col0, t, true);
-      else {
+    for (int q = 0; q < RPW; ++q) {
+      const int64_t i = i0 + q;
+      const bool rv = i < a.nrows;
+      const Tx *row = X + (rv ? i : 0) * a.ldx;
 #pragma unroll
-        for (int e = 0; e < VW; ++e) t[e] = Tx(0);
+      for (int v = 0; v < VMAX; ++v) {
+        const int col0 = (v * 32 + lane) * VW;
+        Tx t[VW];
+        if (rv && col0 < d) Vec<Tx, VW>::load(row + col0, t, true);
+        else {
+#pragma unroll
+          for (int e = 0; e < VW; ++e) t[e] = Tx(0);
+        }
+#pragma unroll
+        for (int e = 0; e < VW; ++e) x[q][v][e] = (col0 + e < d) ? (double)t[e] : 0.0;
       }
-#pragma unroll
-      for (int e = 0; e < VW; ++e) x[v][e] = (col0 + e < d) ? (double)t[e] : 0.0;
+      yv[q] = rv ? (double)Y[i] : 0.0;
     }
-    double s = 0.0;
+    double s[RPW];
 #pragma unroll
-    for (int v = 0; v < VMAX; ++v)
+    for (int q = 0; q < RPW; ++q) {
+      s[q] = 0.0;
 #pragma unroll
-      for (int e = 0; e < VW; ++e) s = fma(x[v][e], b[v][e], s);
-    s = warp_sum(s);
-    const double r = (double)Y[i] - s;
+      for (int v = 0; v < VMAX; ++v)
 #pragma unroll
-    for (int v = 0; v < VMAX; ++v)
+        for (int e = 0; e < VW; ++e) s[q] = fma(x[q][v][e], b[v][e], s[q]);
+    }
+    warp_sum_rows<RPW>(s, lane);
 #pragma unroll
-      for (int e = 0; e < VW; ++e) g[v][e] = fma(x[v][e], r, g[v][e]);
+    for (int q = 0; q < RPW; ++q) {
+      const double r = yv[q] - s[q];  // rows past the end are zero rows: x = 0 adds nothing
+#pragma unroll
+      for (int v = 0; v < VMAX; ++v)
+#pragma unroll
+        for (int e = 0; e < VW; ++e) g[v][e] = fma(x[q][v][e], r, g[v][e]);
+    }
   }
 #pragma unroll
   for (int v = 0; v < VMAX; ++v)
@@ -657,6 +707,21 @@ cudaError_t launch1(K kern, int nblk, const GradArgs &a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// FP64 kernel with its register tile sized to d (lane loads per row) and 4 rows per warp
+// iteration (2 for the widest tiles, whose rows take 32 doubles per lane)
+template <class Tx, int VW>
+cudaError_t launch_f64(int d, int nblk, const GradArgs &a, cudaStream_t s) {
+  constexpr int per = 32 * VW;
+  if (d <= per) return launch1(k_grad_f64<Tx, VW, 1, 4>, nblk, a, s);
+  if (d <= 2 * per) return launch1(k_grad_f64<Tx, VW, 2, 4>, nblk, a, s);
+  if (d <= 4 * per) return launch1(k_grad_f64<Tx, VW, 4, 4>, nblk, a, s);
+  if (d <= 8 * per) return launch1(k_grad_f64<Tx, VW, 8, 2>, nblk, a, s);
+  if constexpr (VW == 1) {
+    if (d <= 16 * per) return launch1(k_grad_f64<Tx, VW, 16, 2>, nblk, a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
 inline bool aligned(const void *p, int64_t ld, int64_t elem_bytes, int vw) {
   return (reinterpret_cast<uintptr_t>(p) % (size_t)(vw * elem_bytes) == 0) && (ld % vw == 0);
 }
@@ -675,11 +740,11 @@ cudaError_t launch_grad(int mode, int xdtype, const void *X, int64_t ldx, const 
     case GM_F64:
     case GM_STAGE1_F64:
       if (xdtype == SLSE_F64) {
-        if (d % 2 == 0 && aligned(X, ldx, 8, 2)) return launch1(k_grad_f64<double, 2, 8>, nblk, a, s);
-        return launch1(k_grad_f64<double, 1, 16>, nblk, a, s);
+        if (d % 2 == 0 && aligned(X, ldx, 8, 2)) return launch_f64<double, 2>(d, nblk, a, s);
+        return launch_f64<double, 1>(d, nblk, a, s);
       } else {
-        if (d % 2 == 0 && aligned(X, ldx, 4, 2)) return launch1(k_grad_f64<float, 2, 8>, nblk, a, s);
-        return launch1(k_grad_f64<float, 1, 16>, nblk, a, s);
+        if (d % 2 == 0 && aligned(X, ldx, 4, 2)) return launch_f64<float, 2>(d, nblk, a, s);
+        return launch_f64<float, 1>(d, nblk, a, s);
       }
     case GM_STAGE1_BF16:
       // the sketch buffer's padding columns are never written: the vector path requires
@@ -727,8 +792,16 @@ cudaError_t launch_grad(int mode, int xdtype, const void *X, int64_t ldx, const 
 cudaError_t preload_grad_kernels() {
   // every kernel launch_grad (modes GM_F64 and GM_MIXED) and launch_reduce can pick
   const void *k[] = {
-      (const void *)k_grad_f64<double, 2, 8>,    (const void *)k_grad_f64<double, 1, 16>,
-      (const void *)k_grad_f64<float, 2, 8>,     (const void *)k_grad_f64<float, 1, 16>,
+      (const void *)k_grad_f64<double, 2, 1, 4>, (const void *)k_grad_f64<double, 2, 2, 4>,
+      (const void *)k_grad_f64<double, 2, 4, 4>, (const void *)k_grad_f64<double, 2, 8, 2>,
+      (const void *)k_grad_f64<double, 1, 1, 4>, (const void *)k_grad_f64<double, 1, 2, 4>,
+      (const void *)k_grad_f64<double, 1, 4, 4>, (const void *)k_grad_f64<double, 1, 8, 2>,
+      (const void *)k_grad_f64<double, 1, 16, 2>,
+      (const void *)k_grad_f64<float, 2, 1, 4>,  (const void *)k_grad_f64<float, 2, 2, 4>,
+      (const void *)k_grad_f64<float, 2, 4, 4>,  (const void *)k_grad_f64<float, 2, 8, 2>,
+      (const void *)k_grad_f64<float, 1, 1, 4>,  (const void *)k_grad_f64<float, 1, 2, 4>,
+      (const void *)k_grad_f64<float, 1, 4, 4>,  (const void *)k_grad_f64<float, 1, 8, 2>,
+      (const void *)k_grad_f64<float, 1, 16, 2>,
       (const void *)k_grad_mixed<1, 16, 1, 1>,   (const void *)k_grad_mixed<4, 1, 1, 8>,
       (const void *)k_grad_mixed<4, 2, 1, 4>,    (const void *)k_grad_mixed<4, 4, 1, 2>,
       (const void *)k_grad_mixed<1, 16, 0, 1>,   (const void *)k_grad_mixed<4, 1, 0, 8>,

@@ -196,7 +196,8 @@ cudaError_t launch_srht(const SrhtPlan &pl, int prec, int xdtype, const void *X,
                         int64_t hat_row0 = 0, int64_t hat_ld = 0,
                         void *copy_out = nullptr /* two-pass plans: X rows read by pass 1 (e.g. from
                                                     mapped host memory) are also stored here, same
-                                                    element offsets (ldx); 16-byte aligned */);
+                                                    element offsets (ldx); 16-byte aligned */,
+                        unsigned *status = nullptr /* ST_TIMEOUT raised here if a bounded wait gave up */);
 
 // grad.cu
 // GM_MIXED_DC: the mixed 2nd stage in correction form: the re-basing pass (error-free residuals),

@@ -22,6 +22,12 @@
 // stores move whole row segments (C = 32 FP32 or 16 FP64 columns = 128 bytes) so
 // every warp access is coalesced.  The work is adds/subtracts only: HBM-bound in
 // FP32, FP64-ALU-bound in FP64 on this part.
+//
+// Cluster synchronisation: a tile is published through an mbarrier per CTA (one thread
+// fences at cluster scope after a CTA barrier and signals every peer; all threads wait with
+// acquire, bounded), rather than a cluster barrier whose release every warp would execute;
+// the exit barrier, which only keeps each tile alive until the peers have read it, is taken
+// without a fence after the CTA's stores (which consumed every remote value).
 #include <cooperative_groups.h>
 #include <cuda_fp8.h>
 
@@ -61,6 +67,7 @@ struct GroupArgs {
   double scale;
   void *copy_out;       // pass 1 reading host memory: every input row segment is also stored
                         // here at the same element offset (the device copy of X)
+  unsigned *status;     // nullable: ST_TIMEOUT is raised here when a bounded wait gave up
 };
 
 // Smallest k with amax <= 448 2^k (448 = 1.75 2^8, the largest E4M3 value), clamped to
@@ -227,6 +234,18 @@ __global__ void __launch_bounds__(NT, MINB) k_group(const GroupArgs a) {
   int64_t *s_off = reinterpret_cast<int64_t *>(smem_raw + (size_t)M * C * sizeof(Ts));
   Ts *s_mul = reinterpret_cast<Ts *>(s_off + M);
   int32_t *s_dst = reinterpret_cast<int32_t *>(s_mul + M);
+  uint64_t *s_mbar = reinterpret_cast<uint64_t *>(s_dst + M);  // tile-ready barrier (Q > 1)
+  const unsigned mb_addr = (unsigned)__cvta_generic_to_shared(s_mbar);
+  if constexpr (Q > 1) {
+    // each of the Q CTAs of the cluster signals this barrier once its tile is ready; the
+    // cluster arrive that publishes the initialisation is waited for only before the first
+    // remote signal
+    if (threadIdx.x == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb_addr), "r"(Q) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+  }
 
   const int rank = (int)(blockIdx.x % Q);
   const int64_t item = (int64_t)(blockIdx.x / Q);
@@ -253,12 +272,19 @@ __global__ void __launch_bounds__(NT, MINB) k_group(const GroupArgs a) {
     s_off[l] = src * a.ldin;
     s_mul[l] = mul;
   }
-  // output rows written in stage O: kappa = q M + rank MQ + l', l' < MQ
+  // output rows written in stage O: kappa = q M + rank MQ + l', l' < MQ; loaded into registers
+  // here and stored to shared memory after stage A, so that the row loads do not wait for them
+  constexpr int PR = (M + NT - 1) / NT;
+  int32_t pos_reg[PR];
   if (a.pos) {
-    for (int e = threadIdx.x; e < M; e += NT) {
-      const int q = e / MQ, lq = e % MQ;
-      const int64_t kappa = (int64_t)q * M + rank * MQ + lq;
-      s_dst[e] = __ldg(a.pos + kappa * a.ostride + g * a.ogstride);
+#pragma unroll
+    for (int k = 0; k < PR; ++k) {
+      const int e = threadIdx.x + k * NT;
+      if (e < M) {
+        const int q = e / MQ, lq = e % MQ;
+        const int64_t kappa = (int64_t)q * M + rank * MQ + lq;
+        pos_reg[k] = __ldg(a.pos + kappa * a.ostride + g * a.ogstride);
+      }
     }
   }
   __syncthreads();
@@ -318,6 +344,13 @@ __global__ void __launch_bounds__(NT, MINB) k_group(const GroupArgs a) {
       smem_store<Ts, VA>(tile + (b + (k << S1)) * C + cq * VA, t);
     }
   }
+  if (a.pos) {
+#pragma unroll
+    for (int k = 0; k < PR; ++k) {
+      const int e = threadIdx.x + k * NT;
+      if (e < M) s_dst[e] = pos_reg[k];
+    }
+  }
   // stage B
   if constexpr (S1 > 0) {
     __syncthreads();
@@ -341,9 +374,37 @@ __global__ void __launch_bounds__(NT, MINB) k_group(const GroupArgs a) {
       }
     }
   }
-  // stage O
-  if constexpr (Q > 1) cg::this_cluster().sync();
-  else __syncthreads();
+  // stage O: tile ready.  The CTA barrier orders every thread's tile stores before thread 0's
+  // single cluster-scope release fence; thread 0 then signals each peer's barrier, and every
+  // thread waits, with acquire, until all Q tiles of the cluster are ready.  The wait gives up
+  // after ~2^22 polls (ST_TIMEOUT; the output is then garbage but no CTA leaves before its
+  // peers, so no remote read outlives its tile).
+  __syncthreads();
+  if constexpr (Q > 1) {
+    asm volatile("barrier.cluster.wait.aligned;" ::: "memory");  // the peers' barriers are initialised
+    if (threadIdx.x == 0) {
+      asm volatile("fence.acq_rel.cluster;" ::: "memory");
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        unsigned remote;
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(mb_addr), "r"(q));
+        asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote) : "memory");
+      }
+    }
+    uint32_t ready = 0;
+    for (long long spin = 0; !ready; ++spin) {
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+          "selp.u32 %0, 1, 0, p;\n\t}"
+          : "=r"(ready)
+          : "r"(mb_addr), "r"(0)
+          : "memory");
+      if (!ready && spin > (1ll << 22)) {
+        if (a.status && threadIdx.x == 0) atomicOr(a.status, ST_TIMEOUT);
+        break;
+      }
+    }
+  }
   const Ts *rt[Q];
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
@@ -420,7 +481,11 @@ __global__ void __launch_bounds__(NT, MINB) k_group(const GroupArgs a) {
       }
     }
   }
-  if constexpr (Q > 1) cg::this_cluster().sync();
+  // every remote value has been stored, so read: release the peers without a memory fence
+  if constexpr (Q > 1) {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
+  }
 }
 
 // The Y column of one group (2^L <= 4096 rows) per CTA, in shared memory: gather
@@ -529,7 +594,7 @@ cudaError_t launch_group_t(const GroupArgs &a0, int64_t ngroups, cudaStream_t s)
   constexpr int NT = 256;
   GroupArgs a = a0;
   a.nslab = (a.d + C - 1) / C;
-  const size_t smem = (size_t)(1 << LOGM) * (C * sizeof(Ts) + 8 + sizeof(Ts) + 4);
+  const size_t smem = (size_t)(1 << LOGM) * (C * sizeof(Ts) + 8 + sizeof(Ts) + 4) + 16;  // + the mbarrier
   auto kern = k_group<Tin, Ts, Tout, LOGM, Q, C, VA, VB, VO, NT, MINB, SA, CPY>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -594,8 +659,9 @@ cudaError_t run_plan(const SrhtPlan &pl, const void *X, int64_t ldx, const void 
                      void *V, int64_t ldu, double scale, cudaStream_t s,
                      cudaError_t (*pass2)(const GroupArgs &, int, int64_t, cudaStream_t), cudaEvent_t ev_mid,
                      uint8_t *Uscale = nullptr, int64_t ld_scale = 0, __nv_bfloat16 *hat = nullptr,
-                     int64_t hat_row0 = 0, int64_t hat_ld = 0, void *copy_out = nullptr) {
+                     int64_t hat_row0 = 0, int64_t hat_ld = 0, void *copy_out = nullptr, unsigned *status = nullptr) {
   GroupArgs a = {};
+  a.status = status;
   a.d = d;
   a.nslab = (d + 1 + C - 1) / C;
   auto vec_ok = [](const void *p, int64_t ld, size_t eb, int v) {
@@ -661,31 +727,31 @@ cudaError_t launch_srht(const SrhtPlan &pl, int prec, int xdtype, const void *X,
                         int64_t N, int d, const int32_t *Psd, const int32_t *pos, void *W, void *WY,
                         int64_t ldw, void *U, void *V, int64_t ldu, double scale, cudaStream_t s,
                         cudaEvent_t ev_mid, uint8_t *Uscale, int64_t ld_scale, __nv_bfloat16 *hat,
-                        int64_t hat_row0, int64_t hat_ld, void *copy_out) {
+                        int64_t hat_row0, int64_t hat_ld, void *copy_out, unsigned *status) {
   using bf16 = __nv_bfloat16;
   if (copy_out && (pl.single || (uintptr_t)copy_out % 16 != 0)) return cudaErrorInvalidValue;
   if (prec == SLSE_PREC_FP64) {
     auto p2 = &launch_pass_t<double, double, double, 1, 1, 2>;
     if (xdtype == SLSE_F64)
       return run_plan<double, double, double, 16, 1, 1, 2>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale, s,
-                                                          p2, ev_mid, nullptr, 0, nullptr, 0, 0, copy_out);
+                                                          p2, ev_mid, nullptr, 0, nullptr, 0, 0, copy_out, status);
     return run_plan<float, double, double, 16, 1, 1, 2>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale, s,
-                                                       p2, ev_mid, nullptr, 0, nullptr, 0, 0, copy_out);
+                                                       p2, ev_mid, nullptr, 0, nullptr, 0, 0, copy_out, status);
   }
   if (prec == SLSE_PREC_MIXED_BF16 && xdtype == SLSE_F32) {
-    // five CTAs per SM in both passes (more row gathers in flight; measured against 3, 4 and 6)
-    auto p2 = &launch_pass_t<bf16, float, bf16, 2, 2, 4, 128, 5>;
-    return run_plan<float, float, bf16, 32, 2, 2, 4, 128, 5>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale,
-                                                             s, p2, ev_mid, nullptr, 0, nullptr, 0, 0, copy_out);
+    // four CTAs per SM in both passes (measured against 3, 4, 5 and 6 with the mbarrier exchange)
+    auto p2 = &launch_pass_t<bf16, float, bf16, 2, 2, 4, 128, 4>;
+    return run_plan<float, float, bf16, 32, 2, 2, 4, 128, 4>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale,
+                                                             s, p2, ev_mid, nullptr, 0, nullptr, 0, 0, copy_out, status);
   }
   if (prec == SLSE_PREC_MIXED_FP8 && xdtype == SLSE_F32) {
     // pass 1 as in the BF16 form; pass 2 writes E4M3 rows with 32-column block scales
     // (single-pass sizes are handled by the caller through the BF16 form)
     if (pl.single || !Uscale) return cudaErrorInvalidValue;
     auto p2 = &launch_pass_t<bf16, float, mx8, 2, 2, 4>;
-    return run_plan<float, float, bf16, 32, 2, 2, 4, 128, 5>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale,
+    return run_plan<float, float, bf16, 32, 2, 2, 4, 128, 4>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale,
                                                              s, p2, ev_mid, Uscale, ld_scale, hat, hat_row0, hat_ld,
-                                                             copy_out);
+                                                             copy_out, status);
   }
   return cudaErrorInvalidValue;
 }
