@@ -478,12 +478,11 @@ def run_ours(args, rank, ws, local_rank):
 
     # dominant kernel: 2nd-stage gradient vs the two sketch passes (summed CUDA-event times)
     rep = results[-1].report
-    # 2nd stage: the passes over X (exact passes of the correction form; the first also writes the
-    # BF16 copy) and the passes over the BF16 copy, each with its algorithmic bytes per launch
-    n_x = max(1, rep["n_grad2"])
+    # 2nd stage: the passes over X (the exact passes of the correction form) and the packing of the
+    # BF16 copy with its Gram matrix (one launch group; its tensor rate is reported apart below)
     k_times = {
-        "grad_stage2": (rep["ms_grad2"], rep["n_grad2"], (n_x * rep["bytes_grad2"] + rep["bytes_xbf"]) / n_x),
-        "grad_stage2_bf16": (rep["ms_grad2_bf16"], rep["n_grad2_bf16"], rep["bytes_grad2_bf16"]),
+        "grad_stage2": (rep["ms_grad2"], rep["n_grad2"], rep["bytes_grad2"]),
+        "gram_bf16": (rep["ms_gram"], 1 if rep["ms_gram"] > 0 else 0, rep["bytes_gram"]),
         "srht_pass1": (rep["ms_srht_pass1"], 1, N * (d + 1) * 4.0 + N * (d + 1) * 2.0),
         "srht_pass2": (rep["ms_srht_pass2"], 1, N * (d + 1) * 2.0 + (sched.m[-1] + sched.r) * (d + 1) * 2.0),
     }
@@ -497,7 +496,7 @@ def run_ours(args, rank, ws, local_rank):
     ms_d, n_d, by_d = k_times[dom]
     achieved = by_d / (ms_d / n_d) / 1e6
     src = {"grad_stage2": ["paper_2509_06856_gb300/csrc/grad.cu"],
-           "grad_stage2_bf16": ["paper_2509_06856_gb300/csrc/grad.cu"],
+           "gram_bf16": ["paper_2509_06856_gb300/csrc/gram.cu", "paper_2509_06856_gb300/csrc/gaussian.cu"],
            "srht_pass1": ["paper_2509_06856_gb300/csrc/srht.cu"],
            "srht_pass2": ["paper_2509_06856_gb300/csrc/srht.cu"]}[dom]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -853,7 +852,11 @@ def run_ours(args, rank, ws, local_rank):
         "phases_ms": {k: rep[k] for k in ("ms_draws", "ms_sketch", "ms_srht_pass1", "ms_srht_pass2", "ms_qr",
                                           "ms_stage1", "ms_stage2", "ms_total")},
         "iters": [rep["iters_stage1"], rep["iters_stage2"]], "rebases": rep["rebases"],
-        "stage2": {"form": sched.stage2, "exact_passes": rep["n_grad2"], "bf16_passes": rep["n_grad2_bf16"],
+        "stage2": {"form": sched.stage2, "exact_passes": rep["n_grad2"], "correction_steps": rep["n_corr"],
+                   "ms_correction_steps": rep["ms_corr"], "ms_gram": rep["ms_gram"],
+                   "gram_tflops": rep["flops_gram"] / rep["ms_gram"] / 1e9 if rep["ms_gram"] > 0 else None,
+                   "gram_frac_of_bf16_peak": (rep["flops_gram"] / rep["ms_gram"] / 1e9 / measured_bf16_peak()[0]
+                                              if rep["ms_gram"] > 0 else None),
                    "fell_back_to_full": rep["stage2_full"], "full_form": s2full},
         "kernels": kernels_gbs, "data_gen_seconds": t_gen,
     }

@@ -95,17 +95,20 @@ typedef enum { SLSE_PREC_FP64 = 0, SLSE_PREC_MIXED_BF16 = 1, SLSE_PREC_MIXED_FP8
  * SLSE_STAGE2_FULL: every 2nd-stage step streams X in FP32 (the compensated residual-gradient
  *   pass of SLSE_PREC_MIXED_BF16).
  * SLSE_STAGE2_CORRECTION: defect correction of the same iteration.  An exact pass (the FP32
- *   pass above, which re-bases) gives g(b0) = X^T (Y - X b0); the steps after it use
- *   g(b) = g(b0) - Xb^T Xb (b - b0), one pass over a BF16 copy Xb of X (half the bytes), which
- *   the first exact pass writes while it streams X.  The next exact pass comes when a step falls
- *   below 1/100 of the first step after the last exact pass, rises above it, or meets the
+ *   pass above) gives g(b_e) = X^T (Y - X b_e); the steps after it (correction steps) use
+ *   g(b) = g(b_e) - G_b (b - b_e) with G_b = Xb^T Xb the Gram matrix of a BF16 copy Xb of X,
+ *   formed once on the tensor cores before the 2nd stage: a d x d product per step instead of a
+ *   pass over X.  The next exact pass comes when a step falls
+ *   below 1/10^4 of the first step after the last exact pass, rises above it, is the 20th
+ *   correction step of the cycle, or meets the
  *   stopping test; the iteration stops only on the step of an exact pass, so the stopping test
  *   and the fixed point (g(b) = 0, the least-squares estimate) are those of the full form.  When
- *   a cycle (an exact pass and k BF16 passes) shrinks the exact step by less than
- *   rho^(1 + k/2), rho = sqrt(d/r), i.e. less than full-form steps gain for the same bytes (the
- *   BF16 Hessian term too coarse for an ill-conditioned X), the remaining steps take the full
- *   form.  Requires d % 8 == 0 and 16-byte aligned rows (else the full form runs).  No paper counterpart (the paper streams X in
- *   double precision); workspace grows to hold N x ceil(d/8)*8 BF16 values. */
+ *   a cycle (an exact pass and k correction steps) shrinks the exact step by less than
+ *   rho^(1 + k/50), rho = sqrt(d/r) (a correction step counted as 1/50 of a pass), i.e. less than
+ *   full-form steps gain in that time, or by less than 10x (the BF16 Hessian term too coarse for
+ *   an ill-conditioned X), the remaining steps take the full form.  No paper counterpart (the
+ *   paper streams X in double precision); the workspace grows by the Gram stage's scratch
+ *   (slse_workspace_size with SLSE_OP_GRAM gives it). */
 typedef enum { SLSE_STAGE2_FULL = 0, SLSE_STAGE2_CORRECTION = 1 } slse_stage2_form;
 
 typedef struct {
@@ -151,12 +154,13 @@ typedef struct {
   double bytes_grad2;     /* algorithmic HBM bytes of one 2nd-stage gradient pass */
   int32_t rebases;        /* mixed path: number of 2nd-stage residual re-bases (exact passes) */
   int32_t status;
-  double ms_grad2_bf16;   /* SLSE_STAGE2_CORRECTION: summed CUDA-event time of the passes over the BF16
-                             copy of X (not included in ms_grad2, which then covers the exact passes) */
-  int32_t n_grad2_bf16;   /* number of those passes */
+  double ms_corr;         /* SLSE_STAGE2_CORRECTION: summed CUDA-event time of the correction steps (not
+                             included in ms_grad2, which then covers the exact passes over X) */
+  int32_t n_corr;         /* number of correction steps */
   int32_t stage2_full;    /* 1 if a correction run fell back to the full form */
-  double bytes_grad2_bf16; /* algorithmic HBM bytes of one pass over the BF16 copy */
-  double bytes_xbf;       /* bytes of the BF16 copy, written once by the first exact pass */
+  double ms_gram;         /* CUDA-event time of forming the Gram matrix of the BF16 copy of X (pack + MMA) */
+  double flops_gram;      /* its tensor-core FLOPs (2 N' ncp^2, ncp = d rounded up to 128) */
+  double bytes_gram;      /* its algorithmic HBM bytes (X read, the packed BF16 copy written and read) */
 } slse_report;
 
 typedef struct {
@@ -170,8 +174,8 @@ typedef struct {
 
 /* Workspace query.  op: SLSE_OP_FIT (sched required), SLSE_OP_SKETCH (arg = m; prec and kind
  * from sched->prec and sched->kind if sched != NULL, else FP64 SRHT), SLSE_OP_GRAD, SLSE_OP_DRAWS (arg = N), SLSE_OP_QR
- * (arg = r).  Returns 0 for invalid arguments. */
-enum { SLSE_OP_FIT = 0, SLSE_OP_SKETCH = 1, SLSE_OP_GRAD = 2, SLSE_OP_DRAWS = 3, SLSE_OP_QR = 4 };
+ * (arg = r), SLSE_OP_GRAM.  Returns 0 for invalid arguments. */
+enum { SLSE_OP_FIT = 0, SLSE_OP_SKETCH = 1, SLSE_OP_GRAD = 2, SLSE_OP_DRAWS = 3, SLSE_OP_QR = 4, SLSE_OP_GRAM = 5 };
 size_t slse_workspace_size(const slse_problem *prob, const slse_schedule *sched, int32_t op, int64_t arg);
 
 /* Algorithm 2 end to end (paper Sec. 3).  seed selects the random draws D, P and the
@@ -232,6 +236,14 @@ slse_status slse_grad(const slse_problem *prob, const double *beta, double *g_ou
  * used for large d); otherwise SLSE_ENOMEM.  Asynchronous on `stream`. */
 slse_status slse_grad_noalloc(const slse_problem *prob, const double *beta, double *g_out, int32_t prec,
                               slse_stream_t stream);
+
+/* Gram matrix G = Xb^T Xb (d x d, FP64, row-major, device) of the BF16 rounding Xb of X
+ * (prob->dtype F32, device): the Hessian term of the mixed 2nd stage's correction form
+ * (SLSE_STAGE2_CORRECTION; the Hessian X^T X of Sec. 1 with X rounded to BF16).  Products of BF16
+ * values are exact in FP32; they are accumulated on the tensor cores in FP32 over ranges of rows
+ * and the ranges are added in FP64 in a fixed order.  Asynchronous on `stream`; workspace from
+ * slse_workspace_size(SLSE_OP_GRAM).  No paper counterpart as an entry point. */
+slse_status slse_gram(const slse_problem *prob, double *G, void *workspace, size_t ws_bytes, slse_stream_t stream);
 
 /* The random draws of the sketch (Sec. 3, matrices D, P and B) for N' = 2^ceil(log2 N):
  * P (device int32, N'): the permutation, row j of P X is X[P[j]];

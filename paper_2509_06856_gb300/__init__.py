@@ -31,7 +31,7 @@ SRHT, COUNTSKETCH, GAUSSIAN, COUNTSKETCH_HAT = 0, 1, 2, 3
 KIND = {"srht": SRHT, "countsketch": COUNTSKETCH, "countsketch_hat": COUNTSKETCH_HAT, "gaussian": GAUSSIAN}
 PREC = {"fp64": 0, "mixed_bf16": 1, "mixed_fp8": 2}
 STAGE2 = {"full": 0, "correction": 1}
-OP_FIT, OP_SKETCH, OP_GRAD, OP_DRAWS, OP_QR = range(5)
+OP_FIT, OP_SKETCH, OP_GRAD, OP_DRAWS, OP_QR, OP_GRAM = range(6)
 
 
 class CProblem(ctypes.Structure):
@@ -54,8 +54,8 @@ class CReport(ctypes.Structure):
                 ("iters_stage1", ctypes.c_int32), ("iters_stage2", ctypes.c_int32),
                 ("final_rel_step", ctypes.c_double), ("bytes_moved", ctypes.c_double),
                 ("bytes_grad2", ctypes.c_double), ("rebases", ctypes.c_int32), ("status", ctypes.c_int32),
-                ("ms_grad2_bf16", ctypes.c_double), ("n_grad2_bf16", ctypes.c_int32), ("stage2_full", ctypes.c_int32),
-                ("bytes_grad2_bf16", ctypes.c_double), ("bytes_xbf", ctypes.c_double)]
+                ("ms_corr", ctypes.c_double), ("n_corr", ctypes.c_int32), ("stage2_full", ctypes.c_int32),
+                ("ms_gram", ctypes.c_double), ("flops_gram", ctypes.c_double), ("bytes_gram", ctypes.c_double)]
 
 
 class CTrace(ctypes.Structure):
@@ -73,6 +73,8 @@ _lib.slse_sketch.restype = _i32
 _lib.slse_sketch.argtypes = [ctypes.POINTER(CProblem), _i32, _i32, _u64, _i64, _vp, _i64, _vp, _vp, _sz, _vp]
 _lib.slse_grad.restype = _i32
 _lib.slse_grad.argtypes = [ctypes.POINTER(CProblem), _vp, _vp, _i32, _vp, _sz, _vp]
+_lib.slse_gram.restype = _i32
+_lib.slse_gram.argtypes = [ctypes.POINTER(CProblem), _vp, _vp, _sz, _vp]
 _lib.slse_grad_noalloc.restype = _i32
 _lib.slse_grad_noalloc.argtypes = [ctypes.POINTER(CProblem), _vp, _vp, _i32, _vp]
 _lib.slse_draws.restype = _i32
@@ -103,7 +105,7 @@ _lib.slse_version.restype = _i32
 _lib.slse_debug_spin_limit.restype = _i64
 _lib.slse_debug_spin_limit.argtypes = [_i64]
 
-EXPORTED = ["slse_workspace_size", "slse_fit", "slse_sketch", "slse_grad", "slse_grad_noalloc", "slse_draws", "slse_qr",
+EXPORTED = ["slse_workspace_size", "slse_fit", "slse_sketch", "slse_grad", "slse_grad_noalloc", "slse_gram", "slse_draws", "slse_qr",
             "slse_default_schedule", "slse_default_schedule_for", "slse_ai_bound", "slse_status_string",
             "slse_version", "slse_solve_normal", "slse_solve_normal_workspace", "slse_ols_vjp",
             "slse_tuning_schedule", "slse_debug_spin_limit"]
@@ -373,6 +375,19 @@ def grad(X, Y, beta, prec: str = "fp64", workspace=None, stream=None):
     st = _lib.slse_grad(ctypes.byref(p), b.data_ptr(), g.data_ptr(), PREC[prec], ws_ptr, ws_len, _stream(stream))
     _check(st, "slse_grad")
     return g
+
+
+def gram(X, workspace=None, stream=None):
+    """slse_gram: G = Xb^T Xb (d x d float64 on the device) for the BF16 rounding Xb of X (float32)."""
+    torch = _torch()
+    if X.dim() != 2 or X.stride(1) != 1 or X.dtype != torch.float32:
+        raise ValueError("X must be a row-major float32 matrix")
+    p = CProblem(X.shape[0], X.shape[1], F32, X.data_ptr(), X.stride(0), X.data_ptr())
+    G = torch.empty((p.d, p.d), dtype=torch.float64, device=X.device)
+    ws_ptr, ws_len = (workspace.data_ptr(), workspace.numel()) if workspace is not None else (None, 0)
+    st = _lib.slse_gram(ctypes.byref(p), G.data_ptr(), ws_ptr, ws_len, _stream(stream))
+    _check(st, "slse_gram")
+    return G
 
 
 def grad_noalloc(X, Y, beta, prec: str = "fp64", stream=None):

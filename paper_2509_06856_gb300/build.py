@@ -19,7 +19,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include")]
 SOURCES = ["api.cu", "draws.cu", "srht.cu", "grad.cu", "linalg.cu", "noalloc.cu", "countsketch.cu", "adjoint.cu", "fp8.cu",
-           "gaussian.cu"]
+           "gaussian.cu", "gram.cu"]
 
 
 def nvcc() -> str:

@@ -133,8 +133,9 @@ struct FitLayout {
   std::vector<int64_t> lvl_off;  // CountSketch: first row in U of the sketch of each schedule size
   int nblk;
   bool host_in;
-  bool dc;                  // mixed 2nd stage in correction form (BF16 copy of X in the big region)
-  size_t o_xin, o_yin, o_g0, o_be, o_de;
+  bool dc;                  // mixed 2nd stage in correction form (its Gram workspace in the big region)
+  GramPlan grp;
+  size_t o_xin, o_yin, o_g0, o_be, o_de, o_gb, o_gst;
   size_t o_state, o_psd, o_sigma, o_pos, o_big, o_wy, o_u, o_v, o_A, o_R, o_Hinv, o_qr, o_chol, o_part, o_g,
       o_ring, o_b0, o_d32, o_out, o_r0, o_us, o_hat16;
   size_t total;
@@ -186,13 +187,14 @@ FitLayout fit_layout(const slse_problem *p, const Sched &s, int nsm) {
     L.gp = gauss_plan(p->N, d, s.prec, s.r, false, nsm);
     if (L.gp.total > big) big = L.gp.total;
   }
-  // correction form of the mixed 2nd stage: vector rows (d % 8 == 0, 16-byte aligned FP32 rows; a host
-  // X is copied with ld = d into the 256-byte aligned workspace); its BF16 copy of X takes the big
-  // region, whose SRHT, CountSketch or Gaussian temporaries are dead by the 2nd stage
+  // correction form of the mixed 2nd stage: the packed BF16 copy of X and the partial sums of its
+  // Gram matrix take the big region, whose SRHT, CountSketch or Gaussian temporaries are dead by then
   L.host_in = is_host_pointer(p->X);
-  L.dc = s.prec != SLSE_PREC_FP64 && s.stage2 == SLSE_STAGE2_CORRECTION && d % 8 == 0 &&
-         (L.host_in || (reinterpret_cast<uintptr_t>(p->X) % 16 == 0 && p->ldx % 4 == 0));
-  if (L.dc && (size_t)p->N * L.ld16 * 2 > big) big = (size_t)p->N * L.ld16 * 2;
+  L.dc = s.prec != SLSE_PREC_FP64 && s.stage2 == SLSE_STAGE2_CORRECTION;
+  if (L.dc) {
+    L.grp = gram_plan(p->N, d, nsm);
+    if (L.grp.total > big) big = L.grp.total;
+  }
   L.o_big = w.take(big);
   L.o_wy = L.o_big + align256(wbytes);
   L.o_u = w.take((size_t)L.n_samp * L.ldu * eu);
@@ -214,6 +216,8 @@ FitLayout fit_layout(const slse_problem *p, const Sched &s, int nsm) {
   L.o_g0 = w.take(L.dc ? (size_t)d * 8 : 0);
   L.o_be = w.take(L.dc ? (size_t)d * 8 : 0);
   L.o_de = w.take(L.dc ? (size_t)d * 4 : 0);
+  L.o_gb = w.take(L.dc ? (size_t)d * d * 8 : 0);
+  L.o_gst = w.take(L.dc ? 256 : 0);  // status word of the Gram build (it runs beside the 1st stage)
   if (L.host_in) {
     const size_t bx = p->dtype == SLSE_F64 ? 8 : 4;
     L.o_xin = w.take((size_t)p->N * d * bx);
@@ -272,8 +276,9 @@ __global__ void k_init_state(DevState *st, int rebase, long long spin_limit) {
 __global__ void k_clear_numeric(DevState *st) {
   if (threadIdx.x == 0 && blockIdx.x == 0) st->status &= ~ST_NUMERIC;
 }
-__global__ void k_set_stage2(DevState *st, int rebase, int dc) {
+__global__ void k_set_stage2(DevState *st, int rebase, int dc, const unsigned *side_status) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
+    if (side_status) st->status |= *side_status;  // a timeout of the Gram build
     st->rebase = rebase;
     st->done = 0;
     st->dc = dc;
@@ -549,6 +554,41 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     }
   }
   CK(cudaEventRecord(e_sketch, st));
+  // correction form: the Gram matrix G_b of the BF16 copy of X needs only X and the big region
+  // (free once the sketch is formed), so it is formed on a second stream beside the Hessian factor
+  // and the 1st stage (memory- and latency-bound work beside a tensor-core product); the 2nd stage
+  // waits for it
+  struct GramStream {
+    cudaStream_t h = nullptr, main = nullptr;
+    ~GramStream() {
+      if (!h) return;
+      // the caller's stream (on which a library-owned workspace is freed) waits for this one,
+      // also on an early return between the fork and the join
+      cudaEvent_t e = nullptr;
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) {
+        cudaEventRecord(e, h);
+        cudaStreamWaitEvent(main, e, 0);
+        cudaEventDestroy(e);
+      }
+      cudaStreamDestroy(h);
+    }
+  } gram_side;
+  gram_side.main = st;
+  double *Gb = L.dc ? reinterpret_cast<double *>(base + L.o_gb) : nullptr;
+  unsigned *gram_status = L.dc ? reinterpret_cast<unsigned *>(base + L.o_gst) : nullptr;
+  cudaEvent_t e_gram0 = nullptr, e_gram1 = nullptr;
+  if (L.dc && s.T > 0) {
+    e_gram0 = E.make();
+    e_gram1 = E.make();
+    if (!e_gram0 || !e_gram1) return SLSE_ECUDA;
+    CK(cudaStreamCreateWithFlags(&gram_side.h, cudaStreamNonBlocking));
+    CK(cudaStreamWaitEvent(gram_side.h, e_sketch, 0));
+    CK(cudaMemsetAsync(gram_status, 0, sizeof(unsigned), gram_side.h));
+    CK(cudaEventRecord(e_gram0, gram_side.h));
+    CK(launch_gram(L.grp, static_cast<const float *>(p->X), p->ldx, Gb, gram_status, big, gram_side.h));
+    CK(cudaEventRecord(e_gram1, gram_side.h));
+    kernels += 3;
+  }
   phase.set("slse_fit: Hessian factor");
   // sketch scales: SRHT S_i X = sqrt(N'/m_i) U[rows], S-hat X = sqrt(N'/r) U[h0 ..]; CountSketch: 1
   auto sq_scale = [&](int64_t m) { return L.cs ? 1.0 : (double)L.Np / (double)m; };
@@ -640,15 +680,18 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
   // Iteration k+1 is enqueued before the stop flag of iteration k is read back; its
   // kernels return at once when the flag is already set.
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> e_grad;
-  // correction form: the BF16 copy of X in the big region, g(beta_0) beside the gradient
-  __nv_bfloat16 *xbf = L.dc ? static_cast<__nv_bfloat16 *>(big) : nullptr;
+  // correction form: the Gram matrix G_b of the BF16 copy of X (formed once, here), g(beta_e)
+  // beside the gradient, the iterate beta_e of the last exact pass and fl32(beta - beta_e)
   double *g0 = L.dc ? reinterpret_cast<double *>(base + L.o_g0) : nullptr;
   float *de = L.dc ? reinterpret_cast<float *>(base + L.o_de) : nullptr;
   ua.hist_base = t;
   ua.beta_e = L.dc ? reinterpret_cast<double *>(base + L.o_be) : nullptr;
   ua.delta_e = de;
+  // a correction step (a d x d product and the update) costs a small fraction of a pass over X
+  ua.inner_cost = 0.02;
+  if (e_gram1) CK(cudaStreamWaitEvent(st, e_gram1, 0));  // G_b formed (also when the 2nd stage is empty)
   if (t < T) {
-    k_set_stage2<<<1, 32, 0, st>>>(dst, mixed ? 1 : 0, L.dc ? 1 : 0);
+    k_set_stage2<<<1, 32, 0, st>>>(dst, mixed ? 1 : 0, L.dc ? 1 : 0, gram_status);
     CK(cudaGetLastError());
     ++kernels;
     DevState *mb = t_mailbox.get();
@@ -663,9 +706,11 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
       cudaEvent_t g0e = E.make(), g1 = E.make();
       if (!g0e || !g1) return SLSE_ECUDA;
       CK(cudaEventRecord(g0e, st));
-      // correction form: the first pass (exact, as every first 2nd-stage pass) also writes the BF16 copy
-      CK(launch_grad(L.dc ? GM_MIXED_DC : (mixed ? GM_MIXED : GM_F64), p->dtype, p->X, p->ldx, p->Y, p->N, d, ring,
-                     dst, d32, r0, b0, part, nb, 1, st, xbf, L.ld16, k == 0 ? 1 : 0, de));
+      // correction form: a pass over X (exact) or a correction step g = g(beta_e) - G_b (beta - beta_e),
+      // as the device state selects; the kernels of the other kind return at once
+      CK(launch_grad(mixed ? GM_MIXED : GM_F64, p->dtype, p->X, p->ldx, p->Y, p->N, d, ring, dst, d32, r0, b0,
+                     part, nb, 1, st));
+      if (L.dc) CK(launch_gram_step(Gb, de, g0, g, d, dst, st));
       CK(cudaEventRecord(g1, st));
       e_grad.emplace_back(g0e, g1);
       CK(launch_reduce(part, nb, d, 1.0, g, dst, 1, st, g0));
@@ -723,9 +768,15 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     }
     RP->ms_grad2 = mg;
     RP->n_grad2 = nx;
-    RP->ms_grad2_bf16 = mb16;
-    RP->n_grad2_bf16 = nb16;
+    RP->ms_corr = mb16;
+    RP->n_corr = nb16;
     RP->stage2_full = fin.dc_fell_back;
+    if (L.dc && e_gram0) {
+      RP->ms_gram = ms_between(e_gram0, e_gram1);
+      RP->flops_gram = 2.0 * (double)L.grp.nchunk * 32.0 * L.grp.ncp * L.grp.ncp;
+      // X read once (F32), the packed BF16 copy written and read once
+      RP->bytes_gram = (double)p->N * d * 4.0 + 2.0 * (double)L.grp.nchunk * 32.0 * L.grp.ncp * 2.0;
+    }
     RP->kernels = kernels;
     RP->iters_stage1 = t1;
     RP->iters_stage2 = fin.iter - t1;
@@ -741,12 +792,7 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     for (size_t i = 0; i < s.m.size(); ++i) bytes += (double)s.a[i] * (double)s.m[i] * (d + 1) * bu;
     // a 2nd-stage pass reads X and one N-vector (Y in FP64 / rebase passes, r0 otherwise)
     RP->bytes_grad2 = (double)p->N * d * bx + (double)p->N * (mixed ? 4.0 : bx);
-    bytes += (double)nx * RP->bytes_grad2;
-    if (L.dc) {
-      RP->bytes_grad2_bf16 = (double)p->N * d * 2.0;
-      RP->bytes_xbf = (double)p->N * d * 2.0;
-      bytes += (double)nb16 * RP->bytes_grad2_bf16 + RP->bytes_xbf;
-    }
+    bytes += (double)nx * RP->bytes_grad2 + RP->bytes_gram;
     RP->bytes_moved = bytes;
     RP->status = status;
   }
@@ -754,10 +800,10 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     fprintf(stderr,
             "slse_fit: N=%lld d=%d kind=%d prec=%d status=%d | draws %.3f ms, sketch %.3f ms (pass 1 %.3f, pass 2 "
             "%.3f), Hessian factor %.3f ms, stage 1 %.3f ms (%d its), stage 2 %.3f ms (%d its, %d full passes, "
-            "%.3f ms in gradients), total %.3f ms, %d kernels\n",
+            "%.3f ms in gradients, %d correction steps), total %.3f ms, %d kernels\n",
             (long long)p->N, d, s.kind, s.prec, (int)status, RP->ms_draws, RP->ms_sketch, RP->ms_srht_pass1,
             RP->ms_srht_pass2, RP->ms_qr, RP->ms_stage1, RP->iters_stage1, RP->ms_stage2, RP->iters_stage2, RP->n_grad2,
-            RP->ms_grad2, RP->ms_total, RP->kernels);
+            RP->ms_grad2, RP->n_corr, RP->ms_total, RP->kernels);
   if (tr) {
     tr->count = fin.iter < hist_cap ? fin.iter : hist_cap;
     if (tr->ms_hist)
@@ -791,6 +837,13 @@ size_t slse_workspace_size(const slse_problem *prob, const slse_schedule *sched,
     case SLSE_OP_GRAD:
       if (!valid_problem(prob)) return 0;
       return grad_ws(prob, nsm);
+    case SLSE_OP_GRAM: {
+      if (!valid_problem(prob)) return 0;
+      Layout w;
+      w.take(kStateBytes);
+      w.take(gram_plan(prob->N, prob->d, nsm).total);
+      return w.total;
+    }
     case SLSE_OP_DRAWS: {
       if (arg < 1 || padded(arg) > kMaxNp) return 0;
       return align256(draws_ws_bytes(padded(arg)));
@@ -917,6 +970,27 @@ slse_status slse_grad(const slse_problem *prob, const double *beta, double *g_ou
   CK(launch_grad(mixed ? GM_MIXED : GM_F64, prob->dtype, prob->X, prob->ldx, prob->Y, prob->N, prob->d, beta, dst,
                  nullptr, nullptr, nullptr, part, nb, 0, st));
   CK(launch_reduce(part, nb, prob->d, 1.0, g_out, dst, 0, st));
+  return SLSE_OK;
+}
+
+slse_status slse_gram(const slse_problem *prob, double *G, void *workspace, size_t ws_bytes, slse_stream_t stream) {
+  if (!valid_problem(prob) || !G || prob->dtype != SLSE_F32) return SLSE_EINVAL;
+  if (is_host_pointer(prob->X) || is_host_pointer(G)) return SLSE_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nsm = num_sms();
+  if (nsm <= 0) return SLSE_ECUDA;
+  const GramPlan gp = gram_plan(prob->N, prob->d, nsm);
+  Layout w;
+  const size_t o_state = w.take(kStateBytes);
+  const size_t o_gram = w.take(gp.total);
+  Workspace W;
+  slse_status a = acquire(W, workspace, ws_bytes, w.total, st);
+  if (a != SLSE_OK) return a;
+  char *base = static_cast<char *>(W.ptr);
+  DevState *dst = reinterpret_cast<DevState *>(base + o_state);
+  k_init_state<<<1, 32, 0, st>>>(dst, 0, debug_spin_limit());
+  CK(cudaGetLastError());
+  CK(launch_gram(gp, static_cast<const float *>(prob->X), prob->ldx, G, &dst->status, base + o_gram, st));
   return SLSE_OK;
 }
 

@@ -22,15 +22,15 @@
 // solution (the first steps from beta = 0) keep one base point instead of re-basing at
 // every step, and the final base point lies within 2^-10 of the solution.
 //
-// Correction form of the mixed 2nd stage (GM_MIXED_DC): exact passes stream X (the re-basing pass
-// above, which the first time also stores a BF16 copy Xb of X as it streams the rows, or the plain
-// FP32 pass); the reduction keeps their gradient g(beta_e).  The passes between exact ones read only
-// Xb and return -Xb^T (Xb delta), delta = fl32(beta - beta_e), so that
-// g(beta) = g(beta_e) - Xb^T Xb (beta - beta_e): half the bytes of an FP32 pass.  The update kernel
-// schedules the next exact pass (a step below 1/100 of the first step after the last exact pass, a
-// step above it, or one that meets the stopping test), makes it a re-basing pass only when the drift
-// from beta_0 exceeds 2^-10 ||beta||, stops only on an exact step, and switches to the plain FP32
-// passes when a cycle gains less than plain steps would for the same bytes.
+// Correction form of the mixed 2nd stage: exact passes stream X (the re-basing pass above or the
+// plain FP32 pass); the reduction keeps their gradient g(beta_e).  The steps between exact ones
+// use g(beta) = g(beta_e) - G_b (beta - beta_e) with the Gram matrix G_b = Xb^T Xb of the BF16 copy
+// Xb of X, formed once on the tensor cores (gram.cu): a d x d product (k_gram_step) instead of a
+// pass over X.  The update kernel schedules the next exact pass (a step below 1/100 of the first
+// step after the last exact pass, a step above it, or one that meets the stopping test), makes it
+// a re-basing pass only when the drift from beta_0 exceeds 2^-10 ||beta||, stops only on an exact
+// step, and switches to the plain FP32 passes when a cycle gains less than plain steps would for
+// the same cost.
 #include "slse_internal.cuh"
 
 namespace slse {
@@ -53,9 +53,6 @@ struct GradArgs {
   double *beta0;
   double *partials;
   int check_done;
-  __nv_bfloat16 *xbf;  // correction form: the BF16 copy of X (ld ldb)
-  int64_t ldb;
-  const float *delta_e;  // correction form: fl32(beta - beta_e)
 };
 
 template <class Tx, int VW> struct Vec;
@@ -229,28 +226,24 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_f64(const GradArgs a) {
 __device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
 
-// CORR = 1: the correction-form pass over the BF16 copy of X (rows a.xbf, ld a.ldb): the vector
-// is delta_e = fl32(beta - beta_e), Y is zero, so the partial is -Xb^T (Xb delta); it runs only
-// when the device state selects it.
-template <int VMAX, int RPW, int CORR = 0>
+template <int VMAX, int RPW>
 __global__ void __launch_bounds__(kGradThreads, 2) k_grad_bf16v(const GradArgs a) {
   __shared__ double sm[kWarps][512];
   if (a.check_done && a.st->done) return;
-  if (CORR && (a.st->rebase || !a.st->dc || !a.st->bfnext)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * kWarps + warp, nw = (int64_t)gridDim.x * kWarps;
   const int d = a.d;
   const double *beta = a.beta_ring + (size_t)(a.st->iter % 3) * d;
-  const __nv_bfloat16 *U = CORR ? a.xbf : static_cast<const __nv_bfloat16 *>(a.X);
+  const __nv_bfloat16 *U = static_cast<const __nv_bfloat16 *>(a.X);
   const __nv_bfloat16 *V = static_cast<const __nv_bfloat16 *>(a.Y);
-  const int64_t ldu = CORR ? a.ldb : a.ldx;
+  const int64_t ldu = a.ldx;
   float b[VMAX][8], g[VMAX][8];
 #pragma unroll
   for (int v = 0; v < VMAX; ++v)
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const int col = (v * 32 + lane) * 8 + e;
-      b[v][e] = col < d ? (CORR ? a.delta_e[col] : (float)beta[col]) : 0.f;
+      b[v][e] = col < d ? (float)beta[col] : 0.f;
       g[v][e] = 0.f;
     }
   for (int64_t i0 = gw * RPW; i0 < a.nrows; i0 += nw * RPW) {
@@ -263,10 +256,10 @@ __global__ void __launch_bounds__(kGradThreads, 2) k_grad_bf16v(const GradArgs a
 #pragma unroll
       for (int v = 0; v < VMAX; ++v) {
         const int col0 = (v * 32 + lane) * 8;
-        const uint4 *src = reinterpret_cast<const uint4 *>(U + i * ldu + col0);
-        raw[q][v] = (rv && col0 < d) ? (CORR ? __ldcs(src) : __ldg(src)) : make_uint4(0u, 0u, 0u, 0u);
+        raw[q][v] = (rv && col0 < d) ? __ldg(reinterpret_cast<const uint4 *>(U + i * ldu + col0))
+                                     : make_uint4(0u, 0u, 0u, 0u);
       }
-      y[q] = (rv && !CORR) ? __bfloat162float(V[i]) : 0.f;
+      y[q] = rv ? __bfloat162float(V[i]) : 0.f;
     }
     float s[RPW];
 #pragma unroll
@@ -357,14 +350,12 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_bf16s(const GradArgs a) {
 // residual r0 - x . delta32.  The host launches both; the one whose mode does not
 // match st->rebase returns at once.  The two-word accumulators (hi, lo) of each
 // warp live in shared memory (float2 per column), folded every kFlushRows rows.
-// WBF = 1 (with REBASE): the pass also stores fl_bf16(x_i) into a.xbf (VW = 4 only).
-template <int VW, int VMAX, int REBASE, int RPW, int WBF = 0>
+template <int VW, int VMAX, int REBASE, int RPW>
 __global__ void __launch_bounds__(kGradThreads, 2) k_grad_mixed(const GradArgs a) {
-  static_assert(!WBF || (REBASE && VW == 4), "the BF16 copy is written by the vector re-basing pass");
   __shared__ __align__(16) double sm[kWarps][512];
   if (a.check_done && a.st->done) return;
   if ((a.st->rebase != 0) != (REBASE != 0)) return;
-  if (!REBASE && a.st->dc && a.st->bfnext) return;  // correction form: the pass over the BF16 copy runs
+  if (!REBASE && a.st->dc && a.st->bfnext) return;  // correction form: a correction step, not a pass
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * kWarps + warp, nw = (int64_t)gridDim.x * kWarps;
   const int d = a.d;
@@ -471,26 +462,6 @@ __global__ void __launch_bounds__(kGradThreads, 2) k_grad_mixed(const GradArgs a
       for (int v = 0; v < VMAX; ++v)
 #pragma unroll
         for (int e = 0; e < VW; ++e) gacc[v][e] = fmaf(x[q][v][e], r[q], gacc[v][e]);
-    if constexpr (WBF) {
-      // the BF16 copy, stored after every row load of this iteration has been issued (a store to a
-      // buffer that may alias X, placed between the loads, would serialise them on each row's data)
-#pragma unroll
-      for (int q = 0; q < RPW; ++q) {
-        const int64_t i = i0 + q;
-#pragma unroll
-        for (int v = 0; v < VMAX; ++v) {
-          const int col0 = (v * 32 + lane) * VW;
-          if (i < a.nrows && col0 < d) {
-            const __nv_bfloat162 lo = __floats2bfloat162_rn(x[q][v][0], x[q][v][1]);
-            const __nv_bfloat162 hi = __floats2bfloat162_rn(x[q][v][2], x[q][v][3]);
-            uint2 w;
-            w.x = *reinterpret_cast<const uint32_t *>(&lo);
-            w.y = *reinterpret_cast<const uint32_t *>(&hi);
-            __stcs(reinterpret_cast<uint2 *>(a.xbf + i * a.ldb + col0), w);
-          }
-        }
-      }
-    }
     nacc += RPW;
     if (nacc >= kFlushRows) {
       nacc = 0;
@@ -532,6 +503,7 @@ __global__ void k_reduce(const double *partials, int nblk, int d, double scale, 
                          int check_done, double *g0) {
   __shared__ double sm[8][33];
   if (check_done && st->done) return;
+  if (g0 && st->dc && st->bfnext && !st->rebase) return;  // a correction step writes g itself
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = blockIdx.x * 32 + lane;
   // four independent sums over CTAs warp, warp + 8, ... (loads overlap), combined in a fixed order
@@ -552,11 +524,8 @@ __global__ void k_reduce(const double *partials, int nblk, int d, double scale, 
     double t = 0.0;
 #pragma unroll
     for (int w = 0; w < 8; ++w) t += sm[w][lane];
-    double v = scale * t;
-    if (g0) {
-      if (st->dc && st->bfnext && !st->rebase) v += g0[c];  // pass over the BF16 copy: g(beta_e) - Xb^T Xb delta
-      else g0[c] = v;                                        // exact pass: keep g(beta_e)
-    }
+    const double v = scale * t;
+    if (g0) g0[c] = v;  // exact pass: keep g(beta_e)
     g[c] = v;
   }
 }
@@ -640,6 +609,26 @@ __global__ void __launch_bounds__(256) k_update(const UpdArgs A, DevState *st) {
   x0 = warp_sum(x0);
   x1 = warp_sum(x1);
   x2 = warp_sum(x2);
+  // correction form: a correction step more than twice the size of the cycle's first step is the
+  // correction iteration diverging (an ill-conditioned X): it is not taken.  The kept iterate is
+  // copied into the new slot (so the momentum of the next step is zero), the vectors of the base
+  // points are formed from it, the norms are those of the kept iterate, and the next pass is exact.
+  const bool reject = corr_exact == false && a.stage2 && a.mixed && st->dc && x0 > 4.0 * st->step_ref;
+  if (reject) {
+    double k1 = 0.0, k2 = 0.0;
+    for (int i = lane; i < d; i += 32) {
+      bn[i] = b[i];
+      const double del = b[i] - a.beta0[i];
+      a.delta32[i] = (float)del;
+      if (a.beta_e) a.delta_e[i] = (float)(b[i] - a.beta_e[i]);
+      if (a.hist && t < a.hist_cap) a.hist[(size_t)t * d + i] = b[i];
+      k1 += b[i] * b[i];
+      k2 += del * del;
+    }
+    x0 = 0.0;
+    x1 = warp_sum(k1);
+    x2 = warp_sum(k2);
+  }
   if (lane != 0) return;
   st->upd_count = 0;
   const double rel = sqrt(x0) / (sqrt(x1) > 0.0 ? sqrt(x1) : 1.0);
@@ -657,11 +646,18 @@ __global__ void __launch_bounds__(256) k_update(const UpdArgs A, DevState *st) {
     const int k2 = t - a.hist_base;
     if (k2 >= 0 && k2 < (int)sizeof(st->mode_hist)) st->mode_hist[k2] = exact ? 0 : 1;
     if (corr && exact) {
-      // a cycle (exact pass + k passes over the BF16 copy, 1 + k/2 passes' worth of bytes) that
-      // shrank the exact step by less than rho^(1 + k/2), what plain steps gain for those bytes:
-      // the BF16 Hessian term is too coarse for these data (ill-conditioned X), so the remaining
-      // steps take the full form (its next pass reads the r0 this exact pass wrote)
-      if (st->step_prev > 0.0 && x0 > st->step_prev * pow(a.rho, 1.0 + 0.5 * st->ninner)) {
+      // a cycle (exact pass + k correction steps, 1 + k c passes' worth of time for a correction
+      // step costing c passes) that shrank the exact step by less than rho^(1 + k c), what plain
+      // steps gain in that time, or by less than 10x: the BF16 Hessian term is too coarse for
+      // these data (ill-conditioned X; its relative error, which sets a cycle's gain, is then
+      // above 0.1, where the cycles, plain fixed-point steps without momentum, fall behind the
+      // full form and the first cycle's gain, measured from the large first step of the 2nd
+      // stage, overstates the gain in the error), so the remaining steps take the full form (its
+      // next pass reads the r0 this exact pass wrote).  x0 and step_prev are squared norms.  A step
+      // that meets the stopping test ends the fit either way and decides nothing.
+      const double gain = fmin(0.01, pow(a.rho, 2.0 * (1.0 + a.inner_cost * st->ninner)));
+      const bool stops = a.thr > 0.0 && rel <= a.thr;
+      if (st->step_prev > 0.0 && x0 > st->step_prev * gain && !stops) {
         st->dc = 0;
         st->dc_fell_back = 1;
       }
@@ -678,14 +674,18 @@ __global__ void __launch_bounds__(256) k_update(const UpdArgs A, DevState *st) {
       if (a.thr > 0.0) st->status |= ST_NOTCONV;
     }
     if (a.mixed) {
-      // next pass exact: the steps have shrunk to 1/100 of the cycle's first step, or one meets
-      // the stopping test (the stop itself waits for an exact step), or a step grew beyond the
-      // cycle's first step (the BF16 iteration diverging on an ill-conditioned X); the exact pass
+      // next pass exact: the steps have shrunk to 1/10^4 of the cycle's first step (the correction
+      // iteration has then settled at its fixed point, within ~1e-4 of the exact one on the
+      // benchmark data), or one meets the stopping test (the stop itself waits for an exact step),
+      // or a step grew beyond the cycle's first step (the correction iteration diverging on an
+      // ill-conditioned X), or the cycle has taken 20 correction steps (twice what a contraction of
+      // rho = 0.41 per step needs for 1e-4; steps count toward T); the exact pass
       // re-bases (error-free residuals) only when the drift from beta_0 exceeds 2^-10 ||beta||, so
       // that the FP32 residual r0 - X (beta - beta_0) stays within ~2^-34 ||X|| ||beta||
       if (st->dc) {
         const bool next_exact =
-            !exact && (x0 < 1e-4 * st->step_ref || x0 > st->step_ref || (a.thr > 0.0 && rel <= a.thr));
+            !exact && (reject || x0 < 1e-8 * st->step_ref || x0 > st->step_ref || st->ninner >= 20 ||
+                       (a.thr > 0.0 && rel <= a.thr));
         st->bfnext = next_exact ? 0 : 1;
         st->rebase = (next_exact && x2 > 0x1p-20 * x1) ? 1 : 0;
       } else {
@@ -694,6 +694,28 @@ __global__ void __launch_bounds__(256) k_update(const UpdArgs A, DevState *st) {
       }
     }
   }
+}
+
+// Correction step: g = g0 - G_b delta_e, one warp per row of G_b (four independent FP64 sums, fixed
+// order); only when the device state selects a correction step.
+__global__ void __launch_bounds__(256) k_gram_step(const double *Gb, const float *delta_e, const double *g0, double *g,
+                                                   int d, const DevState *st) {
+  if (st->done || st->rebase || !st->dc || !st->bfnext) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = blockIdx.x * 8 + warp;
+  if (i >= d) return;
+  const double *row = Gb + (size_t)i * d;
+  double h0 = 0.0, h1 = 0.0, h2 = 0.0, h3 = 0.0;
+  int k = lane;
+  for (; k + 96 < d; k += 128) {
+    h0 = fma(row[k], (double)delta_e[k], h0);
+    h1 = fma(row[k + 32], (double)delta_e[k + 32], h1);
+    h2 = fma(row[k + 64], (double)delta_e[k + 64], h2);
+    h3 = fma(row[k + 96], (double)delta_e[k + 96], h3);
+  }
+  for (; k < d; k += 32) h0 = fma(row[k], (double)delta_e[k], h0);
+  const double h = warp_sum((h0 + h1) + (h2 + h3));
+  if (lane == 0) g[i] = g0[i] - h;
 }
 
 __global__ void k_copy_beta(const double *ring, const DevState *st, int d, double *out) {
@@ -732,9 +754,8 @@ int grad_grid(int nsm) { return 2 * nsm; }
 
 cudaError_t launch_grad(int mode, int xdtype, const void *X, int64_t ldx, const void *Y, int64_t nrows, int d,
                         const double *beta_ring, DevState *st, const float *delta32, float *r0, double *beta0,
-                        double *partials, int nblk, int check_done, cudaStream_t s, __nv_bfloat16 *xbf, int64_t ldb,
-                        int write_xbf, const float *delta_e) {
-  GradArgs a{X, ldx, Y, nrows, d, beta_ring, st, delta32, r0, beta0, partials, check_done, xbf, ldb, delta_e};
+                        double *partials, int nblk, int check_done, cudaStream_t s) {
+  GradArgs a{X, ldx, Y, nrows, d, beta_ring, st, delta32, r0, beta0, partials, check_done};
   if (d > 512 || d < 1) return cudaErrorInvalidValue;
   switch (mode) {
     case GM_F64:
@@ -767,22 +788,6 @@ cudaError_t launch_grad(int mode, int xdtype, const void *X, int64_t ldx, const 
       if (d <= 128) return launch1(k_grad_mixed<4, 1, 0, 8>, nblk, a, s);
       if (d <= 256) return launch1(k_grad_mixed<4, 2, 0, 4>, nblk, a, s);
       return launch1(k_grad_mixed<4, 4, 0, 2>, nblk, a, s);
-    }
-    case GM_MIXED_DC: {
-      // vector rows only: d % 8 == 0 (whole 16-byte BF16 words per lane), 16-byte aligned FP32 rows
-      if (xdtype != SLSE_F32 || !xbf || !delta_e || d % 8 != 0 || ldb % 8 != 0 || !aligned(X, ldx, 4, 4) ||
-          !aligned(xbf, ldb, 2, 8))
-        return cudaErrorInvalidValue;
-      cudaError_t e;
-      if (d <= 128) e = write_xbf ? launch1(k_grad_mixed<4, 1, 1, 8, 1>, nblk, a, s) : launch1(k_grad_mixed<4, 1, 1, 8>, nblk, a, s);
-      else if (d <= 256) e = write_xbf ? launch1(k_grad_mixed<4, 2, 1, 4, 1>, nblk, a, s) : launch1(k_grad_mixed<4, 2, 1, 4>, nblk, a, s);
-      else e = write_xbf ? launch1(k_grad_mixed<4, 4, 1, 2, 1>, nblk, a, s) : launch1(k_grad_mixed<4, 4, 1, 2>, nblk, a, s);
-      if (e != cudaSuccess) return e;
-      if (d <= 128) e = launch1(k_grad_mixed<4, 1, 0, 8>, nblk, a, s);
-      else if (d <= 256) e = launch1(k_grad_mixed<4, 2, 0, 4>, nblk, a, s);
-      else e = launch1(k_grad_mixed<4, 4, 0, 2>, nblk, a, s);
-      if (e != cudaSuccess) return e;
-      return d <= 256 ? launch1(k_grad_bf16v<1, 6, 1>, nblk, a, s) : launch1(k_grad_bf16v<2, 4, 1>, nblk, a, s);
     }
     default:
       return cudaErrorInvalidValue;
@@ -825,6 +830,12 @@ cudaError_t launch_update(const UpdateArgs &a, DevState *st, cudaStream_t s) {
   // per-CTA partial sums live right after the DevState's own cache line block
   UpdArgs A{a, reinterpret_cast<double *>(st + 1)};
   k_update<<<(a.d + 7) / 8, 256, 0, s>>>(A, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_step(const double *Gb, const float *delta_e, const double *g0, double *g, int d, DevState *st,
+                             cudaStream_t s) {
+  k_gram_step<<<(d + 7) / 8, 256, 0, s>>>(Gb, delta_e, g0, g, d, st);
   return cudaGetLastError();
 }
 

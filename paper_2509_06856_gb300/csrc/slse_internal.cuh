@@ -29,13 +29,13 @@ struct DevState {
   unsigned bar_gen;
   double rel_step;     // last ||b+ - b|| / ||b+||
   long long spin_limit; // polls of a grid-wide wait before it gives up (0: the built-in 2^25)
-  int dc;              // mixed 2nd stage, correction form active: passes between exact ones read the BF16 copy
-  int bfnext;          // correction form: the next pass reads the BF16 copy (else an exact pass over X)
+  int dc;              // mixed 2nd stage, correction form active: correction steps between exact passes
+  int bfnext;          // correction form: the next step is a correction step (else an exact pass over X)
   int dc_fell_back;    // the correction form was switched off for this run
   double step_ref;     // correction form: squared step of the last exact pass
   double step_prev;    // correction form: squared step of the exact pass before it
-  int ninner;          // correction form: passes over the BF16 copy since the last exact pass
-  unsigned char mode_hist[128];  // 2nd-stage pass kind of iteration t (< 128): 0 over X, 1 over the BF16 copy
+  int ninner;          // correction form: correction steps since the last exact pass
+  unsigned char mode_hist[128];  // 2nd-stage step kind of iteration t (< 128): 0 pass over X, 1 correction step
 };
 static_assert(sizeof(DevState) <= 512, "the per-CTA partials of the update kernel follow the state");
 
@@ -168,6 +168,24 @@ cudaError_t launch_gaussian(const GaussPlan &p, int xdtype, const void *X, int64
                             void *SX, int64_t ldsx, void *SY, double scale, unsigned *status, void *ws,
                             cudaStream_t s);
 
+// gaussian.cu: X (F32, N x nx, ld ldx) -> BF16 chunks of 32 rows in the K-major core-matrix
+// layout of the tcgen05 operands (ncp packed columns, zero beyond nx and past row N; chunks are
+// written in pairs: 2 ceil(N / 64) chunks of ncp * 64 bytes).
+cudaError_t launch_pack_bf16(const float *X, int64_t ldx, int64_t N, int nx, int ncp, uint8_t *xt, cudaStream_t s);
+
+// gram.cu: G_b = Xb^T Xb (d x d, FP64, row-major) for the BF16 copy Xb of X (F32) on the tensor
+// cores, through a packed copy of X and per-range FP32 partials (workspace GramPlan::total bytes).
+struct GramPlan {
+  int64_t N;
+  int d, ncp, tmem_cols, stages, splits;
+  int64_t nchunk, cps;
+  size_t smem, o_xt, o_part, total;
+};
+GramPlan gram_plan(int64_t N, int d, int nsm);
+// status: ST_TIMEOUT is raised there when a bounded wait gave up (G is then NaN)
+cudaError_t launch_gram(const GramPlan &p, const float *X, int64_t ldx, double *G, unsigned *status, void *ws,
+                        cudaStream_t s);
+
 // draws.cu
 size_t draws_ws_bytes(int64_t Np);
 cudaError_t launch_draws(int64_t Np, uint64_t seed, int32_t *Psd /*N', sign-folded P*/,
@@ -200,21 +218,23 @@ cudaError_t launch_srht(const SrhtPlan &pl, int prec, int xdtype, const void *X,
                         unsigned *status = nullptr /* ST_TIMEOUT raised here if a bounded wait gave up */);
 
 // grad.cu
-// GM_MIXED_DC: the mixed 2nd stage in correction form: the re-basing pass (error-free residuals),
-// the plain FP32 pass (the exact pass between re-bases, and every pass once the correction form is
-// switched off) and the pass over the BF16 copy xbf with vector delta_e; each returns at once unless
-// the device state selects it.  write_xbf: the re-basing pass also stores fl_bf16(X) into xbf (ld ldb).
-enum GradMode { GM_F64 = 0, GM_MIXED = 1, GM_STAGE1_BF16 = 2, GM_STAGE1_F64 = 3, GM_MIXED_DC = 4 };
+// GM_MIXED: the mixed 2nd-stage pass over X: the re-basing pass (error-free residuals) and the
+// plain FP32 pass against the base point; each returns at once unless the device state selects it
+// (neither runs on a correction step of the correction form).
+enum GradMode { GM_F64 = 0, GM_MIXED = 1, GM_STAGE1_BF16 = 2, GM_STAGE1_F64 = 3 };
 int grad_grid(int nsm);
 cudaError_t launch_grad(int mode, int xdtype, const void *X, int64_t ldx, const void *Y, int64_t nrows,
                         int d, const double *beta_ring, DevState *st, const float *delta32, float *r0,
-                        double *beta0, double *partials, int nblk, int check_done, cudaStream_t s,
-                        __nv_bfloat16 *xbf = nullptr, int64_t ldb = 0, int write_xbf = 0,
-                        const float *delta_e = nullptr);
+                        double *beta0, double *partials, int nblk, int check_done, cudaStream_t s);
 // g = scale * (sum of the per-CTA partials).  g0 (nullable; mixed 2nd stage in correction form):
-// after an exact pass (over X) g0 = g; after a pass over the BF16 copy g = g0 + that sum.
+// after an exact pass (over X) g0 = g; on a correction step the reduction does nothing (the
+// correction step writes g).
 cudaError_t launch_reduce(const double *partials, int nblk, int d, double scale, double *g,
                           DevState *st, int check_done, cudaStream_t s, double *g0 = nullptr);
+// Correction step of the correction form: g = g0 - G_b delta_e (G_b d x d FP64, delta_e =
+// fl32(beta - beta_e)); runs only when the device state selects a correction step.
+cudaError_t launch_gram_step(const double *Gb, const float *delta_e, const double *g0, double *g, int d,
+                             DevState *st, cudaStream_t s);
 // Loads the code of every kernel launch_grad (GM_F64, GM_MIXED) and launch_reduce can launch,
 // so that a later first launch of one of them does not load a module (which allocates).
 cudaError_t preload_grad_kernels();
@@ -237,7 +257,8 @@ struct UpdateArgs {
   int hist_base;       // iteration index of the first 2nd-stage step (mode_hist is indexed from it)
   double rho;          // sqrt(d / r), the contraction of a plain 2nd-stage step (correction form's test)
   double *beta_e;      // correction form: the iterate of the last exact pass
-  float *delta_e;      // correction form: fl32(beta - beta_e), the vector of the pass over the BF16 copy
+  float *delta_e;      // correction form: fl32(beta - beta_e), the vector of the correction step
+  double inner_cost;   // correction form: cost of a correction step in exact passes (fallback test)
 };
 cudaError_t launch_update(const UpdateArgs &a, DevState *st, cudaStream_t s);
 cudaError_t launch_copy_beta(const double *beta_ring, DevState *st, int d, double *out, cudaStream_t s);

@@ -218,14 +218,14 @@ def test_fit_mixed_reaches_ols_1e8(slse, N, d, stage2):
     err = np.linalg.norm(res.beta - bh) / np.linalg.norm(bh)
     assert err <= 1e-8, err
     assert res.report["rebases"] >= 1
-    # the correction form runs for d % 8 == 0 (vector rows); its passes over the BF16 copy
-    # are counted apart from the exact passes, and the stop comes on an exact pass
-    bf16_passes = res.report["n_grad2_bf16"]
-    if stage2 == "correction" and d % 8 == 0:
-        assert bf16_passes > 0 and res.report["stage2_full"] == 0
-        assert res.report["bytes_xbf"] == N * d * 2.0
+    # the correction form's correction steps (products with the Gram matrix of the BF16 copy,
+    # formed once) are counted apart from the exact passes; well-conditioned data never need the
+    # fallback to the full form
+    if stage2 == "correction":
+        assert res.report["n_corr"] > 0 and res.report["stage2_full"] == 0
+        assert res.report["ms_gram"] > 0.0
     else:
-        assert bf16_passes == 0
+        assert res.report["n_corr"] == 0
 
 
 def test_fit_mixed_correction_falls_back_on_ill_conditioned_x(slse):
