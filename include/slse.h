@@ -158,9 +158,11 @@ typedef struct {
                              included in ms_grad2, which then covers the exact passes over X) */
   int32_t n_corr;         /* number of correction steps */
   int32_t stage2_full;    /* 1 if a correction run fell back to the full form */
-  double ms_gram;         /* CUDA-event time of forming the Gram matrix of the BF16 copy of X (pack + MMA) */
-  double flops_gram;      /* its tensor-core FLOPs (2 N' ncp^2, ncp = d rounded up to 128) */
-  double bytes_gram;      /* its algorithmic HBM bytes (X read, the packed BF16 copy written and read) */
+  double ms_gram;         /* CUDA-event time of forming the Gram matrix of the BF16 rounding of X */
+  double flops_gram;      /* its tensor-core FLOPs: the upper block triangle, 2 N' 128 sum_b (ncp - 128 b),
+                             ncp = d rounded up to 128, N' = N rounded up to 32 (64 when packed) */
+  double bytes_gram;      /* its algorithmic HBM bytes: X read, the per-range FP32 partials written and
+                             read (and, for X not read directly, the packed BF16 copy written and read) */
 } slse_report;
 
 typedef struct {
@@ -241,7 +243,8 @@ slse_status slse_grad_noalloc(const slse_problem *prob, const double *beta, doub
  * (prob->dtype F32, device): the Hessian term of the mixed 2nd stage's correction form
  * (SLSE_STAGE2_CORRECTION; the Hessian X^T X of Sec. 1 with X rounded to BF16).  Products of BF16
  * values are exact in FP32; they are accumulated on the tensor cores in FP32 over ranges of rows
- * and the ranges are added in FP64 in a fixed order.  Asynchronous on `stream`; workspace from
+ * and the ranges are added in FP64 in a fixed order; the upper triangle is formed and mirrored, so
+ * G is exactly symmetric.  Asynchronous on `stream`; workspace from
  * slse_workspace_size(SLSE_OP_GRAM).  No paper counterpart as an entry point. */
 slse_status slse_gram(const slse_problem *prob, double *G, void *workspace, size_t ws_bytes, slse_stream_t stream);
 

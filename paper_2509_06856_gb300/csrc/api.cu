@@ -276,9 +276,12 @@ __global__ void k_init_state(DevState *st, int rebase, long long spin_limit) {
 __global__ void k_clear_numeric(DevState *st) {
   if (threadIdx.x == 0 && blockIdx.x == 0) st->status &= ~ST_NUMERIC;
 }
-__global__ void k_set_stage2(DevState *st, int rebase, int dc, const unsigned *side_status) {
+__global__ void k_or_status(DevState *st, const unsigned *side_status) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) st->status |= *side_status;
+}
+
+__global__ void k_set_stage2(DevState *st, int rebase, int dc) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
-    if (side_status) st->status |= *side_status;  // a timeout of the Gram build
     st->rebase = rebase;
     st->done = 0;
     st->dc = dc;
@@ -587,7 +590,7 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     CK(cudaEventRecord(e_gram0, gram_side.h));
     CK(launch_gram(L.grp, static_cast<const float *>(p->X), p->ldx, Gb, gram_status, big, gram_side.h));
     CK(cudaEventRecord(e_gram1, gram_side.h));
-    kernels += 3;
+    kernels += gram_fp32_path(L.grp, static_cast<const float *>(p->X), p->ldx) ? 2 : 3;  // (pack,) Gram, reduce
   }
   phase.set("slse_fit: Hessian factor");
   // sketch scales: SRHT S_i X = sqrt(N'/m_i) U[rows], S-hat X = sqrt(N'/r) U[h0 ..]; CountSketch: 1
@@ -689,9 +692,21 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
   ua.delta_e = de;
   // a correction step (a d x d product and the update) costs a small fraction of a pass over X
   ua.inner_cost = 0.02;
-  if (e_gram1) CK(cudaStreamWaitEvent(st, e_gram1, 0));  // G_b formed (also when the 2nd stage is empty)
+  // G_b is first read by the 2nd stage's second step (its first pass is exact), so the main stream
+  // waits for the side stream only there: the Gram build also overlaps that pass.  The wait is
+  // enqueued before the call's last synchronisation in every case.
+  bool gram_joined = e_gram1 == nullptr;
+  auto join_gram = [&]() -> cudaError_t {
+    if (gram_joined) return cudaSuccess;
+    gram_joined = true;
+    cudaError_t e = cudaStreamWaitEvent(st, e_gram1, 0);
+    if (e != cudaSuccess) return e;
+    k_or_status<<<1, 32, 0, st>>>(dst, gram_status);  // a timeout of the Gram build
+    ++kernels;
+    return cudaGetLastError();
+  };
   if (t < T) {
-    k_set_stage2<<<1, 32, 0, st>>>(dst, mixed ? 1 : 0, L.dc ? 1 : 0, gram_status);
+    k_set_stage2<<<1, 32, 0, st>>>(dst, mixed ? 1 : 0, L.dc ? 1 : 0);
     CK(cudaGetLastError());
     ++kernels;
     DevState *mb = t_mailbox.get();
@@ -705,6 +720,7 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     for (int k = 0; t + k < T; ++k) {
       cudaEvent_t g0e = E.make(), g1 = E.make();
       if (!g0e || !g1) return SLSE_ECUDA;
+      if (k == 1) CK(join_gram());
       CK(cudaEventRecord(g0e, st));
       // correction form: a pass over X (exact) or a correction step g = g(beta_e) - G_b (beta - beta_e),
       // as the device state selects; the kernels of the other kind return at once
@@ -727,6 +743,7 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
       }
     }
   }
+  CK(join_gram());
   CK(launch_copy_beta(ring, dst, d, outb, st));
   ++kernels;
   DevState *mb = t_mailbox.get();
@@ -773,9 +790,9 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     RP->stage2_full = fin.dc_fell_back;
     if (L.dc && e_gram0) {
       RP->ms_gram = ms_between(e_gram0, e_gram1);
-      RP->flops_gram = 2.0 * (double)L.grp.nchunk * 32.0 * L.grp.ncp * L.grp.ncp;
-      // X read once (F32), the packed BF16 copy written and read once
-      RP->bytes_gram = (double)p->N * d * 4.0 + 2.0 * (double)L.grp.nchunk * 32.0 * L.grp.ncp * 2.0;
+      const bool f32 = gram_fp32_path(L.grp, static_cast<const float *>(p->X), p->ldx);
+      RP->flops_gram = f32 ? L.grp.flops_f32 : L.grp.flops_packed;
+      RP->bytes_gram = f32 ? L.grp.bytes_f32 : L.grp.bytes_packed;
     }
     RP->kernels = kernels;
     RP->iters_stage1 = t1;

@@ -1,22 +1,39 @@
-// Gram matrix G_b = Xb^T Xb of the BF16 copy Xb of X on the tensor cores, for the Hessian term
+// Gram matrix G_b = Xb^T Xb of the BF16 rounding Xb of X on the tensor cores, for the Hessian term
 // of the mixed 2nd stage's correction form: between exact passes the gradient is
 // g(beta) = g(beta_e) - Xb^T Xb (beta - beta_e), and with G_b formed once each of those steps is a
-// d x d product instead of a pass over the N x d copy.  Xb^T Xb is a dense (d x N)(N x d)
-// contraction, so it runs on tcgen05 (BF16 operands, FP32 accumulation in tensor memory).
+// d x d product instead of a pass over X.  Xb^T Xb is a dense (d x N)(N x d) contraction, so it
+// runs on tcgen05 (BF16 operands, FP32 accumulation in tensor memory).
 //
-// Xb is packed by the Gaussian sketch's packer into chunks of 32 rows in the K-major core-matrix
-// layout of the MMA operands (element (n, k) of a chunk at byte (n div 8) 512 + (k div 8) 128 +
-// (n mod 8) 16 + (k mod 8) 2, n the column of X and k the row in the chunk).  The same chunk is
-// both operands: A is the CTA's block of 128 columns (M = 128: rows m0 .. m0 + 127 of G_b, which
-// start at byte m0 64 of the chunk), B the whole chunk (N = ncp in pieces of <= 256).  The CTAs of
-// one chunk range (one per 128-column block, adjacent in the grid) read the same chunks, the first
-// from DRAM and the others mostly from L2.  Each CTA keeps its 128 x ncp accumulator in tensor
-// memory for its whole range (at most 8192 rows) and writes it as an FP32 partial; k_gram_reduce
-// adds the partials of the ranges in a fixed order in FP64 (deterministic).  Every mbarrier wait gives up after 2 s
-// (ST_TIMEOUT, NaN output), copies in flight are awaited and tensor memory is freed on that path
-// too.  Shared memory is sized so that one CTA runs per SM (its 512-column tensor-memory
-// allocation then always succeeds at once).
+// Both operands of the MMA are the same rows of X in the K-major core-matrix layout (element
+// (n, k) of a 32-row chunk at byte (n div 8) 512 + (k div 8) 128 + (n mod 8) 16 + (k mod 8) 2, n the
+// column of X and k the row in the chunk), so column c of a chunk starts at byte 64 c.  A tile is
+// 128 rows of G_b (MMA M = 128, A = 128 columns of the chunk) times up to 256 columns (B).  Each CTA
+// keeps its tiles in tensor memory for a range of at most 8192 rows and writes them as an FP32
+// partial; k_gram_reduce adds the ranges' partials in a fixed order in FP64 (deterministic) from
+// the upper triangle and mirrors it, so G_b is exactly symmetric.
+//
+// Two ways in:
+//  - k_gram_f32 (X FP32 with 16-byte aligned rows and d a multiple of 4): a cluster of 1-3 CTAs
+//    per range; each CTA copies its segment of the columns of 32 rows at a time into shared memory
+//    (2-D TMA boxes of 32 rows x 128 columns; zeros past the edges), eight converter warps round them to BF16 into
+//    the chunk layout (one column of 8 rows per thread and step: 8 conflict-free 4-byte reads, one
+//    16-byte write), warp 1 issues the MMAs of the CTA's tiles and sends the rounded segment to the
+//    cluster's hub by a bulk copy between shared memories.  X is read from DRAM and rounded once,
+//    the tiles cover the upper triangle with equal MMA work per CTA (roles below).
+//  - k_gram_tc (any other X): X is first packed to BF16 chunks by the Gaussian sketch's packer,
+//    then streamed by bulk copies; the CTA of column block i0 forms rows i0 .. i0 + 127 times all
+//    columns (the CTAs of a range then run at one rate and share the chunks through L2).
+// Every mbarrier wait gives up after 2 s (ST_TIMEOUT, NaN output); copies in flight are awaited
+// and tensor memory is freed on that path too.  Shared memory is sized so that one CTA runs per SM
+// (its tensor-memory allocation then always succeeds at once).
 #include "tc_common.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cuda_bf16.h>
+
+#include <initializer_list>
 
 namespace slse {
 namespace {
@@ -27,6 +44,38 @@ constexpr int kGSBO = kGK * 16;          // bytes between 8-column groups of a c
 constexpr int kGThreads = 128;           // warp 0: copies, warp 1: MMAs, warps 0-3: epilogue
 constexpr int kGMaxStages = 6;
 constexpr int64_t kGMaxRangeChunks = 256;
+constexpr int kFConv = 8;                        // converter warps of k_gram_f32
+constexpr int kFThreads = 64 + 32 * kFConv;      // + copy warp + MMA warp
+
+// MMAs of one 32-row chunk at shared address xb: A = columns i0 .. i0 + 127, B = columns
+// 0 .. W - 1 (W a multiple of 128) in pieces of <= 256 columns; accumulate unless this is the
+// range's first chunk.
+__device__ __forceinline__ void gram_chunk_mma(uint32_t tmem, uint32_t xb, int i0, int W, bool first) {
+  const uint32_t ab = xb + (uint32_t)i0 * 64u;
+#pragma unroll
+  for (int ks = 0; ks < kGK / 16; ++ks) {
+    // K step ks covers core-matrix columns 2 ks, 2 ks + 1 (128 bytes apart)
+    const uint64_t ad = umma_desc(ab + ks * 256, 128, kGSBO);
+    const uint32_t acc = (!first || ks > 0) ? 1u : 0u;
+    for (int c = 0; c < W; c += 256) {
+      const int n = W - c < 256 ? W - c : 256;
+      umma_bf16(tmem + (uint32_t)c, ad, umma_desc(xb + (uint32_t)c * 64u + ks * 256, 128, kGSBO),
+                umma_idesc_bf16(kGM, n), acc);
+    }
+  }
+}
+
+// the accumulator of rows i0 + 32 q + lane (q = warp mod 4), columns c (relative to i0) of
+// c0, c0 + cstep, ... in 32-column pieces, to the range's partial
+__device__ __forceinline__ void gram_store(uint32_t tmem, float *part_row, int W, int q, int c0, int cstep) {
+  for (int c = c0; c < W; c += cstep) {
+    uint32_t v[32];
+    tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
+#pragma unroll
+    for (int j = 0; j < 32; j += 4)
+      *reinterpret_cast<uint4 *>(part_row + c + j) = make_uint4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+  }
+}
 
 struct GramArgs {
   const uint8_t *xt;   // nchunk packed chunks of ncp * 64 bytes
@@ -73,7 +122,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gram_tc(const GramArgs a) {
   const int64_t c0 = (int64_t)blockIdx.y * a.cps;
   const int64_t c1 = c0 + a.cps < a.nchunk ? c0 + a.cps : a.nchunk;
   const int nk = (int)(c1 - c0);
-  const int m0 = (int)blockIdx.x * kGM;
+  const int i0 = (int)blockIdx.x * kGM;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -96,43 +145,24 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gram_tc(const GramArgs a) {
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const int n0 = a.ncp < 256 ? a.ncp : 256;
-      const uint32_t id0 = umma_idesc_bf16(kGM, n0);
-      const uint32_t id1 = a.ncp > 256 ? umma_idesc_bf16(kGM, a.ncp - 256) : 0u;
       int s = 0;
       uint32_t ph = 0;
       for (int k = 0; k < nk; ++k) {
         if (!mbar_wait(&full[s], ph, abort_f, a.status)) break;
         tc_fence_after();
-        const uint32_t xb = smem_u32(sX + (size_t)s * bC);
-        const uint32_t ab = xb + (uint32_t)m0 * 64u;  // columns m0 .. m0 + 127 of the chunk
-#pragma unroll
-        for (int ks = 0; ks < kGK / 16; ++ks) {
-          // K step ks covers core-matrix columns 2 ks, 2 ks + 1 (128 bytes apart)
-          const uint64_t ad = umma_desc(ab + ks * 256, 128, kGSBO);
-          const uint32_t acc = (k > 0 || ks > 0) ? 1u : 0u;
-          umma_bf16(tmem, ad, umma_desc(xb + ks * 256, 128, kGSBO), id0, acc);
-          if (a.ncp > 256) umma_bf16(tmem + 256, ad, umma_desc(xb + 32 * kGSBO + ks * 256, 128, kGSBO), id1, acc);
-        }
+        gram_chunk_mma(tmem, smem_u32(sX + (size_t)s * bC), i0, a.ncp, k == 0);
         umma_commit(&empty[s]);
         if (++s == S) { s = 0; ph ^= 1u; }
       }
       umma_commit(accum);  // arrives once every MMA issued above has completed
     }
   }
-  // epilogue: TMEM lanes 32 warp .. 32 warp + 31 hold rows m0 + 32 warp + lane of G_b
+  // epilogue: TMEM lanes 32 warp .. 32 warp + 31 hold rows i0 + 32 warp + lane of G_b
   {
     const bool ok = mbar_wait(accum, 0u, abort_f, a.status);
     tc_fence_after();
-    if (__all_sync(0xFFFFFFFFu, ok && !*abort_f) && nk > 0) {
-      float *dst = a.part + ((int64_t)blockIdx.y * a.ncp + m0 + 32 * warp + lane) * a.ncp;
-      for (int c = 0; c < a.ncp; c += 32) {
-        uint32_t v[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, v);
-#pragma unroll
-        for (int j = 0; j < 32; j += 4) *reinterpret_cast<uint4 *>(dst + c + j) = make_uint4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-      }
-    }
+    if (__all_sync(0xFFFFFFFFu, ok && !*abort_f) && nk > 0)
+      gram_store(tmem, a.part + ((int64_t)blockIdx.y * a.ncp + i0 + 32 * warp + lane) * a.ncp, a.ncp, warp, 0, 32);
     tc_fence_before();
   }
   __syncthreads();
@@ -143,24 +173,367 @@ __global__ void __launch_bounds__(kGThreads, 1) k_gram_tc(const GramArgs a) {
   }
 }
 
-// G[i, j] = sum over ranges of part[range][i][j] in FP64 (fixed order), i, j < d; an empty range
-// wrote no partial and is skipped; NaN after a timeout.
-__global__ void k_gram_reduce(const float *__restrict__ part, int splits, int64_t nchunk, int64_t cps, int ncp, int d,
+// Roles of the CTAs of one cluster of k_gram_f32 (Q = 1, 2 or 3 CTAs, one range of rows).  CTA r
+// reads and rounds the columns lo .. hi - 1 of X (its segment; empty for the hub of d > 384) and
+// forms its tiles: tile t is rows 128 a_blk .. 128 a_blk + 127 of G_b times columns b_lo .. b_lo +
+// n - 1 (n <= 256, one MMA per K step) in tensor-memory columns toff ...  Rank 0 (the hub) receives
+// every other CTA's rounded segment into its own chunk buffer (a bulk copy between the CTAs' shared
+// memories) and forms the tiles that need columns of several segments.  The tiles of all ranks
+// cover the upper triangle of G_b (i <= j) once, with equal MMA work per CTA:
+//   ncp 128: r0 [0,128)   : (0, 0, 128)
+//   ncp 256: r0 [0,256)   : (0, 0, 256) (1, 128, 128)
+//   ncp 384: r0 [0,128)   : (0, 0, 256) (0, 256, 128)          r1 [128,384): (1, 128, 256) (2, 256, 128)
+//   ncp 512: r0 (none)    : (0, 256, 256) (1, 256, 256)
+//            r1 [0,256)   : (0, 0, 256) (1, 0, 256)            r2 [256,512): (2, 256, 256) (3, 256, 256)
+// so each column of X is read from DRAM and rounded once, and no CTA waits on a wider one.
+struct GramRole {
+  int lo, hi;  // segment
+  int ntile;
+  int a_blk[2], b_lo[2], n[2], toff[2];
+};
+
+struct GramF32Args {
+  CUtensorMap tmap;     // X as (d, N) FP32, boxes of 128 columns x 32 rows
+  int64_t N;
+  int d;
+  float *part;          // [splits][ncp][ncp], upper triangle
+  unsigned *status;
+  int64_t nstage, cps;  // 32-row stages of X, stages per range
+  int ncp, tmem_cols, Q;
+  int in_bytes;         // bytes the hub receives per stage
+  int s3, nb;           // FP32 stages, chunk buffers (the hub's of the full width, a peer's of its segment)
+  int o_bar;            // byte offset of the barriers (the same in every CTA of the cluster)
+  int o16[3];           // byte offset of each role's chunk buffers
+  GramRole role[3];
+};
+
+constexpr int kFMaxB = 8;   // most stages or buffers of any kind
+
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t local, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cl_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cl_addr) : "memory");
+}
+// shared -> peer shared bulk copy completing on the peer's mbarrier (16-byte aligned, size a
+// multiple of 16)
+__device__ __forceinline__ void bulk_s2c(uint32_t cl_dst, const void *src, uint32_t bytes, uint32_t cl_bar) {
+  asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   cl_dst),
+               "r"(smem_u32(src)), "r"(bytes), "r"(cl_bar)
+               : "memory");
+}
+
+// 2-D tiled TMA load of the box at (x, y) of the tensor map into shared memory, completing on an
+// mbarrier (x a multiple of 4 for FP32; boxes past the edge of X read zeros)
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared memory of a CTA: s3 FP32 stages of its segment (32 rows x sw columns, in row-major panels
+// of 128 columns), then its nb chunk buffers (the hub's of the full width, columns at their own
+// offsets; a peer's of its segment, columns relative to lo), then the barriers at o_bar.
+// Per stage k the hub's buffer k mod nb is released (its incoming bytes expected, hubfree signalled
+// to the peers) once the hub's MMAs of stage k - nb have completed; a peer rounds stage k into its
+// buffer k mod nb once its own MMAs of stage k - nb have completed and the hub has released stage k
+// (which implies that the peer's copy of stage k - nb, out of the same buffer, has landed), then
+// copies the segment into the hub's buffer and issues its own tiles.  (A separate signal of each
+// landed copy, so that the hub could hold more buffers than the peers, measured slower.)
+__global__ void __launch_bounds__(kFThreads, 1) k_gram_f32(const __grid_constant__ GramF32Args a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int rank = (int)blockIdx.x;  // cluster (Q, 1, 1) over grid (Q, ranges)
+  const bool hub = rank == 0;
+  const GramRole ro = a.role[rank];
+  const int sw = ro.hi - ro.lo;                      // segment width: 0, 128 or 256
+  const int ncol = sw > 0 ? (ro.hi < a.d ? ro.hi : a.d) - ro.lo : 0;  // columns of X inside the segment
+  const int cbase = hub ? 0 : ro.lo;                 // column at byte 0 of this CTA's chunk buffers
+  const int nb = a.nb;
+  const uint32_t b32 = (uint32_t)sw * (kGK * 4u);    // one FP32 stage
+  const uint32_t b16 = (uint32_t)(hub ? a.ncp : sw) * (kGK * 2u);  // one chunk buffer
+  float *s32 = reinterpret_cast<float *>(sm);
+  uint8_t *s16 = sm + a.o16[rank];
+  uint64_t *full32 = reinterpret_cast<uint64_t *>(sm + a.o_bar);
+  uint64_t *empty32 = full32 + kFMaxB;
+  uint64_t *fullb = empty32 + kFMaxB;
+  uint64_t *emptyb = fullb + kFMaxB;
+  uint64_t *hubfree = emptyb + kFMaxB;  // peers: the hub released its buffer for a stage
+  uint64_t *accum = hubfree + kFMaxB;
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(accum + 1);
+  volatile int *abort_f = reinterpret_cast<volatile int *>(tslot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < a.s3; ++s) {
+      mbar_init(&full32[s], 1);
+      mbar_init(&empty32[s], kFConv);
+    }
+    for (int b = 0; b < nb; ++b) {
+      mbar_init(&fullb[b], hub ? 1 + (sw > 0 ? kFConv : 0) : kFConv);
+      mbar_init(&emptyb[b], 1);
+      mbar_init(&hubfree[b], 1);
+    }
+    mbar_init(accum, 1);
+    *abort_f = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(a.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  // the peers' barriers are initialised before any remote arrive or copy reaches them
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const int64_t st0 = (int64_t)blockIdx.y * a.cps;
+  const int64_t st1 = st0 + a.cps < a.nstage ? st0 + a.cps : a.nstage;
+  const int nk = (int)(st1 - st0);
+  const int64_t row0 = st0 * kGK;
+  auto rows_of = [&](int k) -> int {
+    const int64_t r = a.N - (row0 + (int64_t)k * kGK);
+    return r < kGK ? (int)r : kGK;
+  };
+  auto tiles_mma = [&](uint32_t xb, bool first) {
+#pragma unroll
+    for (int ks = 0; ks < kGK / 16; ++ks) {
+      const uint32_t acc = (!first || ks > 0) ? 1u : 0u;
+      for (int t = 0; t < ro.ntile; ++t) {
+        const uint64_t ad = umma_desc(xb + (uint32_t)(kGM * ro.a_blk[t] - cbase) * 64u + ks * 256, 128, kGSBO);
+        const uint64_t bd = umma_desc(xb + (uint32_t)(ro.b_lo[t] - cbase) * 64u + ks * 256, 128, kGSBO);
+        umma_bf16(tmem + (uint32_t)ro.toff[t], ad, bd, umma_idesc_bf16(kGM, ro.n[t]), acc);
+      }
+    }
+  };
+
+  if (warp == 0) {
+    // copies of the segment: one TMA box (32 rows x 128 columns, 16 KB) per 128 columns and stage
+    if (lane == 0 && ncol > 0) {
+      const int npan = sw / 128;
+      int issued = 0;
+      for (int k = 0; k < nk; ++k) {
+        const int s = k % a.s3;
+        if (!mbar_wait(&empty32[s], ((uint32_t)(k / a.s3) & 1u) ^ 1u, abort_f, a.status)) break;
+        mbar_arrive_expect_tx(&full32[s], b32);
+        for (int pn = 0; pn < npan; ++pn)
+          tma_load_2d(s32 + (size_t)s * (b32 / 4) + pn * (kGK * 128), &a.tmap, ro.lo + 128 * pn,
+                      (int)(row0 + (int64_t)k * kGK), &full32[s]);
+        issued = k + 1;
+      }
+      // copies in flight land before the CTA exits
+      const int first = issued > a.s3 ? issued - a.s3 : 0;
+      for (int k = first; k < issued; ++k) {
+        volatile int never = 0;
+        mbar_wait(&full32[k % a.s3], (uint32_t)(k / a.s3) & 1u, &never, a.status);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      if (hub) {
+        auto release = [&](int j) {
+          const int b = j % nb;
+          mbar_arrive_expect_tx(&fullb[b], (uint32_t)a.in_bytes);
+          for (int r = 1; r < a.Q; ++r) mbar_arrive_remote(cluster_addr(smem_u32(&hubfree[b]), r));
+        };
+        int released = nk < nb ? nk : nb, consumed = 0;
+        for (int j = 0; j < released; ++j) release(j);
+        for (int k = 0; k < nk; ++k) {
+          const int b = k % nb;
+          if (!mbar_wait(&fullb[b], (uint32_t)(k / nb) & 1u, abort_f, a.status)) break;
+          consumed = k + 1;
+          tc_fence_after();
+          tiles_mma(smem_u32(s16 + (size_t)b * b16), k == 0);
+          umma_commit(&emptyb[b]);
+          const int j = k - 1 + nb;  // the stage that reuses stage k - 1's buffer
+          if (k >= 1 && j < nk) {
+            if (!mbar_wait(&emptyb[(k - 1) % nb], (uint32_t)((k - 1) / nb) & 1u, abort_f, a.status)) break;
+            release(j);
+            released = j + 1;
+          }
+        }
+        umma_commit(accum);  // arrives once every MMA issued above has completed
+        // every copy into this CTA has landed before it exits: after a failure, the stages released
+        // but not consumed (the latest phase of their buffers) are awaited, each wait bounded
+        for (int j = consumed; j < released; ++j) {
+          volatile int never = 0;
+          mbar_wait(&fullb[j % nb], (uint32_t)(j / nb) & 1u, &never, a.status);
+        }
+      } else {
+        for (int k = 0; k < nk; ++k) {
+          const int b = k % nb;
+          if (!mbar_wait(&fullb[b], (uint32_t)(k / nb) & 1u, abort_f, a.status)) break;
+          tc_fence_after();
+          // the rounded segment to the hub's buffer b (released for this stage: the converters
+          // waited for that), then this CTA's own tiles
+          uint8_t *seg = s16 + (size_t)b * b16;
+          uint8_t *hub_seg = sm + a.o16[0] + (size_t)b * ((size_t)a.ncp * kGK * 2) + (size_t)ro.lo * 64;
+          bulk_s2c(cluster_addr(smem_u32(hub_seg), 0), seg, b16, cluster_addr(smem_u32(&fullb[b]), 0));
+          tiles_mma(smem_u32(seg), k == 0);
+          umma_commit(&emptyb[b]);
+        }
+        umma_commit(accum);
+      }
+    }
+  } else if (sw > 0) {
+    // converters: item (n, k8) = column lo + n, rows 8 k8 .. 8 k8 + 7 of the stage; consecutive
+    // threads take consecutive columns
+    const int ct = threadIdx.x - 64;
+    const int lsw = sw == 256 ? 8 : 7;
+    for (int k = 0; k < nk; ++k) {
+      const int s = k % a.s3, b = k % nb;
+      const uint32_t pb = (uint32_t)(k / nb) & 1u;
+      bool ok = mbar_wait(&full32[s], (uint32_t)(k / a.s3) & 1u, abort_f, a.status);
+      ok = ok && mbar_wait(&emptyb[b], pb ^ 1u, abort_f, a.status);
+      if (!hub) ok = ok && mbar_wait(&hubfree[b], pb, abort_f, a.status);
+      if (!__all_sync(0xFFFFFFFFu, ok)) break;
+      const int nr = rows_of(k);
+      const float *src = s32 + (size_t)s * (b32 / 4);
+      uint8_t *dst = s16 + (size_t)b * b16 + (size_t)(ro.lo - cbase) * 64;
+      for (int it = ct; it < sw * (kGK / 8); it += 32 * kFConv) {
+        const int n = it & (sw - 1), k8 = it >> lsw;
+        const int pan = (n >> 7) * (kGK * 128) + (n & 127);  // panel of 128 columns, row-major
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int r = 8 * k8 + 2 * q;
+          const float f0 = (n < ncol && r < nr) ? src[pan + r * 128] : 0.f;
+          const float f1 = (n < ncol && r + 1 < nr) ? src[pan + (r + 1) * 128] : 0.f;
+          const __nv_bfloat162 h = __floats2bfloat162_rn(f0, f1);  // row r in the low half
+          w[q] = *reinterpret_cast<const uint32_t *>(&h);
+        }
+        *reinterpret_cast<uint4 *>(dst + (n >> 3) * kGSBO + k8 * 128 + (n & 7) * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+      fence_proxy_async_smem();  // the MMAs and the copy to the hub (async proxy) read these writes
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&fullb[b]);
+        mbar_arrive(&empty32[s]);
+      }
+    }
+  }
+  // epilogue (converter warps): TMEM lanes 32 q .. 32 q + 31, q = warp mod 4, hold rows
+  // 128 a_blk + 32 q + lane of tile t; the two warps of a lane quarter take alternate 32-column
+  // pieces
+  if (warp >= 2) {
+    const bool ok = mbar_wait(accum, 0u, abort_f, a.status);
+    tc_fence_after();
+    const int q = warp & 3;
+    if (__all_sync(0xFFFFFFFFu, ok && !*abort_f) && nk > 0) {
+      for (int t = 0; t < ro.ntile; ++t) {
+        float *row = a.part + ((int64_t)blockIdx.y * a.ncp + kGM * ro.a_blk[t] + 32 * q + lane) * a.ncp + ro.b_lo[t];
+        gram_store(tmem + (uint32_t)ro.toff[t], row, ro.n[t], q, 32 * ((warp - 2) >> 2), 64);
+      }
+    }
+    tc_fence_before();
+  }
+  __syncthreads();
+  if (warp == 0) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+  }
+  // no CTA leaves while a peer may still signal it or copy into it
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// G[i, j] = G[j, i] = sum over ranges of part[range][i][j] (i <= j, the upper triangle) in FP64,
+// fixed order; an empty range wrote no partial and is skipped; NaN after a timeout.  Block row
+// blockIdx.y = i, threads over j >= i.
+__global__ void k_gram_reduce(const float *__restrict__ part, int splits, int64_t nunit, int64_t cps, int ncp, int d,
                               const unsigned *status, double *G) {
   const bool bad = (*(volatile const unsigned *)status & ST_TIMEOUT) != 0;
-  const int64_t total = (int64_t)d * d;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(idx / d), j = (int)(idx - (int64_t)i * d);
-    double v = 0.0;
-    for (int s = 0; s < splits; ++s)
-      if ((int64_t)s * cps < nchunk) v += (double)part[((int64_t)s * ncp + i) * ncp + j];
-    G[idx] = bad ? __longlong_as_double(0x7FF8000000000000ll) : v;
-  }
+  const int i = blockIdx.y;
+  const int j = i + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (j >= d) return;
+  double v = 0.0;
+  for (int s = 0; s < splits; ++s)
+    if ((int64_t)s * cps < nunit) v += (double)part[((int64_t)s * ncp + i) * ncp + j];
+  if (bad) v = __longlong_as_double(0x7FF8000000000000ll);
+  G[(int64_t)i * d + j] = v;
+  G[(int64_t)j * d + i] = v;
 }
 
 int64_t gcdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 size_t gal256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// ranges of at most kGMaxRangeChunks 32-row units (8192 rows): the FP32 sum of a range in tensor
+// memory then stays within ~2e-5 of sum |x_i x_j| (measured 9e-6 at 3400 rows); at least one
+// range per SM and column block
+void gram_split(int64_t nunit, int mt, int nsm, int64_t &cps, int &splits) {
+  int64_t sp = (nsm > 0 ? nsm : 152) / mt;
+  if (sp < gcdiv(nunit, kGMaxRangeChunks)) sp = gcdiv(nunit, kGMaxRangeChunks);
+  if (sp < 1) sp = 1;
+  if (sp > nunit) sp = nunit;
+  cps = gcdiv(nunit, sp);
+  splits = (int)gcdiv(nunit, cps);
+}
+
+// the roles of the cluster's CTAs for ncp columns (the table above k_gram_f32); returns Q
+int gram_roles(int ncp, GramRole *ro, int *in_bytes) {
+  auto set = [](GramRole &r, int lo, int hi, std::initializer_list<int> t) {
+    r = GramRole{};
+    r.lo = lo;
+    r.hi = hi;
+    const int *v = t.begin();
+    r.ntile = (int)t.size() / 3;
+    int off = 0;
+    for (int k = 0; k < r.ntile; ++k) {
+      r.a_blk[k] = v[3 * k];
+      r.b_lo[k] = v[3 * k + 1];
+      r.n[k] = v[3 * k + 2];
+      r.toff[k] = off;
+      off += r.n[k];
+    }
+  };
+  int Q = 1;
+  if (ncp == 128) {
+    set(ro[0], 0, 128, {0, 0, 128});
+  } else if (ncp == 256) {
+    set(ro[0], 0, 256, {0, 0, 256, 1, 128, 128});
+  } else if (ncp == 384) {
+    Q = 2;
+    set(ro[0], 0, 128, {0, 0, 256, 0, 256, 128});
+    set(ro[1], 128, 384, {1, 128, 256, 2, 256, 128});
+  } else {
+    Q = 3;
+    set(ro[0], 0, 0, {0, 256, 256, 1, 256, 256});
+    set(ro[1], 0, 256, {0, 0, 256, 1, 0, 256});
+    set(ro[2], 256, 512, {2, 256, 256, 3, 256, 256});
+  }
+  int in = 0;
+  for (int r = 1; r < Q; ++r) in += (ro[r].hi - ro[r].lo) * 64;
+  if (in_bytes) *in_bytes = in;
+  return Q;
+}
+
+// shared-memory layout of k_gram_f32 (see there): 3 FP32 stages and 3 chunk buffers (measured
+// fastest: 4 stages and up to 6 hub buffers were slower); the barriers at one offset for all
+// roles; one CTA per SM
+void gram_f32_layout(int ncp, const GramRole *ro, int Q, GramF32Args &a, size_t &smem) {
+  a.s3 = 3;
+  a.nb = 3;
+  int top = 0;
+  for (int r = 0; r < Q; ++r) {
+    const int sw = ro[r].hi - ro[r].lo;
+    a.o16[r] = a.s3 * sw * kGK * 4;
+    const int end = a.o16[r] + (r == 0 ? ncp : sw) * a.nb * kGK * 2;
+    if (end > top) top = end;
+  }
+  a.o_bar = (top + 7) & ~7;
+  smem = (size_t)a.o_bar + (5 * kFMaxB + 1) * 8 + 8 + 1024;
+  if (smem < 233472 / 2 + 1) smem = 233472 / 2 + 1;
+}
 
 }  // namespace
 
@@ -172,46 +545,110 @@ GramPlan gram_plan(int64_t N, int d, int nsm) {
   int tc = 32;
   while (tc < p.ncp) tc <<= 1;
   p.tmem_cols = tc;
+  const int mt = p.ncp / kGM;
+  // packed path
   const size_t bC = (size_t)p.ncp * kGK * 2;
   int S = (int)((232448 - 2048) / bC);
   if (S > kGMaxStages) S = kGMaxStages;
   p.stages = S;
-  // one CTA per SM: its tensor-memory allocation (up to 512 columns) never waits
   size_t smem = (size_t)S * bC + (2 * S + 1) * 8 + 8 + 1024;
-  if (smem < 233472 / 2 + 1) smem = 233472 / 2 + 1;
+  if (smem < 233472 / 2 + 1) smem = 233472 / 2 + 1;  // one CTA per SM
   p.smem = smem;
   p.nchunk = gcdiv(N, 2 * kGK) * 2;  // the packer writes chunks in pairs (zero rows past N)
-  // ranges of at most kGMaxRangeChunks chunks (8192 rows): the FP32 sum of a range in tensor memory
-  // then stays within ~2e-5 of sum |x_i x_j| (measured 9e-6 at 3400 rows); at least one range per
-  // SM and column block
-  const int mt = p.ncp / kGM;
-  int64_t splits = (nsm > 0 ? nsm : 152) / mt;
-  if (splits < gcdiv(p.nchunk, kGMaxRangeChunks)) splits = gcdiv(p.nchunk, kGMaxRangeChunks);
-  if (splits < 1) splits = 1;
-  if (splits > p.nchunk) splits = p.nchunk;
-  p.cps = gcdiv(p.nchunk, splits);
-  p.splits = (int)gcdiv(p.nchunk, p.cps);
+  gram_split(p.nchunk, mt, nsm, p.cps, p.splits);
+  // FP32 path: one cluster of Q CTAs per range
+  GramRole ro[3];
+  p.q_f = gram_roles(p.ncp, ro, nullptr);
+  p.nstage = gcdiv(N, kGK);
+  gram_split(p.nstage, p.q_f, nsm, p.cps_f, p.splits_f);
+  GramF32Args lay{};
+  gram_f32_layout(p.ncp, ro, p.q_f, lay, p.smem_f);
+  double ent_f = 0.0;  // accumulator entries of one range
+  for (int r = 0; r < p.q_f; ++r)
+    for (int t = 0; t < ro[r].ntile; ++t) ent_f += (double)kGM * ro[r].n[t];
+  const double ent_p = (double)p.ncp * p.ncp;
+  p.flops_f32 = 2.0 * (double)p.nstage * kGK * ent_f;
+  p.flops_packed = 2.0 * (double)p.nchunk * kGK * ent_p;
+  p.bytes_f32 = (double)N * d * 4.0 + 2.0 * (double)p.splits_f * ent_f * 4.0;
+  p.bytes_packed = (double)N * d * 4.0 + 2.0 * (double)p.nchunk * kGK * p.ncp * 2.0 + 2.0 * (double)p.splits * ent_p * 4.0;
+  const int sp = p.splits > p.splits_f ? p.splits : p.splits_f;
   p.o_xt = 0;
   p.o_part = gal256((size_t)p.nchunk * bC);
-  p.total = p.o_part + gal256((size_t)p.splits * p.ncp * p.ncp * 4);
+  p.total = p.o_part + gal256((size_t)sp * p.ncp * p.ncp * 4);
   return p;
+}
+
+namespace {
+// X as a 2-D tensor (d columns, N rows, row stride ldx floats) with 128 x 32 boxes; false when the
+// driver's encoder is unavailable or refuses
+bool gram_tensor_map(CUtensorMap *m, const float *X, int64_t ldx, int64_t N, int d) {
+  static PFN_cuTensorMapEncodeTiled_v12000 enc = [] {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+    cudaGetLastError();
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)N};
+  const cuuint64_t strides[1] = {(cuuint64_t)ldx * 4u};
+  const cuuint32_t box[2] = {128u, (cuuint32_t)kGK};
+  const cuuint32_t estr[2] = {1u, 1u};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(X), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+}  // namespace
+
+bool gram_fp32_path(const GramPlan &p, const float *X, int64_t ldx) {
+  return p.d % 4 == 0 && ldx % 4 == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0;
 }
 
 cudaError_t launch_gram(const GramPlan &p, const float *X, int64_t ldx, double *G, unsigned *status, void *ws,
                         cudaStream_t s) {
   uint8_t *base = static_cast<uint8_t *>(ws);
-  uint8_t *xt = base + p.o_xt;
   float *part = reinterpret_cast<float *>(base + p.o_part);
-  cudaError_t e = launch_pack_bf16(X, ldx, p.N, p.d, p.ncp, xt, s);
-  if (e != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem))) return e;
-  GramArgs a{};
-  a.xt = xt; a.part = part; a.status = status; a.nchunk = p.nchunk; a.cps = p.cps; a.ncp = p.ncp;
-  a.tmem_cols = p.tmem_cols; a.stages = p.stages;
-  k_gram_tc<<<dim3((unsigned)(p.ncp / kGM), (unsigned)p.splits), kGThreads, p.smem, s>>>(a);
+  const int mt = p.ncp / kGM;
+  cudaError_t e;
+  int splits;
+  int64_t nunit, cps;
+  GramF32Args a{};
+  if (gram_fp32_path(p, X, ldx) && gram_tensor_map(&a.tmap, X, ldx, p.N, p.d)) {
+    if ((e = cudaFuncSetAttribute(k_gram_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem_f))) return e;
+    a.N = p.N; a.d = p.d; a.part = part; a.status = status;
+    a.nstage = p.nstage; a.cps = p.cps_f; a.ncp = p.ncp; a.tmem_cols = p.tmem_cols;
+    a.Q = gram_roles(p.ncp, a.role, &a.in_bytes);
+    size_t smem_f = 0;
+    gram_f32_layout(p.ncp, a.role, a.Q, a, smem_f);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)a.Q, (unsigned)p.splits_f);
+    cfg.blockDim = dim3(kFThreads);
+    cfg.dynamicSmemBytes = p.smem_f;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)a.Q;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if ((e = cudaLaunchKernelEx(&cfg, k_gram_f32, a))) return e;
+    splits = p.splits_f; nunit = p.nstage; cps = p.cps_f;
+  } else {
+    uint8_t *xt = base + p.o_xt;
+    if ((e = launch_pack_bf16(X, ldx, p.N, p.d, p.ncp, xt, s))) return e;
+    if ((e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem))) return e;
+    GramArgs a{};
+    a.xt = xt; a.part = part; a.status = status; a.nchunk = p.nchunk; a.cps = p.cps; a.ncp = p.ncp;
+    a.tmem_cols = p.tmem_cols; a.stages = p.stages;
+    k_gram_tc<<<dim3((unsigned)mt, (unsigned)p.splits), kGThreads, p.smem, s>>>(a);
+    splits = p.splits; nunit = p.nchunk; cps = p.cps;
+  }
   if ((e = cudaGetLastError())) return e;
-  const int64_t tot = (int64_t)p.d * p.d;
-  k_gram_reduce<<<(unsigned)gcdiv(tot, 256), 256, 0, s>>>(part, p.splits, p.nchunk, p.cps, p.ncp, p.d, status, G);
+  k_gram_reduce<<<dim3((unsigned)gcdiv(p.d, 256), (unsigned)p.d), 256, 0, s>>>(part, splits, nunit, cps, p.ncp, p.d,
+                                                                               status, G);
   return cudaGetLastError();
 }
 

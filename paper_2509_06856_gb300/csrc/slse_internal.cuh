@@ -180,8 +180,18 @@ struct GramPlan {
   int d, ncp, tmem_cols, stages, splits;
   int64_t nchunk, cps;
   size_t smem, o_xt, o_part, total;
+  // FP32 path (rows read and rounded on chip): 32-row stages, stages per range, ranges, shared memory
+  int64_t nstage, cps_f;
+  int splits_f, q_f;  // ranges, CTAs per range (a cluster)
+  size_t smem_f;
+  // tensor-core work (upper block triangle, padded rows) and DRAM bytes of each path: X read,
+  // (packed path) the BF16 copy written and read, the partials written and read
+  double flops_f32, flops_packed, bytes_f32, bytes_packed;
 };
 GramPlan gram_plan(int64_t N, int d, int nsm);
+// whether launch_gram reads X directly (d and ldx multiples of 4, X 16-byte aligned) instead of
+// packing it first
+bool gram_fp32_path(const GramPlan &p, const float *X, int64_t ldx);
 // status: ST_TIMEOUT is raised there when a bounded wait gave up (G is then NaN)
 cudaError_t launch_gram(const GramPlan &p, const float *X, int64_t ldx, double *G, unsigned *status, void *ws,
                         cudaStream_t s);

@@ -1,7 +1,9 @@
 """The Gram matrix of the BF16-rounded data (slse_gram), the Hessian term the mixed 2nd stage's
 correction form uses between exact passes: against the same product formed on the CPU in FP64
 from the BF16 rounding of X (round to nearest even, PyTorch's CPU cast), at sizes with a ragged
-last chunk of rows, d below, at and between multiples of the 128-column tiles."""
+last chunk of rows, d below, at and between multiples of the 128-column tiles.  X with d and the
+row stride multiples of 4 and 16-byte aligned rows is read directly (rounded on chip); any other X
+(d = 129, a view one column in) is packed to BF16 first: both ways are covered."""
 import numpy as np
 import pytest
 
@@ -25,7 +27,24 @@ def test_gram_matches_cpu_product_of_bf16_rows(N, d):
     err = np.abs(G - ref) / scale
     print(f"N={N} d={d}: max error / sum|x x| = {err.max():.2e}")
     assert np.all(err <= 1e-4)
-    assert np.array_equal(G, G.T) or np.max(np.abs(G - G.T) / scale) <= 1e-6
+    assert np.array_equal(G, G.T)  # the upper triangle is formed and mirrored
+
+
+@pytest.mark.parametrize("N,d,off", [(30011, 200, 4), (30011, 200, 1), (20000, 128, 4)])
+def test_gram_of_row_strided_views(N, d, off):
+    """X a view of a wider buffer (row stride d + 4): starting 4 columns in keeps the rows 16-byte
+    aligned (direct path), 1 column in does not (packed path)."""
+    torch = torch_cuda()
+    import paper_2509_06856_gb300 as slse
+    buf = workloads.cfg3(N=N, d=d + 4, seed=13)["X"]
+    Xv = dev(buf)[:, off:off + d]
+    assert Xv.stride(0) == d + 4
+    G = host(slse.gram(Xv))
+    Xb = torch.from_numpy(np.ascontiguousarray(buf[:, off:off + d])).bfloat16().double().numpy()
+    err = np.abs(G - Xb.T @ Xb) / (np.abs(Xb).T @ np.abs(Xb))
+    print(f"N={N} d={d} offset {off}: max error / sum|x x| = {err.max():.2e}")
+    assert np.all(err <= 1e-4)
+    assert np.array_equal(G, G.T)
 
 
 def test_gram_is_deterministic():
