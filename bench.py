@@ -476,13 +476,13 @@ def run_ours(args, rank, ws, local_rank):
     ms_per_step = reduce_max(ms_total / args.steps, ws)
     launches = int(reduce_sum(sum(r.report["kernels"] for r in results), ws))
 
-    # dominant kernel: 2nd-stage gradient vs the two sketch passes (summed CUDA-event times)
+    # dominant kernel: the largest of the main path's kernels by summed CUDA-event time (the 2nd-stage
+    # passes over X, the two sketch passes); the Gram build of the correction form runs on a second
+    # stream beside the main path (its time overlaps other kernels) and is listed, not chosen
     rep = results[-1].report
-    # 2nd stage: the passes over X (the exact passes of the correction form) and the packing of the
-    # BF16 copy with its Gram matrix (one launch group; its tensor rate is reported apart below)
     k_times = {
         "grad_stage2": (rep["ms_grad2"], rep["n_grad2"], rep["bytes_grad2"]),
-        "gram_bf16": (rep["ms_gram"], 1 if rep["ms_gram"] > 0 else 0, rep["bytes_gram"]),
+        "gram": (rep["ms_gram"], 1 if rep["ms_gram"] > 0 else 0, rep["bytes_gram"]),
         "srht_pass1": (rep["ms_srht_pass1"], 1, N * (d + 1) * 4.0 + N * (d + 1) * 2.0),
         "srht_pass2": (rep["ms_srht_pass2"], 1, N * (d + 1) * 2.0 + (sched.m[-1] + sched.r) * (d + 1) * 2.0),
     }
@@ -492,11 +492,10 @@ def run_ours(args, rank, ws, local_rank):
         if ms > 0 and n > 0:
             kernels_gbs[k] = {"ms_per_launch": ms / n, "launches": n, "alg_bytes_per_launch": by,
                               "gbs": by / (ms / n) / 1e6, "frac_of_" + peak_kind: by / (ms / n) / 1e6 / peak}
-    dom = max(k_times, key=lambda k: k_times[k][0])
+    dom = max((k for k in k_times if k != "gram"), key=lambda k: k_times[k][0])
     ms_d, n_d, by_d = k_times[dom]
     achieved = by_d / (ms_d / n_d) / 1e6
     src = {"grad_stage2": ["paper_2509_06856_gb300/csrc/grad.cu"],
-           "gram_bf16": ["paper_2509_06856_gb300/csrc/gram.cu", "paper_2509_06856_gb300/csrc/gaussian.cu"],
            "srht_pass1": ["paper_2509_06856_gb300/csrc/srht.cu"],
            "srht_pass2": ["paper_2509_06856_gb300/csrc/srht.cu"]}[dom]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

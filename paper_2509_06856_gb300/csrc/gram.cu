@@ -250,7 +250,9 @@ __global__ void __launch_bounds__(kFThreads, 1) k_gram_f32(const __grid_constant
   uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int rank = (int)blockIdx.x;  // cluster (Q, 1, 1) over grid (Q, ranges)
   const bool hub = rank == 0;
-  const GramRole ro = a.role[rank];
+  // the role, selected with static indices so that it stays in registers (a dynamic index into
+  // the parameter array would copy it to local memory, on the MMA issue path)
+  const GramRole ro = rank == 0 ? a.role[0] : (rank == 1 ? a.role[1] : a.role[2]);
   const int sw = ro.hi - ro.lo;                      // segment width: 0, 128 or 256
   const int ncol = sw > 0 ? (ro.hi < a.d ? ro.hi : a.d) - ro.lo : 0;  // columns of X inside the segment
   const int cbase = hub ? 0 : ro.lo;                 // column at byte 0 of this CTA's chunk buffers
@@ -304,15 +306,23 @@ __global__ void __launch_bounds__(kFThreads, 1) k_gram_f32(const __grid_constant
     const int64_t r = a.N - (row0 + (int64_t)k * kGK);
     return r < kGK ? (int)r : kGK;
   };
+  // operand offsets and instruction descriptors of the (at most 2) tiles, once
+  uint32_t a_off[2], b_off[2], idesc[2];
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    a_off[t] = (uint32_t)(kGM * ro.a_blk[t] - cbase) * 64u;
+    b_off[t] = (uint32_t)(ro.b_lo[t] - cbase) * 64u;
+    idesc[t] = umma_idesc_bf16(kGM, t < ro.ntile ? ro.n[t] : 128);
+  }
   auto tiles_mma = [&](uint32_t xb, bool first) {
 #pragma unroll
     for (int ks = 0; ks < kGK / 16; ++ks) {
       const uint32_t acc = (!first || ks > 0) ? 1u : 0u;
-      for (int t = 0; t < ro.ntile; ++t) {
-        const uint64_t ad = umma_desc(xb + (uint32_t)(kGM * ro.a_blk[t] - cbase) * 64u + ks * 256, 128, kGSBO);
-        const uint64_t bd = umma_desc(xb + (uint32_t)(ro.b_lo[t] - cbase) * 64u + ks * 256, 128, kGSBO);
-        umma_bf16(tmem + (uint32_t)ro.toff[t], ad, bd, umma_idesc_bf16(kGM, ro.n[t]), acc);
-      }
+#pragma unroll
+      for (int t = 0; t < 2; ++t)
+        if (t < ro.ntile)
+          umma_bf16(tmem + (uint32_t)ro.toff[t], umma_desc(xb + a_off[t] + ks * 256, 128, kGSBO),
+                    umma_desc(xb + b_off[t] + ks * 256, 128, kGSBO), idesc[t], acc);
     }
   };
 
@@ -429,7 +439,9 @@ __global__ void __launch_bounds__(kFThreads, 1) k_gram_f32(const __grid_constant
     tc_fence_after();
     const int q = warp & 3;
     if (__all_sync(0xFFFFFFFFu, ok && !*abort_f) && nk > 0) {
-      for (int t = 0; t < ro.ntile; ++t) {
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        if (t >= ro.ntile) break;
         float *row = a.part + ((int64_t)blockIdx.y * a.ncp + kGM * ro.a_blk[t] + 32 * q + lane) * a.ncp + ro.b_lo[t];
         gram_store(tmem + (uint32_t)ro.toff[t], row, ro.n[t], q, 32 * ((warp - 2) >> 2), 64);
       }
