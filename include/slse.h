@@ -240,7 +240,9 @@ slse_status slse_grad_noalloc(const slse_problem *prob, const double *beta, doub
                               slse_stream_t stream);
 
 /* Gram matrix G = Xb^T Xb (d x d, FP64, row-major, device) of the BF16 rounding Xb of X
- * (prob->dtype F32, device): the Hessian term of the mixed 2nd stage's correction form
+ * (prob->dtype F32, device; or prob->dtype SLSE_BF16 with ldx a multiple of 8 and X 16-byte
+ * aligned: G = X^T X of those values, Y unused but non-null): the Hessian term of the mixed 2nd
+ * stage's correction form
  * (SLSE_STAGE2_CORRECTION; the Hessian X^T X of Sec. 1 with X rounded to BF16).  Products of BF16
  * values are exact in FP32; they are accumulated on the tensor cores in FP32 over ranges of rows
  * and the ranges are added in FP64 in a fixed order; the upper triangle is formed and mirrored, so

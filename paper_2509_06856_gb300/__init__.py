@@ -378,11 +378,13 @@ def grad(X, Y, beta, prec: str = "fp64", workspace=None, stream=None):
 
 
 def gram(X, workspace=None, stream=None):
-    """slse_gram: G = Xb^T Xb (d x d float64 on the device) for the BF16 rounding Xb of X (float32)."""
+    """slse_gram: G = Xb^T Xb (d x d float64 on the device) for the BF16 rounding Xb of X (float32),
+    or G = X^T X for X in bfloat16 (row stride a multiple of 8)."""
     torch = _torch()
-    if X.dim() != 2 or X.stride(1) != 1 or X.dtype != torch.float32:
-        raise ValueError("X must be a row-major float32 matrix")
-    p = CProblem(X.shape[0], X.shape[1], F32, X.data_ptr(), X.stride(0), X.data_ptr())
+    if X.dim() != 2 or X.stride(1) != 1 or X.dtype not in (torch.float32, torch.bfloat16):
+        raise ValueError("X must be a row-major float32 or bfloat16 matrix")
+    code = F32 if X.dtype == torch.float32 else BF16
+    p = CProblem(X.shape[0], X.shape[1], code, X.data_ptr(), X.stride(0), X.data_ptr())
     G = torch.empty((p.d, p.d), dtype=torch.float64, device=X.device)
     ws_ptr, ws_len = (workspace.data_ptr(), workspace.numel()) if workspace is not None else (None, 0)
     st = _lib.slse_gram(ctypes.byref(p), G.data_ptr(), ws_ptr, ws_len, _stream(stream))

@@ -42,6 +42,17 @@ bool slse::valid_problem(const slse_problem *p) {
 
 namespace {
 
+// slse_gram: F32 X, or BF16 X with a row stride that is a multiple of 8 (Y unused but non-null)
+bool valid_gram_problem(const slse_problem *p) {
+  if (!p) return false;
+  if (p->dtype == SLSE_BF16) {
+    slse_problem q = *p;
+    q.dtype = SLSE_F32;
+    return slse::valid_problem(&q) && p->ldx % 8 == 0;
+  }
+  return slse::valid_problem(p) && p->dtype == SLSE_F32;
+}
+
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 constexpr size_t kStateBytes = 4096;  // DevState + per-CTA partials of the update kernel
@@ -135,6 +146,9 @@ struct FitLayout {
   bool host_in;
   bool dc;                  // mixed 2nd stage in correction form (its Gram workspace in the big region)
   GramPlan grp;
+  bool gw;                  // correction form: G_b from the SRHT intermediate W (W^T W = n2 X^T X)
+  GramWPlan gwp;
+  size_t o_gpart;           // its partial sums, inside the big region after W and its Y column
   size_t o_xin, o_yin, o_g0, o_be, o_de, o_gb, o_gst;
   size_t o_state, o_psd, o_sigma, o_pos, o_big, o_wy, o_u, o_v, o_A, o_R, o_Hinv, o_qr, o_chol, o_part, o_g,
       o_ring, o_b0, o_d32, o_out, o_r0, o_us, o_hat16;
@@ -191,7 +205,14 @@ FitLayout fit_layout(const slse_problem *p, const Sched &s, int nsm) {
   // Gram matrix take the big region, whose SRHT, CountSketch or Gaussian temporaries are dead by then
   L.host_in = is_host_pointer(p->X);
   L.dc = s.prec != SLSE_PREC_FP64 && s.stage2 == SLSE_STAGE2_CORRECTION;
-  if (L.dc) {
+  // with a two-pass SRHT, G_b is formed from the pass-1 intermediate W (BF16, kept until the 2nd
+  // stage) instead of X: its partial sums follow W in the big region
+  L.gw = L.dc && !L.cs && !L.gauss && !L.sp.single && L.n_samp > 0;
+  if (L.gw) {
+    L.gwp = gram_w_plan(L.Np, d, nsm);
+    L.o_gpart = align256(wbytes) + align256(wybytes);
+    if (L.o_gpart + L.gwp.part_bytes > big) big = L.o_gpart + L.gwp.part_bytes;
+  } else if (L.dc) {
     L.grp = gram_plan(p->N, d, nsm);
     if (L.grp.total > big) big = L.grp.total;
   }
@@ -585,12 +606,21 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     e_gram1 = E.make();
     if (!e_gram0 || !e_gram1) return SLSE_ECUDA;
     CK(cudaStreamCreateWithFlags(&gram_side.h, cudaStreamNonBlocking));
+    // after the sketch: beside pass 2 (which also reads W) the build measured slower and slowed the
+    // pass; from X, its workspace reuses the sketch's temporaries
     CK(cudaStreamWaitEvent(gram_side.h, e_sketch, 0));
     CK(cudaMemsetAsync(gram_status, 0, sizeof(unsigned), gram_side.h));
     CK(cudaEventRecord(e_gram0, gram_side.h));
-    CK(launch_gram(L.grp, static_cast<const float *>(p->X), p->ldx, Gb, gram_status, big, gram_side.h));
+    if (L.gw) {
+      const double n2 = (double)(int64_t(1) << L.sp.log2);
+      CK(launch_gram_w(L.gwp, big, L.ld16, 1.0 / n2, Gb, gram_status,
+                       reinterpret_cast<float *>(static_cast<char *>(big) + L.o_gpart), gram_side.h));
+      kernels += 2;  // Gram, reduce
+    } else {
+      CK(launch_gram(L.grp, static_cast<const float *>(p->X), p->ldx, Gb, gram_status, big, gram_side.h));
+      kernels += gram_fp32_path(L.grp, static_cast<const float *>(p->X), p->ldx) ? 2 : 3;  // (pack,) Gram, reduce
+    }
     CK(cudaEventRecord(e_gram1, gram_side.h));
-    kernels += gram_fp32_path(L.grp, static_cast<const float *>(p->X), p->ldx) ? 2 : 3;  // (pack,) Gram, reduce
   }
   // With the Gram build beside it, the main path (Hessian factor, stages 1 and 2) runs on an
   // internal stream of the highest priority: the build's grid is larger than the GPU, and without
@@ -824,9 +854,14 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     RP->stage2_full = fin.dc_fell_back;
     if (L.dc && e_gram0) {
       RP->ms_gram = ms_between(e_gram0, e_gram1);
-      const bool f32 = gram_fp32_path(L.grp, static_cast<const float *>(p->X), p->ldx);
-      RP->flops_gram = f32 ? L.grp.flops_f32 : L.grp.flops_packed;
-      RP->bytes_gram = f32 ? L.grp.bytes_f32 : L.grp.bytes_packed;
+      if (L.gw) {
+        RP->flops_gram = L.gwp.flops;
+        RP->bytes_gram = L.gwp.bytes;
+      } else {
+        const bool f32 = gram_fp32_path(L.grp, static_cast<const float *>(p->X), p->ldx);
+        RP->flops_gram = f32 ? L.grp.flops_f32 : L.grp.flops_packed;
+        RP->bytes_gram = f32 ? L.grp.bytes_f32 : L.grp.bytes_packed;
+      }
     }
     RP->kernels = kernels;
     RP->iters_stage1 = t1;
@@ -889,10 +924,11 @@ size_t slse_workspace_size(const slse_problem *prob, const slse_schedule *sched,
       if (!valid_problem(prob)) return 0;
       return grad_ws(prob, nsm);
     case SLSE_OP_GRAM: {
-      if (!valid_problem(prob)) return 0;
+      if (!valid_gram_problem(prob)) return 0;
       Layout w;
       w.take(kStateBytes);
-      w.take(gram_plan(prob->N, prob->d, nsm).total);
+      w.take(prob->dtype == SLSE_BF16 ? gram_w_plan(prob->N, prob->d, nsm).part_bytes
+                                      : gram_plan(prob->N, prob->d, nsm).total);
       return w.total;
     }
     case SLSE_OP_DRAWS: {
@@ -1025,15 +1061,18 @@ slse_status slse_grad(const slse_problem *prob, const double *beta, double *g_ou
 }
 
 slse_status slse_gram(const slse_problem *prob, double *G, void *workspace, size_t ws_bytes, slse_stream_t stream) {
-  if (!valid_problem(prob) || !G || prob->dtype != SLSE_F32) return SLSE_EINVAL;
+  if (!valid_gram_problem(prob) || !G) return SLSE_EINVAL;
   if (is_host_pointer(prob->X) || is_host_pointer(G)) return SLSE_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   const int nsm = num_sms();
   if (nsm <= 0) return SLSE_ECUDA;
-  const GramPlan gp = gram_plan(prob->N, prob->d, nsm);
+  const bool bf16 = prob->dtype == SLSE_BF16;
+  const GramPlan gp = bf16 ? GramPlan{} : gram_plan(prob->N, prob->d, nsm);
+  const GramWPlan wp = bf16 ? gram_w_plan(prob->N, prob->d, nsm) : GramWPlan{};
+  if (bf16 && !gram_w_ok(wp, prob->X, prob->ldx)) return SLSE_EINVAL;
   Layout w;
   const size_t o_state = w.take(kStateBytes);
-  const size_t o_gram = w.take(gp.total);
+  const size_t o_gram = w.take(bf16 ? wp.part_bytes : gp.total);
   Workspace W;
   slse_status a = acquire(W, workspace, ws_bytes, w.total, st);
   if (a != SLSE_OK) return a;
@@ -1041,7 +1080,10 @@ slse_status slse_gram(const slse_problem *prob, double *G, void *workspace, size
   DevState *dst = reinterpret_cast<DevState *>(base + o_state);
   k_init_state<<<1, 32, 0, st>>>(dst, 0, debug_spin_limit());
   CK(cudaGetLastError());
-  CK(launch_gram(gp, static_cast<const float *>(prob->X), prob->ldx, G, &dst->status, base + o_gram, st));
+  if (bf16)
+    CK(launch_gram_w(wp, prob->X, prob->ldx, 1.0, G, &dst->status, reinterpret_cast<float *>(base + o_gram), st));
+  else
+    CK(launch_gram(gp, static_cast<const float *>(prob->X), prob->ldx, G, &dst->status, base + o_gram, st));
   return SLSE_OK;
 }
 

@@ -459,12 +459,12 @@ __global__ void __launch_bounds__(kFThreads, 1) k_gram_f32(const __grid_constant
   asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// G[i, j] = G[j, i] = sum over ranges of part[range][i][j] (i <= j, the upper triangle) in FP64,
+// G[i, j] = G[j, i] = scale x the sum over ranges of part[range][i][j] (i <= j, the upper triangle) in FP64,
 // in a fixed order: eight interleaved sums (range mod 8, so that eight loads are in flight; a single
 // chain of dependent loads took 0.48 ms at 512 ranges), added in a fixed tree at the end; NaN after
 // a timeout.  Block row blockIdx.y = i, threads over j >= i; every range wrote its partial.
-__global__ void k_gram_reduce(const float *__restrict__ part, int splits, int ncp, int d, const unsigned *status,
-                              double *G) {
+__global__ void k_gram_reduce(const float *__restrict__ part, int splits, int ncp, int d, double scale,
+                              const unsigned *status, double *G) {
   const bool bad = (*(volatile const unsigned *)status & ST_TIMEOUT) != 0;
   const int i = blockIdx.y;
   const int j = i + (int)(blockIdx.x * blockDim.x + threadIdx.x);
@@ -481,7 +481,7 @@ __global__ void k_gram_reduce(const float *__restrict__ part, int splits, int nc
     for (int q = 0; q < 8; ++q) acc[q] += (double)v[q];
   }
   for (int q = 0; s < splits; ++s, ++q) acc[q] += (double)__ldg(p + (int64_t)s * step);
-  double v = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+  double v = scale * (((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7])));
   if (bad) v = __longlong_as_double(0x7FF8000000000000ll);
   G[(int64_t)i * d + j] = v;
   G[(int64_t)j * d + i] = v;
@@ -490,12 +490,12 @@ __global__ void k_gram_reduce(const float *__restrict__ part, int splits, int nc
 int64_t gcdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 size_t gal256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// ranges of at most kGMaxRangeChunks 32-row units (8192 rows): the FP32 sum of a range in tensor
-// memory then stays within ~2e-5 of sum |x_i x_j| (measured 9e-6 at 3400 rows); at least one
-// range per SM and column block
-void gram_split(int64_t nunit, int mt, int nsm, int64_t &cps, int &splits) {
+// ranges of at most max_units units (8192 rows): the FP32 sum of a range in tensor memory then
+// stays within ~2e-5 of sum |x_i x_j| (measured 9e-6 at 3400 rows); at least one range per SM and
+// column block (or cluster)
+void gram_split(int64_t nunit, int mt, int nsm, int64_t &cps, int &splits, int64_t max_units = kGMaxRangeChunks) {
   int64_t sp = (nsm > 0 ? nsm : 152) / mt;
-  if (sp < gcdiv(nunit, kGMaxRangeChunks)) sp = gcdiv(nunit, kGMaxRangeChunks);
+  if (sp < gcdiv(nunit, max_units)) sp = gcdiv(nunit, max_units);
   if (sp < 1) sp = 1;
   if (sp > nunit) sp = nunit;
   cps = gcdiv(nunit, sp);
@@ -555,6 +555,259 @@ void gram_f32_layout(int ncp, const GramRole *ro, int Q, GramF32Args &a, size_t 
   }
   a.o_bar = (top + 7) & ~7;
   smem = (size_t)a.o_bar + (5 * kFMaxB + 1) * 8 + 8 + 1024;
+  if (smem < 233472 / 2 + 1) smem = 233472 / 2 + 1;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Gram matrix of a BF16 matrix B (k_gram_w): of the SRHT intermediate W inside the mixed fit, and
+// of BF16 X through slse_gram.  Pass 1 of the two-pass SRHT writes W = (I (x) H_n2) P D X in BF16
+// (H_n2 unnormalised, P a row permutation with zero padding rows, D signs): W^T W = n2 X^T X
+// exactly, so G_b = W_b^T W_b / n2 serves the correction form like the Gram of the BF16 rounding of
+// X (the same relative rounding, 2^-9 per element), at half the bytes and with no rounding work:
+// the MMA reads W's row-major tiles as MN-major operands straight from the TMA boxes (64 columns x
+// 64 rows, 128-byte swizzle).
+// Roles as in k_gram_f32 (the same tiles); each 64-column box of a stage is loaded once by one CTA
+// and multicast to the CTAs whose tiles read it, the loads spread over the cluster:
+//   ncp 512: boxes 0-3 -> {r0, r1}: r1 loads 0, 1, 2, r0 loads 3; boxes 4-7 -> {r0, r2}: r2 loads
+//            4, 5, 6, r0 loads 7
+//   ncp 384: boxes 0-1 -> {r0}: r0 loads; boxes 2-5 -> {r0, r1}: r1 loads 2, 3, 4, r0 loads 5
+//   ncp <= 256: one CTA loads every box
+// A CTA releases a stage's buffer (its incoming bytes expected, the loaders of its boxes told) once
+// its MMAs of the stage that used the buffer before have completed; a loader issues a stage's
+// boxes once every destination has released the buffer.
+// rows of B per stage: KR = 64 (4 K steps; 32-row stages, twice as many in flight, measured 1.7x
+// slower at d = 512); a box is 64 columns x KR rows (KR 128 bytes)
+constexpr int kWThreads = 224;           // warp 0: loads, warp 1: MMAs, warp 2: releases, warps 3-6: epilogue
+
+struct GramWRole {
+  int ntile;
+  int a_blk[2], b_lo[2], n[2], toff[2];
+  uint32_t issue;      // bit j: this CTA loads box j
+  uint32_t feeds;      // bit q: CTA q loads boxes this CTA reads (it is told of releases)
+  int nfree;           // number of CTAs a release of this CTA's loads waits for
+  int recv_bytes;      // bytes this CTA receives per stage
+};
+
+struct GramWArgs {
+  CUtensorMap tmap;    // B as (d, rows) BF16, boxes of 64 columns x 64 rows, 128-byte swizzle
+  float *part;         // [splits][ncp][ncp], upper triangle
+  unsigned *status;
+  int64_t nstage, cps;
+  int ncp, nbox, tmem_cols, Q, S;
+  int o_bar;
+  uint16_t dest[8];    // CTA mask receiving box j
+  GramWRole role[3];
+};
+
+// shared-memory descriptor of a tcgen05 operand in the 128-byte-swizzled layout (MN-major here:
+// lbo = bytes between 64-element groups along M/N, sbo = bytes between 8-row groups along K)
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+         (1ull << 46) | (2ull << 61);
+}
+// 2-D TMA load multicast to the CTAs of mask (the same shared offset and mbarrier in each)
+__device__ __forceinline__ void tma_load_2d_mc(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar,
+                                               uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, "
+      "{%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask)
+      : "memory");
+}
+
+template <int KR>
+__global__ void __launch_bounds__(kWThreads, 1) k_gram_w(const __grid_constant__ GramWArgs a) {
+  constexpr uint32_t kBox = KR * 128;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int rank = (int)blockIdx.x;  // cluster (Q, 1, 1) over grid (Q, ranges)
+  const GramWRole ro = rank == 0 ? a.role[0] : (rank == 1 ? a.role[1] : a.role[2]);
+  const int S = a.S;
+  const uint32_t bstage = (uint32_t)a.nbox * kBox;
+  uint64_t *full = reinterpret_cast<uint64_t *>(sm + a.o_bar);
+  uint64_t *empty = full + kFMaxB;
+  uint64_t *slotfree = empty + kFMaxB;  // the destinations of this CTA's loads released a buffer
+  uint64_t *accum = slotfree + kFMaxB;
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(accum + 1);
+  volatile int *abort_f = reinterpret_cast<volatile int *>(tslot + 1);
+  volatile int *s_released = reinterpret_cast<volatile int *>(tslot + 2);
+  volatile int *s_consumed = reinterpret_cast<volatile int *>(tslot + 3);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+      mbar_init(&slotfree[s], ro.nfree > 0 ? ro.nfree : 1);
+    }
+    mbar_init(accum, 1);
+    *abort_f = 0;
+    *s_released = 0;
+    *s_consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(a.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const int64_t st0 = (int64_t)blockIdx.y * a.cps;
+  const int64_t st1 = st0 + a.cps < a.nstage ? st0 + a.cps : a.nstage;
+  const int nk = (int)(st1 - st0);
+
+  if (warp == 0) {
+    if (lane == 0 && ro.issue != 0u) {
+      for (int k = 0; k < nk; ++k) {
+        const int s = k % S;
+        if (!mbar_wait(&slotfree[s], (uint32_t)(k / S) & 1u, abort_f, a.status)) break;
+        const int y = (int)((st0 + k) * KR);
+        for (int j = 0; j < a.nbox; ++j) {
+          if (!(ro.issue >> j & 1u)) continue;
+          uint8_t *dst = sm + (size_t)s * bstage + (size_t)j * kBox;
+          if (a.Q == 1) tma_load_2d(dst, &a.tmap, 64 * j, y, &full[s]);
+          else tma_load_2d_mc(dst, &a.tmap, 64 * j, y, &full[s], a.dest[j]);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // MMAs only: stage k as soon as its boxes have landed (no other wait on this path)
+    if (lane == 0) {
+      uint32_t idesc[2];
+#pragma unroll
+      for (int t = 0; t < 2; ++t)
+        idesc[t] = umma_idesc_bf16(kGM, t < ro.ntile ? ro.n[t] : 128) | (1u << 15) | (1u << 16);  // A, B MN-major
+      int consumed = 0;
+      for (int k = 0; k < nk; ++k) {
+        const int s = k % S;
+        if (!mbar_wait(&full[s], (uint32_t)(k / S) & 1u, abort_f, a.status)) break;
+        consumed = k + 1;
+        tc_fence_after();
+        const uint32_t xb = smem_u32(sm + (size_t)s * bstage);
+#pragma unroll
+        for (int ks = 0; ks < KR / 16; ++ks) {
+          const uint32_t acc = (k > 0 || ks > 0) ? 1u : 0u;
+#pragma unroll
+          for (int t = 0; t < 2; ++t)
+            if (t < ro.ntile)
+              umma_bf16(tmem + (uint32_t)ro.toff[t],
+                        umma_desc_sw128(xb + (uint32_t)(2 * ro.a_blk[t]) * kBox + ks * 2048u, kBox, 1024),
+                        umma_desc_sw128(xb + (uint32_t)(ro.b_lo[t] / 64) * kBox + ks * 2048u, kBox, 1024),
+                        idesc[t], acc);
+        }
+        umma_commit(&empty[s]);
+      }
+      umma_commit(accum);
+      *s_consumed = consumed;
+    }
+  } else if (warp == 2) {
+    // releases: buffer s for stage j (its incoming bytes expected, its loaders told) once the MMAs
+    // of stage j - S have completed
+    if (lane == 0) {
+      int released = 0;
+      for (int j = 0; j < nk; ++j) {
+        const int s = j % S;
+        if (j >= S && !mbar_wait(&empty[s], (uint32_t)((j - S) / S) & 1u, abort_f, a.status)) break;
+        mbar_arrive_expect_tx(&full[s], (uint32_t)ro.recv_bytes);
+        for (int q = 0; q < a.Q; ++q) {
+          if (!(ro.feeds >> q & 1u)) continue;
+          if (q == rank) mbar_arrive(&slotfree[s]);
+          else mbar_arrive_remote(cluster_addr(smem_u32(&slotfree[s]), q));
+        }
+        released = j + 1;
+      }
+      *s_released = released;
+    }
+  } else {
+    // epilogue: TMEM lanes 32 q .. 32 q + 31, q = warp mod 4, hold rows 128 a_blk + 32 q + lane
+    const bool ok = mbar_wait(accum, 0u, abort_f, a.status);
+    tc_fence_after();
+    const int q = warp & 3;
+    if (__all_sync(0xFFFFFFFFu, ok && !*abort_f) && nk > 0) {
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        if (t >= ro.ntile) break;
+        float *row = a.part + ((int64_t)blockIdx.y * a.ncp + kGM * ro.a_blk[t] + 32 * q + lane) * a.ncp + ro.b_lo[t];
+        gram_store(tmem + (uint32_t)ro.toff[t], row, ro.n[t], q, 0, 32);
+      }
+    }
+    tc_fence_before();
+  }
+  __syncthreads();
+  // every copy into this CTA has landed before it exits: after a failure, the stages released but
+  // not consumed (the latest phase of their buffers) are awaited, each wait bounded
+  if (threadIdx.x == 0) {
+    for (int j = *s_consumed; j < *s_released; ++j) {
+      volatile int never = 0;
+      mbar_wait(&full[j % S], (uint32_t)(j / S) & 1u, &never, a.status);
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+  }
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// roles of k_gram_w for ncp columns (the table above it); returns Q
+int gram_w_roles(int ncp, int box_bytes, GramWArgs &a) {
+  GramRole cr[3];
+  const int Q = gram_roles(ncp, cr, nullptr);
+  a.Q = Q;
+  a.nbox = ncp / 64;
+  for (int r = 0; r < 3; ++r) {
+    GramWRole &w = a.role[r];
+    w = GramWRole{};
+    if (r >= Q) continue;
+    w.ntile = cr[r].ntile;
+    for (int t = 0; t < 2; ++t) {
+      w.a_blk[t] = cr[r].a_blk[t];
+      w.b_lo[t] = cr[r].b_lo[t];
+      w.n[t] = cr[r].n[t];
+      w.toff[t] = cr[r].toff[t];
+    }
+  }
+  uint32_t issuer[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int j = 0; j < 8; ++j) a.dest[j] = 0;
+  if (Q == 1) {
+    for (int j = 0; j < a.nbox; ++j) { a.dest[j] = 1; issuer[j] = 0; }
+  } else if (Q == 2) {
+    const int iss[6] = {0, 0, 1, 1, 1, 0};
+    for (int j = 0; j < 6; ++j) { a.dest[j] = j < 2 ? 0x1 : 0x3; issuer[j] = (uint32_t)iss[j]; }
+  } else {
+    const int iss[8] = {1, 1, 1, 0, 2, 2, 2, 0};
+    for (int j = 0; j < 8; ++j) { a.dest[j] = j < 4 ? 0x3 : 0x5; issuer[j] = (uint32_t)iss[j]; }
+  }
+  for (int r = 0; r < Q; ++r) {
+    GramWRole &w = a.role[r];
+    uint32_t dests = 0;
+    for (int j = 0; j < a.nbox; ++j) {
+      if ((int)issuer[j] == r) { w.issue |= 1u << j; dests |= a.dest[j]; }
+      if (a.dest[j] >> r & 1u) { w.recv_bytes += box_bytes; w.feeds |= 1u << issuer[j]; }
+    }
+    w.nfree = __builtin_popcount(dests);
+  }
+  return Q;
+}
+
+// shared memory of k_gram_w: S stages of all boxes (the same offsets in every CTA), the barriers
+void gram_w_layout(int ncp, int kr, GramWArgs &a, size_t &smem) {
+  const int bstage = ncp / 64 * kr * 128;
+  int S = 200 * 1024 / bstage;
+  if (S > kFMaxB) S = kFMaxB;
+  if (S < 2) S = 2;
+  a.S = S;
+  a.o_bar = S * bstage;
+  smem = (size_t)a.o_bar + (3 * kFMaxB + 1) * 8 + 16 + 1024;
   if (smem < 233472 / 2 + 1) smem = 233472 / 2 + 1;
 }
 
@@ -669,7 +922,87 @@ cudaError_t launch_gram(const GramPlan &p, const float *X, int64_t ldx, double *
     splits = p.splits;
   }
   if ((e = cudaGetLastError())) return e;
-  k_gram_reduce<<<dim3((unsigned)gcdiv(p.d, 256), (unsigned)p.d), 256, 0, s>>>(part, splits, p.ncp, p.d, status, G);
+  k_gram_reduce<<<dim3((unsigned)gcdiv(p.d, 256), (unsigned)p.d), 256, 0, s>>>(part, splits, p.ncp, p.d, 1.0, status,
+                                                                               G);
+  return cudaGetLastError();
+}
+
+GramWPlan gram_w_plan(int64_t rows, int d, int nsm) {
+  GramWPlan p{};
+  p.rows = rows;
+  p.d = d;
+  p.ncp = (int)gcdiv(d, kGM) * kGM;
+  int tc = 32;
+  while (tc < p.ncp) tc <<= 1;
+  p.tmem_cols = tc;
+  GramWArgs a{};
+  p.kr = 64;
+  const int Q = gram_w_roles(p.ncp, p.kr * 128, a);
+  p.q = Q;
+  p.nstage = gcdiv(rows, p.kr);
+  gram_split(p.nstage, Q, nsm, p.cps, p.splits, 8192 / p.kr);
+  gram_w_layout(p.ncp, p.kr, a, p.smem);
+  double ent = 0.0;
+  for (int r = 0; r < Q; ++r)
+    for (int t = 0; t < a.role[r].ntile; ++t) ent += (double)kGM * a.role[r].n[t];
+  p.part_bytes = gal256((size_t)p.splits * p.ncp * p.ncp * 4);
+  p.flops = 2.0 * (double)p.nstage * p.kr * ent;
+  p.bytes = (double)rows * d * 2.0 + 2.0 * (double)p.splits * ent * 4.0;
+  return p;
+}
+
+bool gram_w_ok(const GramWPlan &p, const void *B, int64_t ldb) {
+  return ldb % 8 == 0 && (reinterpret_cast<uintptr_t>(B) & 15u) == 0 && p.d >= 1 && p.d <= 512;
+}
+
+cudaError_t launch_gram_w(const GramWPlan &p, const void *B, int64_t ldb, double scale, double *G, unsigned *status,
+                          float *part, cudaStream_t s) {
+  static PFN_cuTensorMapEncodeTiled_v12000 enc = [] {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+    cudaGetLastError();
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  if (!enc || !gram_w_ok(p, B, ldb)) return cudaErrorInvalidValue;
+  GramWArgs a{};
+  const cuuint64_t dims[2] = {(cuuint64_t)p.d, (cuuint64_t)p.rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ldb * 2u};
+  const cuuint32_t box[2] = {64u, (cuuint32_t)p.kr};
+  const cuuint32_t estr[2] = {1u, 1u};
+  if (enc(&a.tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(B), dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  a.part = part;
+  a.status = status;
+  a.nstage = p.nstage;
+  a.cps = p.cps;
+  a.ncp = p.ncp;
+  a.tmem_cols = p.tmem_cols;
+  gram_w_roles(p.ncp, p.kr * 128, a);
+  size_t smem = 0;
+  gram_w_layout(p.ncp, p.kr, a, smem);
+  cudaError_t e;
+  auto kern = p.kr == 32 ? k_gram_w<32> : k_gram_w<64>;
+  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)a.Q, (unsigned)p.splits);
+  cfg.blockDim = dim3(kWThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)a.Q;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if ((e = cudaLaunchKernelEx(&cfg, kern, a))) return e;
+  k_gram_reduce<<<dim3((unsigned)gcdiv(p.d, 256), (unsigned)p.d), 256, 0, s>>>(part, p.splits, p.ncp, p.d, scale,
+                                                                               status, G);
   return cudaGetLastError();
 }
 

@@ -195,6 +195,19 @@ bool gram_fp32_path(const GramPlan &p, const float *X, int64_t ldx);
 // status: ST_TIMEOUT is raised there when a bounded wait gave up (G is then NaN)
 cudaError_t launch_gram(const GramPlan &p, const float *X, int64_t ldx, double *G, unsigned *status, void *ws,
                         cudaStream_t s);
+// Gram matrix of a BF16 matrix B (rows x d, row stride ldb elements, a multiple of 8, 16-byte
+// aligned), scaled: G = scale B^T B, through per-range FP32 partials (part_bytes at part)
+struct GramWPlan {
+  int64_t rows;
+  int d, ncp, tmem_cols, q, splits, kr;  // kr: rows per stage
+  int64_t nstage, cps;
+  size_t smem, part_bytes;
+  double flops, bytes;
+};
+GramWPlan gram_w_plan(int64_t rows, int d, int nsm);
+bool gram_w_ok(const GramWPlan &p, const void *B, int64_t ldb);
+cudaError_t launch_gram_w(const GramWPlan &p, const void *B, int64_t ldb, double scale, double *G, unsigned *status,
+                          float *part, cudaStream_t s);
 
 // draws.cu
 size_t draws_ws_bytes(int64_t Np);

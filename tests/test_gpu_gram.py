@@ -47,6 +47,26 @@ def test_gram_of_row_strided_views(N, d, off):
     assert np.array_equal(G, G.T)
 
 
+@pytest.mark.parametrize("N,d", [(4096 + 40, 64), (65536 + 17, 200), (1 << 17, 512), (70000, 384), (30000, 129),
+                                 (200, 128)])
+def test_gram_of_bf16_rows(N, d):
+    """BF16 X: the tensor cores read the row-major BF16 tiles directly (MN-major operands, 128-byte
+    swizzle, boxes multicast within a cluster); against the FP64 product of the same BF16 values."""
+    torch = torch_cuda()
+    import paper_2509_06856_gb300 as slse
+    X = workloads.cfg3(N=N, d=d, seed=17)["X"]
+    ld = (d + 7) // 8 * 8
+    buf = torch.zeros((N, ld), dtype=torch.bfloat16)
+    buf[:, :d] = torch.from_numpy(X).bfloat16()
+    Xd = buf.cuda()[:, :d]
+    G = host(slse.gram(Xd))
+    Xb = buf[:, :d].double().numpy()
+    err = np.abs(G - Xb.T @ Xb) / (np.abs(Xb).T @ np.abs(Xb))
+    print(f"BF16 N={N} d={d}: max error / sum|x x| = {err.max():.2e}")
+    assert np.all(err <= 1e-4)
+    assert np.array_equal(G, G.T)
+
+
 def test_gram_is_deterministic():
     torch_cuda()
     import paper_2509_06856_gb300 as slse

@@ -181,10 +181,16 @@ def test_stage2_form_field(lib):
     assert slse._lib.slse_fit(ctypes.byref(good), ctypes.byref(sch), 0, beta, None, None, None, 0, None) == slse.EINVAL
 
 
-def test_gram_rejects_non_f32(lib):
+def test_gram_rejects_bad_inputs(lib):
     import paper_2509_06856_gb300 as slse
     p64 = slse.CProblem(1000, 8, slse.F64, 256, 8, 512)
     assert slse._lib.slse_gram(ctypes.byref(p64), 1024, None, 0, None) == slse.EINVAL
     p32 = slse.CProblem(1000, 8, slse.F32, 256, 8, 512)
     assert slse._lib.slse_gram(ctypes.byref(p32), None, None, 0, None) == slse.EINVAL
     assert slse._lib.slse_workspace_size(ctypes.byref(p32), None, slse.OP_GRAM, 0) > 0
+    # BF16 X needs a row stride that is a multiple of 8 elements
+    pb = slse.CProblem(1000, 12, slse.BF16, 256, 12, 512)
+    assert slse._lib.slse_gram(ctypes.byref(pb), 1024, None, 0, None) == slse.EINVAL
+    assert slse._lib.slse_workspace_size(ctypes.byref(pb), None, slse.OP_GRAM, 0) == 0
+    pb = slse.CProblem(1000, 12, slse.BF16, 256, 16, 512)
+    assert slse._lib.slse_workspace_size(ctypes.byref(pb), None, slse.OP_GRAM, 0) > 0
