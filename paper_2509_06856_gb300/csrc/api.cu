@@ -606,22 +606,29 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     e_gram1 = E.make();
     if (!e_gram0 || !e_gram1) return SLSE_ECUDA;
     CK(cudaStreamCreateWithFlags(&gram_side.h, cudaStreamNonBlocking));
-    // after the sketch: beside pass 2 (which also reads W) the build measured slower and slowed the
-    // pass; from X, its workspace reuses the sketch's temporaries
-    CK(cudaStreamWaitEvent(gram_side.h, e_sketch, 0));
-    CK(cudaMemsetAsync(gram_status, 0, sizeof(unsigned), gram_side.h));
-    CK(cudaEventRecord(e_gram0, gram_side.h));
+  }
+  // The build is forked once the Hessian factor is formed: beside pass 2 (which also reads W) it
+  // slowed the pass by half, and beside the Hessian factor's chain of short kernels it tripled the
+  // factor's time; beside the 1st stage and the first exact pass it costs least.  (From X, its
+  // workspace reuses the sketch's temporaries.)
+  auto fork_gram = [&](cudaEvent_t after) -> cudaError_t {
+    if (!gram_side.h) return cudaSuccess;
+    cudaError_t e;
+    if ((e = cudaStreamWaitEvent(gram_side.h, after, 0))) return e;
+    if ((e = cudaMemsetAsync(gram_status, 0, sizeof(unsigned), gram_side.h))) return e;
+    if ((e = cudaEventRecord(e_gram0, gram_side.h))) return e;
     if (L.gw) {
       const double n2 = (double)(int64_t(1) << L.sp.log2);
-      CK(launch_gram_w(L.gwp, big, L.ld16, 1.0 / n2, Gb, gram_status,
-                       reinterpret_cast<float *>(static_cast<char *>(big) + L.o_gpart), gram_side.h));
+      e = launch_gram_w(L.gwp, big, L.ld16, 1.0 / n2, Gb, gram_status,
+                        reinterpret_cast<float *>(static_cast<char *>(big) + L.o_gpart), gram_side.h);
       kernels += 2;  // Gram, reduce
     } else {
-      CK(launch_gram(L.grp, static_cast<const float *>(p->X), p->ldx, Gb, gram_status, big, gram_side.h));
+      e = launch_gram(L.grp, static_cast<const float *>(p->X), p->ldx, Gb, gram_status, big, gram_side.h);
       kernels += gram_fp32_path(L.grp, static_cast<const float *>(p->X), p->ldx) ? 2 : 3;  // (pack,) Gram, reduce
     }
-    CK(cudaEventRecord(e_gram1, gram_side.h));
-  }
+    if (e) return e;
+    return cudaEventRecord(e_gram1, gram_side.h);
+  };
   // With the Gram build beside it, the main path (Hessian factor, stages 1 and 2) runs on an
   // internal stream of the highest priority: the build's grid is larger than the GPU, and without
   // priority its pending CTAs were dispatched first, so the short kernels of the Hessian factor
@@ -698,6 +705,7 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     kernels += 3;
   }
   CK(cudaEventRecord(e_qr, st));
+  CK(fork_gram(e_qr));
   phase.set("slse_fit: stage 1");
   if (tr && tr->hinv_out)
     CK(cudaMemcpyAsync(tr->hinv_out, Hinv, (size_t)d * d * 8, cudaMemcpyDeviceToDevice, st));

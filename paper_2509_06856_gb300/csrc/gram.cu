@@ -577,6 +577,10 @@ void gram_f32_layout(int ncp, const GramRole *ro, int Q, GramF32Args &a, size_t 
 // boxes once every destination has released the buffer.
 // rows of B per stage: KR = 64 (4 K steps; 32-row stages, twice as many in flight, measured 1.7x
 // slower at d = 512); a box is 64 columns x KR rows (KR 128 bytes)
+// boxes multicast within a cluster (each loaded once) or loaded by every CTA that reads them: the
+// latter measured 1.8x faster at d = 512 (1.83 against 3.28 ms at N = 2^22; the cluster's
+// buffer hand-offs serialised the stages), so multicast is kept only as the other form of the roles
+constexpr bool kWMulticast = false;
 constexpr int kWThreads = 224;           // warp 0: loads, warp 1: MMAs, warp 2: releases, warps 3-6: epilogue
 
 struct GramWRole {
@@ -595,7 +599,8 @@ struct GramWArgs {
   int64_t nstage, cps;
   int ncp, nbox, tmem_cols, Q, S;
   int o_bar;
-  uint16_t dest[8];    // CTA mask receiving box j
+  uint16_t dest[8];    // CTA mask receiving box j (multicast)
+  int mc;              // boxes multicast within the cluster (else every CTA loads its own)
   GramWRole role[3];
 };
 
@@ -671,7 +676,7 @@ __global__ void __launch_bounds__(kWThreads, 1) k_gram_w(const __grid_constant__
         for (int j = 0; j < a.nbox; ++j) {
           if (!(ro.issue >> j & 1u)) continue;
           uint8_t *dst = sm + (size_t)s * bstage + (size_t)j * kBox;
-          if (a.Q == 1) tma_load_2d(dst, &a.tmap, 64 * j, y, &full[s]);
+          if (!a.mc) tma_load_2d(dst, &a.tmap, 64 * j, y, &full[s]);
           else tma_load_2d_mc(dst, &a.tmap, 64 * j, y, &full[s], a.dest[j]);
         }
       }
@@ -759,7 +764,7 @@ __global__ void __launch_bounds__(kWThreads, 1) k_gram_w(const __grid_constant__
 }
 
 // roles of k_gram_w for ncp columns (the table above it); returns Q
-int gram_w_roles(int ncp, int box_bytes, GramWArgs &a) {
+int gram_w_roles(int ncp, int box_bytes, GramWArgs &a, bool multicast) {
   GramRole cr[3];
   const int Q = gram_roles(ncp, cr, nullptr);
   a.Q = Q;
@@ -776,8 +781,24 @@ int gram_w_roles(int ncp, int box_bytes, GramWArgs &a) {
       w.toff[t] = cr[r].toff[t];
     }
   }
-  uint32_t issuer[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  a.mc = multicast && Q > 1 ? 1 : 0;
   for (int j = 0; j < 8; ++j) a.dest[j] = 0;
+  if (!a.mc) {
+    // every CTA loads the boxes its tiles read (the CTAs of a range run side by side, so the
+    // second reader of a box mostly finds it in L2)
+    for (int r = 0; r < Q; ++r) {
+      GramWRole &w = a.role[r];
+      for (int t = 0; t < w.ntile; ++t) {
+        for (int c = kGM * w.a_blk[t]; c < kGM * (w.a_blk[t] + 1); c += 64) w.issue |= 1u << (c / 64);
+        for (int c = w.b_lo[t]; c < w.b_lo[t] + w.n[t]; c += 64) w.issue |= 1u << (c / 64);
+      }
+      w.feeds = 1u << r;
+      w.nfree = 1;
+      w.recv_bytes = __builtin_popcount(w.issue) * box_bytes;
+    }
+    return Q;
+  }
+  uint32_t issuer[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   if (Q == 1) {
     for (int j = 0; j < a.nbox; ++j) { a.dest[j] = 1; issuer[j] = 0; }
   } else if (Q == 2) {
@@ -937,7 +958,7 @@ GramWPlan gram_w_plan(int64_t rows, int d, int nsm) {
   p.tmem_cols = tc;
   GramWArgs a{};
   p.kr = 64;
-  const int Q = gram_w_roles(p.ncp, p.kr * 128, a);
+  const int Q = gram_w_roles(p.ncp, p.kr * 128, a, kWMulticast);
   p.q = Q;
   p.nstage = gcdiv(rows, p.kr);
   gram_split(p.nstage, Q, nsm, p.cps, p.splits, 8192 / p.kr);
@@ -982,7 +1003,7 @@ cudaError_t launch_gram_w(const GramWPlan &p, const void *B, int64_t ldb, double
   a.cps = p.cps;
   a.ncp = p.ncp;
   a.tmem_cols = p.tmem_cols;
-  gram_w_roles(p.ncp, p.kr * 128, a);
+  gram_w_roles(p.ncp, p.kr * 128, a, kWMulticast);
   size_t smem = 0;
   gram_w_layout(p.ncp, p.kr, a, smem);
   cudaError_t e;
@@ -995,7 +1016,7 @@ cudaError_t launch_gram_w(const GramWPlan &p, const void *B, int64_t ldb, double
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)a.Q;
+  attr[0].val.clusterDim.x = a.mc ? (unsigned)a.Q : 1u;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
