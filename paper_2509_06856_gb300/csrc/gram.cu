@@ -9,17 +9,19 @@
 // column of X and k the row in the chunk), so column c of a chunk starts at byte 64 c.  A tile is
 // 128 rows of G_b (MMA M = 128, A = 128 columns of the chunk) times up to 256 columns (B).  Each CTA
 // keeps its tiles in tensor memory for a range of at most 8192 rows and writes them as an FP32
-// partial; k_gram_reduce adds the ranges' partials in a fixed order in FP64 (deterministic) from
+// partial; the reduction adds the ranges' partials in a fixed order in FP64 (deterministic) from
 // the upper triangle and mirrors it, so G_b is exactly symmetric.
 //
-// Two ways in:
-//  - k_gram_f32 (X FP32 with 16-byte aligned rows and d a multiple of 4): a cluster of 1-3 CTAs
-//    per range; each CTA copies its segment of the columns of 32 rows at a time into shared memory
-//    (2-D TMA boxes of 32 rows x 128 columns; zeros past the edges), eight converter warps round them to BF16 into
-//    the chunk layout (one column of 8 rows per thread and step: 8 conflict-free 4-byte reads, one
-//    16-byte write), warp 1 issues the MMAs of the CTA's tiles and sends the rounded segment to the
-//    cluster's hub by a bulk copy between shared memories.  X is read from DRAM and rounded once,
-//    the tiles cover the upper triangle with equal MMA work per CTA (roles below).
+// Three ways in:
+//  - k_gram_w (BF16 input: the SRHT intermediate W inside the fit, BF16 X through slse_gram): the
+//    MMAs read the row-major tiles as MN-major operands straight from TMA boxes.
+//  - k_gram_f32 (X FP32 with 16-byte aligned rows and d a multiple of 4): 1-3 CTAs per range of
+//    rows; each copies the columns its tiles read, 32 rows at a time, into shared memory (2-D TMA
+//    boxes of 32 rows x 128 columns; zeros past the edges), eight converter warps round them to
+//    BF16 into the chunk layout (one column of 8 rows per thread and step: 8 conflict-free 4-byte
+//    reads, one 16-byte write) and warp 1 issues the MMAs of the CTA's tiles.  The CTAs of a range
+//    sit next to each other in the grid and share X's rows through L2; the tiles cover the upper
+//    triangle with equal MMA work per CTA (roles below).
 //  - k_gram_tc (any other X): X is first packed to BF16 chunks by the Gaussian sketch's packer,
 //    then streamed by bulk copies; the CTA of column block i0 forms rows i0 .. i0 + 127 times all
 //    columns (the CTAs of a range then run at one rate and share the chunks through L2).
@@ -44,6 +46,11 @@ constexpr int kGSBO = kGK * 16;          // bytes between 8-column groups of a c
 constexpr int kGThreads = 128;           // warp 0: copies, warp 1: MMAs, warps 0-3: epilogue
 constexpr int kGMaxStages = 6;
 constexpr int64_t kGMaxRangeChunks = 256;
+// k_gram_f32: every CTA reads and rounds the columns its tiles read (own segments, no copies
+// between CTAs) rather than one segment each with the hub receiving the others': measured faster
+// at N = 2^22 (d = 512: 3.5 against 4.2 ms; d = 384: 2.7 against 3.1 ms), the CTAs of a range
+// sharing X through L2; the hub form is kept as the other form of the roles
+constexpr bool kFOwn = true;
 constexpr int kFConv = 8;                        // converter warps of k_gram_f32
 constexpr int kFThreads = 64 + 32 * kFConv;      // + copy warp + MMA warp
 
@@ -201,6 +208,8 @@ struct GramF32Args {
   int64_t nstage, cps;  // 32-row stages of X, stages per range
   int ncp, tmem_cols, Q;
   int in_bytes;         // bytes the hub receives per stage
+  int own;              // every CTA reads and rounds the columns its tiles read (segment = that
+                        // range; no copies between CTAs, a cluster of one)
   int s3, nb;           // FP32 stages, chunk buffers (the hub's of the full width, a peer's of its segment)
   int o_bar;            // byte offset of the barriers (the same in every CTA of the cluster)
   int o16[3];           // byte offset of each role's chunk buffers
@@ -249,7 +258,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_gram_f32(const __grid_constant
   extern __shared__ uint8_t smem_raw[];
   uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int rank = (int)blockIdx.x;  // cluster (Q, 1, 1) over grid (Q, ranges)
-  const bool hub = rank == 0;
+  const bool hub = rank == 0 && !a.own;
   // the role, selected with static indices so that it stays in registers (a dynamic index into
   // the parameter array would copy it to local memory, on the MMA issue path)
   const GramRole ro = rank == 0 ? a.role[0] : (rank == 1 ? a.role[1] : a.role[2]);
@@ -387,7 +396,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_gram_f32(const __grid_constant
           // waited for that), then this CTA's own tiles
           uint8_t *seg = s16 + (size_t)b * b16;
           uint8_t *hub_seg = sm + a.o16[0] + (size_t)b * ((size_t)a.ncp * kGK * 2) + (size_t)ro.lo * 64;
-          bulk_s2c(cluster_addr(smem_u32(hub_seg), 0), seg, b16, cluster_addr(smem_u32(&fullb[b]), 0));
+          if (!a.own) bulk_s2c(cluster_addr(smem_u32(hub_seg), 0), seg, b16, cluster_addr(smem_u32(&fullb[b]), 0));
           tiles_mma(smem_u32(seg), k == 0);
           umma_commit(&emptyb[b]);
         }
@@ -398,19 +407,19 @@ __global__ void __launch_bounds__(kFThreads, 1) k_gram_f32(const __grid_constant
     // converters: item (n, k8) = column lo + n, rows 8 k8 .. 8 k8 + 7 of the stage; consecutive
     // threads take consecutive columns
     const int ct = threadIdx.x - 64;
-    const int lsw = sw == 256 ? 8 : 7;
+    const int lsw = sw == 512 ? 9 : (sw == 256 ? 8 : (sw == 128 ? 7 : -1));  // -1: divide
     for (int k = 0; k < nk; ++k) {
       const int s = k % a.s3, b = k % nb;
       const uint32_t pb = (uint32_t)(k / nb) & 1u;
       bool ok = mbar_wait(&full32[s], (uint32_t)(k / a.s3) & 1u, abort_f, a.status);
       ok = ok && mbar_wait(&emptyb[b], pb ^ 1u, abort_f, a.status);
-      if (!hub) ok = ok && mbar_wait(&hubfree[b], pb, abort_f, a.status);
+      if (!hub && !a.own) ok = ok && mbar_wait(&hubfree[b], pb, abort_f, a.status);
       if (!__all_sync(0xFFFFFFFFu, ok)) break;
       const int nr = rows_of(k);
       const float *src = s32 + (size_t)s * (b32 / 4);
       uint8_t *dst = s16 + (size_t)b * b16 + (size_t)(ro.lo - cbase) * 64;
       for (int it = ct; it < sw * (kGK / 8); it += 32 * kFConv) {
-        const int n = it & (sw - 1), k8 = it >> lsw;
+        const int n = lsw >= 0 ? (it & (sw - 1)) : it % sw, k8 = lsw >= 0 ? (it >> lsw) : it / sw;
         const int pan = (n >> 7) * (kGK * 128) + (n & 127);  // panel of 128 columns, row-major
         uint32_t w[4];
 #pragma unroll
@@ -459,33 +468,54 @@ __global__ void __launch_bounds__(kFThreads, 1) k_gram_f32(const __grid_constant
   asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// G[i, j] = G[j, i] = scale x the sum over ranges of part[range][i][j] (i <= j, the upper triangle) in FP64,
-// in a fixed order: eight interleaved sums (range mod 8, so that eight loads are in flight; a single
-// chain of dependent loads took 0.48 ms at 512 ranges), added in a fixed tree at the end; NaN after
-// a timeout.  Block row blockIdx.y = i, threads over j >= i; every range wrote its partial.
-__global__ void k_gram_reduce(const float *__restrict__ part, int splits, int ncp, int d, double scale,
+// The partials are summed in two streaming steps, each in a fixed order (deterministic): groups of
+// kRG ranges into FP64 group sums (consecutive threads read consecutive entries of one range's
+// partial: every partial is read in contiguous rows), then the groups, scaled and mirrored.  (One
+// thread per entry walking all ranges, 1 MB apart, took 0.49 ms at 512 ranges: latency and TLB
+// bound.)  Only the upper triangle (j >= i) is read; NaN after a timeout.
+constexpr int kRG = 16;
+
+// grp[g][i][j] = sum of part[r][i][j] over ranges r of group g, j >= i; grid (ncp rows x ncp / 128
+// column blocks, groups), 128 threads
+__global__ void __launch_bounds__(128) k_gram_reduce_grp(const float *__restrict__ part, int splits, int ncp,
+                                                         double *__restrict__ grp) {
+  const int i = blockIdx.x / (ncp / 128), j = (blockIdx.x % (ncp / 128)) * 128 + threadIdx.x;
+  if (j < i) return;
+  const int g = blockIdx.y;
+  const int r1 = (g + 1) * kRG < splits ? (g + 1) * kRG : splits;
+  const int64_t e = (int64_t)i * ncp + j, step = (int64_t)ncp * ncp;
+  double acc = 0.0;
+  for (int r = g * kRG; r < r1; ++r) acc += (double)__ldg(part + r * step + e);
+  grp[g * step + e] = acc;
+}
+
+// G[i, j] = G[j, i] = scale x the sum of the group sums, i <= j < d
+__global__ void k_gram_reduce(const double *__restrict__ grp, int ngroups, int ncp, int d, double scale,
                               const unsigned *status, double *G) {
   const bool bad = (*(volatile const unsigned *)status & ST_TIMEOUT) != 0;
   const int i = blockIdx.y;
   const int j = i + (int)(blockIdx.x * blockDim.x + threadIdx.x);
   if (j >= d) return;
-  const float *p = part + (int64_t)i * ncp + j;
-  const int64_t step = (int64_t)ncp * ncp;
-  double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  int s = 0;
-  for (; s + 8 <= splits; s += 8) {
-    float v[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = __ldg(p + (int64_t)(s + q) * step);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] += (double)v[q];
-  }
-  for (int q = 0; s < splits; ++s, ++q) acc[q] += (double)__ldg(p + (int64_t)s * step);
-  double v = scale * (((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7])));
+  const int64_t e = (int64_t)i * ncp + j, step = (int64_t)ncp * ncp;
+  double v = 0.0;
+  for (int g = 0; g < ngroups; ++g) v += grp[g * step + e];
+  v *= scale;
   if (bad) v = __longlong_as_double(0x7FF8000000000000ll);
   G[(int64_t)i * d + j] = v;
   G[(int64_t)j * d + i] = v;
 }
+
+// both reduction steps; grp holds ceil(splits / kRG) ncp^2 doubles
+cudaError_t launch_gram_reduce(const float *part, int splits, int ncp, int d, double scale, double *grp,
+                               const unsigned *status, double *G, cudaStream_t s) {
+  const int ng = (splits + kRG - 1) / kRG;
+  k_gram_reduce_grp<<<dim3((unsigned)(ncp / 128) * (unsigned)ncp, (unsigned)ng), 128, 0, s>>>(part, splits, ncp, grp);
+  cudaError_t e = cudaGetLastError();
+  if (e) return e;
+  k_gram_reduce<<<dim3((unsigned)((d + 255) / 256), (unsigned)d), 256, 0, s>>>(grp, ng, ncp, d, scale, status, G);
+  return cudaGetLastError();
+}
+size_t gram_grp_bytes(int splits, int ncp) { return (size_t)((splits + kRG - 1) / kRG) * ncp * ncp * 8; }
 
 int64_t gcdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 size_t gal256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -540,17 +570,35 @@ int gram_roles(int ncp, GramRole *ro, int *in_bytes) {
   return Q;
 }
 
+// own segments: each CTA's segment becomes the range of columns its tiles read
+void gram_own_segments(int Q, GramRole *ro) {
+  for (int r = 0; r < Q; ++r) {
+    int lo = 1 << 30, hi = 0;
+    for (int t = 0; t < ro[r].ntile; ++t) {
+      const int c[4] = {kGM * ro[r].a_blk[t], kGM * (ro[r].a_blk[t] + 1), ro[r].b_lo[t], ro[r].b_lo[t] + ro[r].n[t]};
+      lo = c[0] < lo ? c[0] : lo;
+      lo = c[2] < lo ? c[2] : lo;
+      hi = c[1] > hi ? c[1] : hi;
+      hi = c[3] > hi ? c[3] : hi;
+    }
+    ro[r].lo = lo;
+    ro[r].hi = hi;
+  }
+}
+
 // shared-memory layout of k_gram_f32 (see there): 3 FP32 stages and 3 chunk buffers (measured
 // fastest: 4 stages and up to 6 hub buffers were slower); the barriers at one offset for all
 // roles; one CTA per SM
 void gram_f32_layout(int ncp, const GramRole *ro, int Q, GramF32Args &a, size_t &smem) {
-  a.s3 = 3;
-  a.nb = 3;
+  int wmax = 0;
+  for (int r = 0; r < Q; ++r) wmax = ro[r].hi - ro[r].lo > wmax ? ro[r].hi - ro[r].lo : wmax;
+  a.s3 = wmax > 256 ? 2 : 3;  // own segments up to 512 columns: 2 + 2 buffers fit
+  a.nb = wmax > 256 ? 2 : 3;
   int top = 0;
   for (int r = 0; r < Q; ++r) {
     const int sw = ro[r].hi - ro[r].lo;
     a.o16[r] = a.s3 * sw * kGK * 4;
-    const int end = a.o16[r] + (r == 0 ? ncp : sw) * a.nb * kGK * 2;
+    const int end = a.o16[r] + (r == 0 && !a.own ? ncp : sw) * a.nb * kGK * 2;
     if (end > top) top = end;
   }
   a.o_bar = (top + 7) & ~7;
@@ -859,6 +907,8 @@ GramPlan gram_plan(int64_t N, int d, int nsm) {
   p.nstage = gcdiv(N, kGK);
   gram_split(p.nstage, p.q_f, nsm, p.cps_f, p.splits_f);
   GramF32Args lay{};
+  lay.own = kFOwn ? 1 : 0;
+  if (lay.own) gram_own_segments(p.q_f, ro);
   gram_f32_layout(p.ncp, ro, p.q_f, lay, p.smem_f);
   double ent_f = 0.0;  // accumulator entries of one range
   for (int r = 0; r < p.q_f; ++r)
@@ -871,7 +921,8 @@ GramPlan gram_plan(int64_t N, int d, int nsm) {
   const int sp = p.splits > p.splits_f ? p.splits : p.splits_f;
   p.o_xt = 0;
   p.o_part = gal256((size_t)p.nchunk * bC);
-  p.total = p.o_part + gal256((size_t)sp * p.ncp * p.ncp * 4);
+  p.o_grp = p.o_part + gal256((size_t)sp * p.ncp * p.ncp * 4);
+  p.total = p.o_grp + gal256(gram_grp_bytes(sp, p.ncp));
   return p;
 }
 
@@ -916,6 +967,8 @@ cudaError_t launch_gram(const GramPlan &p, const float *X, int64_t ldx, double *
     a.N = p.N; a.d = p.d; a.part = part; a.status = status;
     a.nstage = p.nstage; a.cps = p.cps_f; a.ncp = p.ncp; a.tmem_cols = p.tmem_cols;
     a.Q = gram_roles(p.ncp, a.role, &a.in_bytes);
+    a.own = kFOwn ? 1 : 0;
+    if (a.own) gram_own_segments(a.Q, a.role);
     size_t smem_f = 0;
     gram_f32_layout(p.ncp, a.role, a.Q, a, smem_f);
     cudaLaunchConfig_t cfg = {};
@@ -925,7 +978,7 @@ cudaError_t launch_gram(const GramPlan &p, const float *X, int64_t ldx, double *
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)a.Q;
+    attr[0].val.clusterDim.x = a.own ? 1u : (unsigned)a.Q;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
@@ -943,9 +996,7 @@ cudaError_t launch_gram(const GramPlan &p, const float *X, int64_t ldx, double *
     splits = p.splits;
   }
   if ((e = cudaGetLastError())) return e;
-  k_gram_reduce<<<dim3((unsigned)gcdiv(p.d, 256), (unsigned)p.d), 256, 0, s>>>(part, splits, p.ncp, p.d, 1.0, status,
-                                                                               G);
-  return cudaGetLastError();
+  return launch_gram_reduce(part, splits, p.ncp, p.d, 1.0, reinterpret_cast<double *>(base + p.o_grp), status, G, s);
 }
 
 GramWPlan gram_w_plan(int64_t rows, int d, int nsm) {
@@ -966,7 +1017,8 @@ GramWPlan gram_w_plan(int64_t rows, int d, int nsm) {
   double ent = 0.0;
   for (int r = 0; r < Q; ++r)
     for (int t = 0; t < a.role[r].ntile; ++t) ent += (double)kGM * a.role[r].n[t];
-  p.part_bytes = gal256((size_t)p.splits * p.ncp * p.ncp * 4);
+  p.o_grp = gal256((size_t)p.splits * p.ncp * p.ncp * 4);
+  p.part_bytes = p.o_grp + gal256(gram_grp_bytes(p.splits, p.ncp));
   p.flops = 2.0 * (double)p.nstage * p.kr * ent;
   p.bytes = (double)rows * d * 2.0 + 2.0 * (double)p.splits * ent * 4.0;
   return p;
@@ -1022,9 +1074,8 @@ cudaError_t launch_gram_w(const GramWPlan &p, const void *B, int64_t ldb, double
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   if ((e = cudaLaunchKernelEx(&cfg, kern, a))) return e;
-  k_gram_reduce<<<dim3((unsigned)gcdiv(p.d, 256), (unsigned)p.d), 256, 0, s>>>(part, p.splits, p.ncp, p.d, scale,
-                                                                               status, G);
-  return cudaGetLastError();
+  return launch_gram_reduce(part, p.splits, p.ncp, p.d, scale,
+                            reinterpret_cast<double *>(reinterpret_cast<char *>(part) + p.o_grp), status, G, s);
 }
 
 }  // namespace slse

@@ -179,7 +179,7 @@ struct GramPlan {
   int64_t N;
   int d, ncp, tmem_cols, stages, splits;
   int64_t nchunk, cps;
-  size_t smem, o_xt, o_part, total;
+  size_t smem, o_xt, o_part, o_grp, total;
   // FP32 path (rows read and rounded on chip): 32-row stages, stages per range, ranges, shared memory
   int64_t nstage, cps_f;
   int splits_f, q_f;  // ranges, CTAs per range (a cluster)
@@ -201,7 +201,7 @@ struct GramWPlan {
   int64_t rows;
   int d, ncp, tmem_cols, q, splits, kr;  // kr: rows per stage
   int64_t nstage, cps;
-  size_t smem, part_bytes;
+  size_t smem, o_grp, part_bytes;  // the FP64 group sums of the reduction start at o_grp
   double flops, bytes;
 };
 GramWPlan gram_w_plan(int64_t rows, int d, int nsm);
