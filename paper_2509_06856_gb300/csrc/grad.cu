@@ -85,16 +85,6 @@ template <> struct Vec<float, 2> {  // FP32 data widened to FP64 arithmetic uses
   }
 };
 
-__device__ __forceinline__ void load_bf16x8(const __nv_bfloat16 *p, float (&o)[8]) {
-  const uint4 t = __ldg(reinterpret_cast<const uint4 *>(p));
-  const uint32_t w[4] = {t.x, t.y, t.z, t.w};
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    o[2 * k] = __uint_as_float(w[k] << 16);
-    o[2 * k + 1] = __uint_as_float(w[k] & 0xFFFF0000u);
-  }
-}
-
 template <class T> __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
