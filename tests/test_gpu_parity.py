@@ -107,6 +107,33 @@ def test_grad_fp64_on_fp32_storage(slse, N, d):
     np.testing.assert_array_less(np.abs(g - go), 1e-13 * _grad_bound(X, Y, beta) + 1e-300)
 
 
+@pytest.mark.parametrize("d", [7, 256, 512])
+def test_grad_fp64_on_fp32_storage_special_values(slse, d):
+    # FP32 storage widened to FP64: signed zeros, denormals, the largest and smallest normals and
+    # powers of two exactly at the exponent limits, in scattered rows and columns, then a row with
+    # an infinity and one with a NaN (the gradient is then non-finite exactly where the oracle's is)
+    rng = np.random.default_rng(d)
+    N = 3000
+    X = rng.standard_normal((N, d)).astype(np.float32)
+    Y = rng.standard_normal(N).astype(np.float32)
+    specials = np.array([0.0, -0.0, 1e-40, -3e-45, 1.1754944e-38, -1.1754942e-38, 2.0 ** -126, 2.0 ** 127,
+                         -3.4e38, 1.0, -1.0, 0.5], np.float32)
+    idx = rng.integers(0, N * d, size=4 * len(specials))
+    X.reshape(-1)[idx] = np.tile(specials, 4)
+    Y[rng.integers(0, N, size=6)] = np.array([0.0, -0.0, 1e-40, -1e-42, 2.0 ** -126, 3e38], np.float32)
+    beta = 1e-3 * rng.standard_normal(d)
+    go = osl.grad(X.astype(np.float64), Y.astype(np.float64), beta)
+    g = host(slse.grad(dev(X), dev(Y), beta, prec="fp64"))
+    np.testing.assert_array_less(np.abs(g - go), 1e-13 * _grad_bound(X, Y, beta) + 1e-300)
+    for bad in (np.float32(np.inf), np.float32(np.nan)):
+        Xb = X.copy()
+        Xb[N // 3, d // 2] = bad
+        gob = osl.grad(Xb.astype(np.float64), Y.astype(np.float64), beta)
+        gb = host(slse.grad(dev(Xb), dev(Y), beta, prec="fp64"))
+        assert np.array_equal(np.isfinite(gb), np.isfinite(gob))
+        assert np.array_equal(np.isnan(gb), np.isnan(gob))
+
+
 @pytest.mark.parametrize("N,d", [(100, 3), (20000, 64), ((1 << 16) + 7, 256), (3000, 512), (4097, 50), (999, 7)])
 def test_grad_mixed_matches_oracle(slse, N, d):
     # FP32 arithmetic with error-free residuals: the residual is exact to ~2^-48
