@@ -150,6 +150,8 @@ struct FitLayout {
   GramWPlan gwp;
   size_t o_gpart;           // its partial sums, inside the big region after W and its Y column
   size_t o_xin, o_yin, o_g0, o_be, o_de, o_gb, o_gst;
+  bool sig_side;            // two-pass SRHT: sigma and pos drawn on a side stream beside pass 1
+  size_t o_sigws;           // the temporaries of that sort (the big region is W by then)
   size_t o_state, o_psd, o_sigma, o_pos, o_big, o_wy, o_u, o_v, o_A, o_R, o_Hinv, o_qr, o_chol, o_part, o_g,
       o_ring, o_b0, o_d32, o_out, o_r0, o_us, o_hat16;
   size_t total;
@@ -189,6 +191,8 @@ FitLayout fit_layout(const slse_problem *p, const Sched &s, int nsm) {
   L.o_psd = w.take(nperm);
   L.o_sigma = w.take(nperm);
   L.o_pos = w.take(nperm);
+  L.sig_side = !L.cs && !L.sp.single && L.n_samp > 0;
+  L.o_sigws = w.take(L.sig_side ? draws_one_ws_bytes(L.Np) : 0);
   size_t big = L.cs ? L.csp.total : draws_ws_bytes(L.Np);
   const size_t wbytes = (L.sp.single || L.cs) ? 0 : (size_t)L.Np * L.ld16 * ew;
   const size_t wybytes = (L.sp.single || L.cs) ? 0 : (size_t)L.Np * ew;
@@ -453,8 +457,8 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
 
   Events E;
   cudaEvent_t e_start = E.make(), e_draws = E.make(), e_mid = E.make(), e_sketch = E.make(), e_qr = E.make(),
-              e_s1 = E.make(), e_end = E.make(), e_copied = E.make();
-  if (!e_start || !e_end || !e_mid || !e_copied) return SLSE_ECUDA;
+              e_s1 = E.make(), e_end = E.make(), e_copied = E.make(), e_sig = E.make();
+  if (!e_start || !e_end || !e_mid || !e_copied || !e_sig) return SLSE_ECUDA;
   const int hist_cap = tr ? (tr->cap < T ? tr->cap : T) : 0;
   std::vector<cudaEvent_t> e_it;
   if (tr && tr->ms_hist)
@@ -482,6 +486,22 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
       if (h) cudaStreamDestroy(h);
     }
   } side;
+  // the stream of the sigma draws; the caller's stream waits for it on every return (pass 2
+  // waits for it anyway), so no work of the fit outlives the call's stream order
+  struct JoinedStream {
+    cudaStream_t h = nullptr, main = nullptr;
+    ~JoinedStream() {
+      if (!h) return;
+      cudaEvent_t e = nullptr;
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) {
+        cudaEventRecord(e, h);
+        cudaStreamWaitEvent(main, e, 0);
+        cudaEventDestroy(e);
+      }
+      cudaStreamDestroy(h);
+    }
+  } sig_side;
+  sig_side.main = st;
   const void *x_mapped = nullptr;  // device address of host X read by pass 1 (fused path)
   void *x_copy = nullptr;          // where pass 1 stores it
   if (L.host_in) {
@@ -538,13 +558,30 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
     CK(cudaEventRecord(e_mid, st));
   } else {
     // a1: random draws (none when nothing is sampled: a Gaussian Hessian sketch without subproblems)
-    if (L.n_samp > 0) {
-      CK(launch_draws(L.Np, seed, Psd, nullptr, sigma, nullptr, big, st));
-      kernels += 9;
-      CK(launch_pos_map(sigma, L.Np, 0, L.n_samp, L.sp.single ? L.sp.logN : L.sp.log2, pos, st));
-      kernels += 1;
+    if (L.sig_side) {
+      // pass 1 needs only P: sigma and its position map (read from pass 2 on) are drawn after P
+      // on a side stream of the lowest priority, beside pass 1 (a latency-bound pass), and pass 2
+      // waits for them.  Measured at N' = 2^22: draws 0.57 -> 0.32 ms, pass 1 unchanged (3.49 ms);
+      // at the highest priority the sort's CTAs displaced pass 1's clusters (pass 1 4.59 ms)
+      CK(launch_draws_perm(L.Np, seed, Psd, big, st));
+      CK(cudaEventRecord(e_draws, st));
+      int least = 0, greatest = 0;
+      CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+      CK(cudaStreamCreateWithPriority(&sig_side.h, cudaStreamNonBlocking, least));
+      CK(cudaStreamWaitEvent(sig_side.h, e_draws, 0));
+      CK(launch_draws_sigma(L.Np, seed, sigma, base + L.o_sigws, sig_side.h));
+      CK(launch_pos_map(sigma, L.Np, 0, L.n_samp, L.sp.log2, pos, sig_side.h));
+      CK(cudaEventRecord(e_sig, sig_side.h));
+      kernels += 10;
+    } else {
+      if (L.n_samp > 0) {
+        CK(launch_draws(L.Np, seed, Psd, nullptr, sigma, nullptr, big, st));
+        kernels += 5;  // histogram, scan, scatter, bucket sort (both permutations each), sign fold
+        CK(launch_pos_map(sigma, L.Np, 0, L.n_samp, L.sp.single ? L.sp.logN : L.sp.log2, pos, st));
+        kernels += 1;
+      }
+      CK(cudaEventRecord(e_draws, st));
     }
-    CK(cudaEventRecord(e_draws, st));
     phase.set("slse_fit: sketch");
     if (L.host_in) CK(cudaStreamWaitEvent(st, e_copied, 0));
     // a2-a4: SRHT into the sampled rows (U = Z[sigma] with Z = H D P X / sqrt(N'); sketch scales applied later)
@@ -563,8 +600,9 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
       // FP8 form: the Hessian-sketch rows (sampling positions >= h0) are written in BF16 to h16
       CK(launch_srht(L.sp, s.prec, p->dtype, x_mapped ? x_mapped : p->X, p->ldx, p->Y, p->N, d, Psd, pos, big, WY,
                      L.ld16, U, V, L.ldu, 1.0 / std::sqrt((double)L.Np), st, L.sp.single ? nullptr : e_mid, Us, L.nsb,
-                     h16, L.h0 > 0 ? L.h0 : INT64_MAX, L.ld16, x_copy, &dst->status));
-      kernels += L.sp.single ? 1 : 2;
+                     h16, L.h0 > 0 ? L.h0 : INT64_MAX, L.ld16, x_copy, &dst->status,
+                     L.sig_side ? e_sig : nullptr));
+      kernels += L.sp.single ? 1 : 4;  // per pass: the X columns and the Y column
     }
     if (L.gauss) {
       // S-hat X = G X / sqrt(r) (Gaussian sketch, Sec. 2) in place of sampled SRHT rows:
@@ -621,7 +659,7 @@ slse_status fit_impl(const slse_problem *pin, const Sched &s, uint64_t seed, dou
       const double n2 = (double)(int64_t(1) << L.sp.log2);
       e = launch_gram_w(L.gwp, big, L.ld16, 1.0 / n2, Gb, gram_status,
                         reinterpret_cast<float *>(static_cast<char *>(big) + L.o_gpart), gram_side.h);
-      kernels += 2;  // Gram, reduce
+      kernels += 3;  // Gram, group sums, final sum
     } else {
       e = launch_gram(L.grp, static_cast<const float *>(p->X), p->ldx, Gb, gram_status, big, gram_side.h);
       kernels += gram_fp32_path(L.grp, static_cast<const float *>(p->X), p->ldx) ? 2 : 3;  // (pack,) Gram, reduce

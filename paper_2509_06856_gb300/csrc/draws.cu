@@ -64,6 +64,37 @@ cudaError_t launch_draws(int64_t Np, uint64_t seed, int32_t *Psd, int32_t *P, in
   return cudaGetLastError();
 }
 
+size_t draws_one_ws_bytes(int64_t Np) {
+  const int B = sortk::bits_for(Np) > 10 ? sortk::bits_for(Np) - 10 : 0;
+  return sortk::align256(sortk::sort_ws_bytes(Np, B));
+}
+
+cudaError_t launch_draws_perm(int64_t Np, uint64_t seed, int32_t *Psd, void *ws, cudaStream_t s) {
+  const int B = sortk::bits_for(Np) > 10 ? sortk::bits_for(Np) - 10 : 0;
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  char *p = static_cast<char *>(ws);
+  sortk::SortArrays w{};
+  w.key[0] = sortk::RowKey{sortk::KEY_PHILOX, STREAM_P, k0, k1, 0, 0u, 0, 0};
+  sortk::carve_sort(w, 0, p, Np, B);
+  int32_t *perm = reinterpret_cast<int32_t *>(p + sortk::align256(sortk::sort_ws_bytes(Np, B)));
+  w.out[0] = perm;
+  cudaError_t e = sortk::launch_sort_one(w, 0, s);
+  if (e != cudaSuccess) return e;
+  const int T = 256;
+  k_fold_signs<<<(unsigned)((Np + T - 1) / T), T, 0, s>>>(Np, k0, k1, perm, Psd, nullptr, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_draws_sigma(int64_t Np, uint64_t seed, int32_t *sigma, void *ws, cudaStream_t s) {
+  const int B = sortk::bits_for(Np) > 10 ? sortk::bits_for(Np) - 10 : 0;
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  sortk::SortArrays w{};
+  w.key[0] = sortk::RowKey{sortk::KEY_PHILOX, STREAM_SIGMA, k0, k1, 0, 0u, 0, 0};
+  sortk::carve_sort(w, 0, ws, Np, B);
+  w.out[0] = sigma;
+  return sortk::launch_sort_one(w, 0, s);
+}
+
 cudaError_t launch_pos_map(const int32_t *sigma, int64_t Np, int64_t s0, int64_t s1, int log2, int32_t *pos,
                            cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(pos, 0xFF, 4 * (size_t)Np, s);

@@ -214,6 +214,12 @@ size_t draws_ws_bytes(int64_t Np);
 cudaError_t launch_draws(int64_t Np, uint64_t seed, int32_t *Psd /*N', sign-folded P*/,
                          int32_t *P /*nullable*/, int32_t *sigma, int8_t *D /*nullable*/,
                          void *ws, cudaStream_t s);
+// The two permutations one at a time, so that sigma (needed from pass 2 on) can be drawn beside
+// pass 1: launch_draws_perm writes Psd (ws: draws_one_ws_bytes + 4 N' bytes), launch_draws_sigma
+// writes sigma (ws: draws_one_ws_bytes).  Each gives the same array as launch_draws.
+size_t draws_one_ws_bytes(int64_t Np);
+cudaError_t launch_draws_perm(int64_t Np, uint64_t seed, int32_t *Psd, void *ws, cudaStream_t s);
+cudaError_t launch_draws_sigma(int64_t Np, uint64_t seed, int32_t *sigma, void *ws, cudaStream_t s);
 // pos[idx(k)] = s for k = sigma[s], s in [s0, s1), -1 elsewhere; idx(k) = (k mod n2) n1 + k div n2
 // with n2 = 2^log2 (the pass-1 group size; log2 = log2 N' for single-pass plans).
 cudaError_t launch_pos_map(const int32_t *sigma, int64_t Np, int64_t s0, int64_t s1, int log2, int32_t *pos,
@@ -238,7 +244,8 @@ cudaError_t launch_srht(const SrhtPlan &pl, int prec, int xdtype, const void *X,
                         void *copy_out = nullptr /* two-pass plans: X rows read by pass 1 (e.g. from
                                                     mapped host memory) are also stored here, same
                                                     element offsets (ldx); 16-byte aligned */,
-                        unsigned *status = nullptr /* ST_TIMEOUT raised here if a bounded wait gave up */);
+                        unsigned *status = nullptr /* ST_TIMEOUT raised here if a bounded wait gave up */,
+                        cudaEvent_t wait_pass2 = nullptr /* two-pass plans: s waits for it before pass 2 */);
 
 // grad.cu
 // GM_MIXED: the mixed 2nd-stage pass over X: the re-basing pass (error-free residuals) and the

@@ -254,5 +254,23 @@ inline cudaError_t launch_sort_pair(const SortArrays &w, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Runs sort y of `w` alone (its entry copied to slot 0; the other sort is not touched).
+inline cudaError_t launch_sort_one(const SortArrays &w, int y, cudaStream_t s) {
+  SortArrays v = w;
+  v.key[0] = w.key[y]; v.B[0] = w.B[y]; v.n[0] = w.n[y]; v.tidx[0] = w.tidx[y];
+  v.counts[0] = w.counts[y]; v.offsets[0] = w.offsets[y]; v.cursor[0] = w.cursor[y]; v.out[0] = w.out[y];
+  v.key[1] = v.key[0]; v.B[1] = v.B[0]; v.n[1] = v.n[0]; v.tidx[1] = v.tidx[0];
+  v.counts[1] = v.counts[0]; v.offsets[1] = v.offsets[0]; v.cursor[1] = v.cursor[0]; v.out[1] = v.out[0];
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(v.counts[0], 0, 4 * ((size_t)1 << v.B[0]), s)) != cudaSuccess) return e;
+  const int T = 256;
+  const unsigned grid = (unsigned)((v.n[0] + T - 1) / T);
+  if (grid > 0) k_keys_hist<<<dim3(grid, 1), T, 0, s>>>(v);
+  k_scan<<<1, 1024, 0, s>>>(v);
+  if (grid > 0) k_scatter<<<dim3(grid, 1), T, 0, s>>>(v);
+  k_bucket_sort<<<dim3(1u << v.B[0], 1), kSortThreads, 0, s>>>(v);
+  return cudaGetLastError();
+}
+
 }  // namespace sortk
 }  // namespace slse

@@ -659,7 +659,8 @@ cudaError_t run_plan(const SrhtPlan &pl, const void *X, int64_t ldx, const void 
                      void *V, int64_t ldu, double scale, cudaStream_t s,
                      cudaError_t (*pass2)(const GroupArgs &, int, int64_t, cudaStream_t), cudaEvent_t ev_mid,
                      uint8_t *Uscale = nullptr, int64_t ld_scale = 0, __nv_bfloat16 *hat = nullptr,
-                     int64_t hat_row0 = 0, int64_t hat_ld = 0, void *copy_out = nullptr, unsigned *status = nullptr) {
+                     int64_t hat_row0 = 0, int64_t hat_ld = 0, void *copy_out = nullptr, unsigned *status = nullptr,
+                     cudaEvent_t wait_pass2 = nullptr) {
   GroupArgs a = {};
   a.status = status;
   a.d = d;
@@ -679,6 +680,10 @@ cudaError_t run_plan(const SrhtPlan &pl, const void *X, int64_t ldx, const void 
     a.ostride = 1; a.ogstride = 0;
     a.scale = scale;
     a.logq = 0;
+    if (wait_pass2) {  // the one pass also reads pos
+      const cudaError_t e = cudaStreamWaitEvent(s, wait_pass2, 0);
+      if (e != cudaSuccess) return e;
+    }
     return launch_small_t<Tin, Ts, Tout, C>(a, pl.logN, s);
   }
   const int64_t n1 = int64_t(1) << pl.log1, n2 = int64_t(1) << pl.log2;
@@ -693,6 +698,7 @@ cudaError_t run_plan(const SrhtPlan &pl, const void *X, int64_t ldx, const void 
                            : launch_pass_t<Tin, Ts, Tout, VA, VB, VO, P1_SLAB, P1_MB, false>(a, pl.log2, n1, s);
   if (e != cudaSuccess) return e;
   if (ev_mid && (e = cudaEventRecord(ev_mid, s)) != cudaSuccess) return e;
+  if (wait_pass2 && (e = cudaStreamWaitEvent(s, wait_pass2, 0)) != cudaSuccess) return e;
   // pass 2: groups g = k2 (n2 of them), rows rho = j1 at stride n2, outputs kappa = k1
   GroupArgs b = a;
   b.Psd = nullptr;
@@ -727,22 +733,25 @@ cudaError_t launch_srht(const SrhtPlan &pl, int prec, int xdtype, const void *X,
                         int64_t N, int d, const int32_t *Psd, const int32_t *pos, void *W, void *WY,
                         int64_t ldw, void *U, void *V, int64_t ldu, double scale, cudaStream_t s,
                         cudaEvent_t ev_mid, uint8_t *Uscale, int64_t ld_scale, __nv_bfloat16 *hat,
-                        int64_t hat_row0, int64_t hat_ld, void *copy_out, unsigned *status) {
+                        int64_t hat_row0, int64_t hat_ld, void *copy_out, unsigned *status, cudaEvent_t wait_pass2) {
   using bf16 = __nv_bfloat16;
   if (copy_out && (pl.single || (uintptr_t)copy_out % 16 != 0)) return cudaErrorInvalidValue;
   if (prec == SLSE_PREC_FP64) {
     auto p2 = &launch_pass_t<double, double, double, 1, 1, 2>;
     if (xdtype == SLSE_F64)
       return run_plan<double, double, double, 16, 1, 1, 2>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale, s,
-                                                          p2, ev_mid, nullptr, 0, nullptr, 0, 0, copy_out, status);
+                                                          p2, ev_mid, nullptr, 0, nullptr, 0, 0, copy_out, status,
+                                                          wait_pass2);
     return run_plan<float, double, double, 16, 1, 1, 2>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale, s,
-                                                       p2, ev_mid, nullptr, 0, nullptr, 0, 0, copy_out, status);
+                                                       p2, ev_mid, nullptr, 0, nullptr, 0, 0, copy_out, status,
+                                                          wait_pass2);
   }
   if (prec == SLSE_PREC_MIXED_BF16 && xdtype == SLSE_F32) {
     // four CTAs per SM in both passes (measured against 3, 4, 5 and 6 with the mbarrier exchange)
     auto p2 = &launch_pass_t<bf16, float, bf16, 2, 2, 4, 128, 4>;
     return run_plan<float, float, bf16, 32, 2, 2, 4, 128, 4>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale,
-                                                             s, p2, ev_mid, nullptr, 0, nullptr, 0, 0, copy_out, status);
+                                                             s, p2, ev_mid, nullptr, 0, nullptr, 0, 0, copy_out, status,
+                                                          wait_pass2);
   }
   if (prec == SLSE_PREC_MIXED_FP8 && xdtype == SLSE_F32) {
     // pass 1 as in the BF16 form; pass 2 writes E4M3 rows with 32-column block scales
@@ -751,7 +760,7 @@ cudaError_t launch_srht(const SrhtPlan &pl, int prec, int xdtype, const void *X,
     auto p2 = &launch_pass_t<bf16, float, mx8, 2, 2, 4>;
     return run_plan<float, float, bf16, 32, 2, 2, 4, 128, 4>(pl, X, ldx, Y, N, d, Psd, pos, W, WY, ldw, U, V, ldu, scale,
                                                              s, p2, ev_mid, Uscale, ld_scale, hat, hat_row0, hat_ld,
-                                                             copy_out, status);
+                                                             copy_out, status, wait_pass2);
   }
   return cudaErrorInvalidValue;
 }
