@@ -138,22 +138,9 @@ __device__ __forceinline__ void warp_sum_rows(double (&v)[R], int lane) {
   for (int q = 0; q < R; ++q) v[q] = tot[q];
 }
 
-// Exact FP32 -> FP64 widening on the integer pipe.  The conversion instruction costs this pass
-// more than its two FP64 FMAs per element (measured at 2^21 x 512: 6.8 ms from FP32 storage
-// against 4.1 ms from FP64 storage), so normal floats and zeros are widened with integer
-// operations, without a branch: exponent re-biased by 1023 - 127 = 896 (zero keeps only its sign),
-// mantissa shifted up by 29 bits.  Denormals, infinities and NaNs are not: they set `special`,
-// and the caller then redoes its rows with the conversion instruction.
-__device__ __forceinline__ double widen(double v, bool &) { return v; }
-__device__ __forceinline__ double widen(float f, bool &special) {
-  const uint32_t u = __float_as_uint(f);
-  const uint32_t a = u & 0x7FFFFFFFu;
-  const uint32_t e = a >> 23;
-  special |= (e == 255u) | ((e == 0u) & (a != 0u));
-  const uint32_t hi = (u & 0x80000000u) | (a != 0u ? (a >> 3) + 0x38000000u : 0u);
-  return __hiloint2double((int)hi, (int)(u << 29));
-}
-
+// FP32 storage is widened by `widen` (integer pipe): the conversion instruction cost this pass
+// more than its two FP64 FMAs per element (at 2^21 x 512: 6.8 ms from FP32 storage against
+// 4.1 ms from FP64 storage, before the change).
 // Tx = double (X F64 or U F64) or float (X F32, widened exactly).  VW = elements per lane load,
 // VMAX = lane loads per row (sized to d), RPW = rows per warp iteration.
 template <class Tx, int VW, int VMAX, int RPW>

@@ -71,6 +71,22 @@ __device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
   e = fmaf(a, b, -p);
 }
 
+// Exact FP32 -> FP64 widening on the integer pipe.  The conversion instruction runs on the FP64
+// unit, which FP64-bound kernels need for their own arithmetic, so normal floats and zeros are
+// widened with integer operations, without a branch: exponent re-biased by 1023 - 127 = 896
+// (zero keeps only its sign), mantissa shifted up by 29 bits.  Denormals, infinities and NaNs
+// are not: they set `special`, and the caller redoes those values with the conversion
+// instruction (a warp-uniform, rare path).
+__device__ __forceinline__ double widen(double v, bool &) { return v; }
+__device__ __forceinline__ double widen(float f, bool &special) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t a = u & 0x7FFFFFFFu;
+  const uint32_t e = a >> 23;
+  special |= (e == 255u) | ((e == 0u) & (a != 0u));
+  const uint32_t hi = (u & 0x80000000u) | (a != 0u ? (a >> 3) + 0x38000000u : 0u);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
 // ----------------------------------------------------------------------------------
 // Bounded grid barrier for cooperative launches.  All CTAs of the grid must call it
 // the same number of times.  Gives up after ~1 s and raises ST_TIMEOUT; returns false

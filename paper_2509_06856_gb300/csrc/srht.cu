@@ -299,12 +299,33 @@ __global__ void __launch_bounds__(NT, MINB) k_group(const GroupArgs a) {
     const int col = col0 + cq * VA;
     Ts v[VA][RA];
     if (fast_in) {
+      if constexpr (sizeof(Tin) == 4 && sizeof(Ts) == 8 && Q > 1 && !CPY) {
+        // FP64 arithmetic on FP32 storage (clustered sizes, device input): widened on the
+        // integer pipe (the FP64 pipe bounds this pass), the rare denormal, infinity or NaN
+        // with the conversion instruction
+        bool special = false;
 #pragma unroll
-      for (int k = 0; k < RA; ++k) {
-        Ts t[VA];
-        load_vec<Tin, Ts, VA>(in + s_off[b + (k << S1)] + col, t);
+        for (int k = 0; k < RA; ++k) {
+          const Tin *p = in + s_off[b + (k << S1)] + col;
 #pragma unroll
-        for (int e = 0; e < VA; ++e) v[e][k] = t[e];
+          for (int e = 0; e < VA; ++e) v[e][k] = widen(__ldcs(p + e), special);
+        }
+        if (__any_sync(__activemask(), special)) {
+#pragma unroll
+          for (int k = 0; k < RA; ++k) {
+            const Tin *p = in + s_off[b + (k << S1)] + col;
+#pragma unroll
+            for (int e = 0; e < VA; ++e) v[e][k] = (Ts)p[e];
+          }
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < RA; ++k) {
+          Ts t[VA];
+          load_vec<Tin, Ts, VA>(in + s_off[b + (k << S1)] + col, t);
+#pragma unroll
+          for (int e = 0; e < VA; ++e) v[e][k] = t[e];
+        }
       }
       if constexpr (CPY) {
 #pragma unroll

@@ -60,6 +60,31 @@ def test_sketch_fp64_from_fp32_storage(slse):
     np.testing.assert_allclose(host(SY), oy, rtol=0, atol=1e-11)
 
 
+def test_sketch_fp64_from_fp32_storage_clustered_special_values(slse):
+    # a size whose pass-1 groups span a cluster (N' = 2^18: groups of 2^9 rows on 2 CTAs), FP32
+    # storage with signed zeros, denormals and the exponent limits scattered through X; then an
+    # infinity and a NaN, which must leave the sketch non-finite exactly where the oracle's is
+    rng = np.random.default_rng(11)
+    N, d, m = (1 << 17) + 5, 24, 4096
+    X = rng.standard_normal((N, d)).astype(np.float32)
+    Y = rng.standard_normal(N).astype(np.float32)
+    specials = np.array([0.0, -0.0, 1e-40, -3e-45, 1.1754944e-38, -1.1754942e-38, 2.0 ** -126, 3.0e30,
+                         -2.5e30, 1.0], np.float32)
+    X.reshape(-1)[rng.integers(0, N * d, size=5 * len(specials))] = np.tile(specials, 5)
+    SX, SY = slse.sketch(dev(X), dev(Y), m, seed=6, prec="fp64")
+    ox, oy = osk.sketch(X.astype(np.float64), Y.astype(np.float64), m, 6)
+    scale = np.sqrt((X.astype(np.float64) ** 2).sum(0).max() / m)
+    np.testing.assert_allclose(host(SX), ox, rtol=0, atol=1e-12 * scale)
+    for bad in (np.float32(np.inf), np.float32(np.nan)):
+        Xb = X.copy()
+        Xb[N // 2, d // 3] = bad
+        SXb, _ = slse.sketch(dev(Xb), dev(Y), m, seed=6, prec="fp64")
+        oxb, _ = osk.sketch(Xb.astype(np.float64), Y.astype(np.float64), m, 6)
+        g = host(SXb)
+        assert np.array_equal(np.isfinite(g), np.isfinite(oxb))
+        assert np.array_equal(np.isnan(g), np.isnan(oxb))
+
+
 @pytest.mark.parametrize("N,d,m", [(37, 3, 11), (20000, 50, 6400), ((1 << 17) + 9, 64, 8192), ((1 << 20), 31, 1 << 14)])
 def test_sketch_bf16_matches_oracle_within_bf16_rounding(slse, N, d, m):
     # BF16 storage of the intermediate and of the output: relative rounding 2^-9 at
